@@ -1,0 +1,265 @@
+/*
+ * dogip.h -- C ABI of the GB300-native DoGIP library.
+ *
+ * DoGIP (double-grid integration with interpolation-projection; Vondrejc,
+ * arXiv 1710.09913) writes the Galerkin matrix of the weighted projection
+ * (Section 2.2, eq. linsys_gp) or of the scalar elliptic problem (Section 2.3,
+ * eq. linsys_se) on a simplex mesh with continuous P_p Lagrange elements as
+ *
+ *     A u . v = sum_T  B^* A_T B u_T . v_T
+ *
+ * (Theorems "Element-wise DoGIP for weighted projection" and "Element-wise
+ * DoGIP for the elliptic problem", eqs. wp_dogip_mul and ep_dogip_mul), where
+ * B interpolates the local P_p dofs u_T (their reference gradients for the
+ * elliptic form) onto the nodes of the double-grid space W (P_2p resp.
+ * discontinuous P_{2p-2}) of the reference simplex, and A_T is diagonal
+ * (projection) or block-diagonal with symmetric d x d blocks that carry the
+ * element Jacobian (elliptic).  dogip_apply evaluates Algorithm 1
+ * ("Matrix-vector multiplication for element-wise DoGIP") on the GPU;
+ * dogip_solve runs a Jacobi-preconditioned CG around it.
+ *
+ * Conventions for every entry point below:
+ *  - Return value: DOGIP_OK (0) or one of the DOGIP_E* codes; the message of
+ *    the last failure on the calling thread is dogip_last_error().  No C++
+ *    exception crosses this interface.
+ *  - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *    global memory of the context's device (e.g. torch CUDA tensors).  The
+ *    caller owns every pointer it passes; the library copies what it keeps.
+ *  - cuda_stream is a cudaStream_t (NULL = legacy default stream).  Calls
+ *    documented as asynchronous only enqueue work on it.
+ *  - Vectors with several right-hand sides are dof-major: entry (i, r) of an
+ *    [n x nrhs] array is at i * nrhs + r.
+ *  - Element numbering is the caller's cell order; dof numbering is the
+ *    library's (dogip_get_dofmap): dofs are numbered in order of first
+ *    appearance scanning cells in order and local nodes in local order.
+ *  - Local node order of P_q on the reference simplex: multi-indices alpha,
+ *    |alpha| <= q, in lexicographic order with the last coordinate fastest;
+ *    node alpha sits at sum_i (alpha_i / q) (v_i - v_0) + v_0.
+ */
+#ifndef DOGIP_H
+#define DOGIP_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DOGIP_API __attribute__((visibility("default")))
+#else
+#define DOGIP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define DOGIP_OK 0
+#define DOGIP_EINVAL 1      /* invalid argument, mesh or coefficient            */
+#define DOGIP_ENOMEM 2      /* device or host allocation failed                 */
+#define DOGIP_ECUDA 3       /* a CUDA runtime call failed                       */
+#define DOGIP_ENOTCONV 4    /* solver hit its iteration limit (result written)  */
+#define DOGIP_EBREAKDOWN 5  /* CG breakdown: p^T K p <= 0 or not finite         */
+#define DOGIP_ETIMEOUT 6    /* a host-side wait exceeded its time limit         */
+#define DOGIP_EUNSUPPORTED 7 /* valid request outside the compiled instances    */
+
+/* ------------------------------------------------------------ enumerations */
+#define DOGIP_PROJECTION 0  /* a(u,v) = int m u v            (Section 2.2)     */
+#define DOGIP_ELLIPTIC 1    /* a(u,v) = int M grad u . grad v (Section 2.3)    */
+
+#define DOGIP_COEF_ELEM_SCALAR 0 /* one scalar per cell: m_T, or M_T = m_T I   */
+#define DOGIP_COEF_ELEM_TENSOR 1 /* one symmetric d x d tensor M_T per cell    */
+
+#define DOGIP_FP64 0        /* FP64 storage and arithmetic                     */
+#define DOGIP_FP32 1        /* FP32 A_T, vectors and arithmetic                */
+
+#define DOGIP_SCATTER_ATOMIC 0 /* one pass, atomic adds (order not fixed)      */
+#define DOGIP_SCATTER_COLOUR 1 /* one pass per element colour, plain adds      */
+
+#define DOGIP_SOLVE_FP64 0  /* FP64 Jacobi-PCG                                 */
+#define DOGIP_SOLVE_MIXED 1 /* FP64 iterative refinement around an FP32 PCG    */
+
+typedef struct dogip_ctx dogip_ctx;
+
+/* Simplex mesh, host memory, caller order.  The library copies it. */
+typedef struct {
+  int dim;                 /* 2 (triangles) or 3 (tetrahedra)                  */
+  int64_t n_vertices;
+  const double* coords;    /* host [n_vertices x dim]                          */
+  int64_t n_cells;
+  const int32_t* cells;    /* host [n_cells x (dim+1)] vertex ids              */
+} dogip_mesh;
+
+typedef struct {
+  int dirichlet;   /* -1 default (1 for elliptic, 0 for projection); 1: zero
+                      Dirichlet rows/columns on boundary dofs (facets of one
+                      cell), i.e. the operator P K P + (I - P)                 */
+  int scatter;     /* DOGIP_SCATTER_*: element storage order (COLOUR sorts the
+                      cells by colour) and the default scatter of solves      */
+  int keep_fp32;   /* 1 (default): also keep an FP32 copy of A_T              */
+  int device;      /* CUDA device ordinal, -1 = current device                */
+} dogip_opts;
+
+/* Fill *o with the defaults above.  Never fails for o != NULL. */
+DOGIP_API int dogip_opts_default(dogip_opts* o);
+
+/*
+ * Build a context: dof map l_T (Section 2.1), boundary set, greedy element
+ * colouring, reference tables B and w (Theorems above), and -- on the device --
+ * the element factors A_T (dogip_set_coef) and the Jacobi diagonal.
+ *   m       : mesh (host), copied.
+ *   p       : polynomial order, 1 <= p <= 4.
+ *   form    : DOGIP_PROJECTION or DOGIP_ELLIPTIC.
+ *   coef_kind, coef : host coefficients in caller cell order, [n_cells] for
+ *             DOGIP_COEF_ELEM_SCALAR or [n_cells x dim x dim] for
+ *             DOGIP_COEF_ELEM_TENSOR (elliptic only); copied.
+ *   o       : options or NULL for defaults.
+ *   out     : receives the context; the caller frees it with dogip_destroy.
+ * Errors: EINVAL (bad sizes, vertex ids out of range, degenerate or
+ * non-finite cell, non-symmetric / non-positive coefficient), ENOMEM, ECUDA,
+ * EUNSUPPORTED (p outside the compiled range).  Synchronous.
+ */
+DOGIP_API int dogip_setup(const dogip_mesh* m, int p, int form, int coef_kind,
+                const double* coef, const dogip_opts* o, dogip_ctx** out);
+
+/* Free a context and all memory it owns (synchronises its device). */
+DOGIP_API void dogip_destroy(dogip_ctx* ctx);
+
+/*
+ * Recompute A_T (eq. ep_dogip_mul: A_T,j = |det R_T| w_j R_T^-1 M_T R_T^-T;
+ * eq. wp_dogip_mul: A_T,j = m_T |det R_T| w_j) and the Jacobi diagonal from new
+ * coefficients, keeping mesh, dofs and tables.  coef is DEVICE memory in caller
+ * cell order with the layout of dogip_setup.  Enqueued on cuda_stream; the
+ * call then synchronises that stream to report invalid coefficients (EINVAL).
+ */
+DOGIP_API int dogip_set_coef(dogip_ctx* ctx, int coef_kind, const double* coef,
+                   void* cuda_stream);
+
+/* ----------------------------------------------------------------- queries */
+typedef struct {
+  int dim, p, form, coef_kind, dirichlet, scatter;
+  int64_t n_cells, n_dofs, n_boundary;
+  int v_loc;        /* V_T = dim P_p                                          */
+  int w_loc;        /* W_T = dim P_2p (projection) or dim P_{2p-2} (elliptic) */
+  int n_sym;        /* stored entries per W node: 1 or dim(dim+1)/2           */
+  int n_colours;
+  int64_t nnz_b, nnz_pm1_b; /* nonzero / +-1 entries of B (eq. comp_eff)     */
+  int64_t bytes_ahat_fp64, bytes_ahat_fp32, bytes_conn;
+} dogip_info;
+
+DOGIP_API int dogip_get_info(const dogip_ctx* ctx, dogip_info* info);
+DOGIP_API int64_t dogip_ndofs(const dogip_ctx* ctx); /* -1 on NULL ctx */
+
+/* Dof map l_T: host [n_cells x V_T] global dof ids, caller cell order. */
+DOGIP_API int dogip_get_dofmap(const dogip_ctx* ctx, int32_t* host_out);
+/* Colour of every cell: host [n_cells]; *n_colours receives the count. */
+DOGIP_API int dogip_get_colouring(const dogip_ctx* ctx, int32_t* host_out, int* n_colours);
+/* Boundary flags: host [n_dofs], 1 on dofs of boundary facets. */
+DOGIP_API int dogip_get_boundary(const dogip_ctx* ctx, uint8_t* host_out);
+/* A_T in FP64: device [n_cells x W_T x n_sym], caller cell order; symmetric
+ * blocks packed as (00,01,11) in 2D and (00,01,02,11,12,22) in 3D.  Async. */
+DOGIP_API int dogip_get_ahat(const dogip_ctx* ctx, double* dev_out, void* cuda_stream);
+/* Jacobi diagonal of the operator (1 on Dirichlet rows): device [n_dofs]. Async. */
+DOGIP_API int dogip_get_diag(const dogip_ctx* ctx, double* dev_out, void* cuda_stream);
+
+/*
+ * Reference tables of the library, independent of any context (host):
+ *   bhat : [NB x W_T x V_T], NB = 1 (projection) or dim (elliptic), may be NULL
+ *   what : [W_T] integrals of the W basis over the reference simplex, may be NULL
+ *   sizes: [3] receives NB, W_T, V_T, may be NULL.
+ */
+DOGIP_API int dogip_get_tables(int dim, int p, int form, double* bhat, double* what,
+                     int* sizes);
+
+/* ------------------------------------------------------------------- apply */
+/*
+ * y = K u  (Algorithm 1: gather u_T, interpolate B u_T, multiply by A_T, project
+ * back B^*, scatter-add), with K = P K P + (I - P) when Dirichlet rows are on.
+ *   u, y  : DEVICE [n_dofs x nrhs], double (DOGIP_FP64) or float (DOGIP_FP32);
+ *           y is overwritten; u and y must not overlap.
+ *   nrhs  : >= 1.
+ *   prec  : DOGIP_FP64 or DOGIP_FP32 (the latter needs keep_fp32).
+ *   scatter: DOGIP_SCATTER_ATOMIC, or DOGIP_SCATTER_COLOUR (needs a context
+ *           set up with scatter = COLOUR), or -1 for the context default.
+ * Asynchronous on cuda_stream; no host synchronisation.
+ */
+DOGIP_API int dogip_apply(dogip_ctx* ctx, const void* u, void* y, int nrhs, int prec,
+                int scatter, void* cuda_stream);
+
+/*
+ * Load vector of an element-wise constant source: b_i = sum_T f_T int_T phi_i
+ * (f = 1 when f_elem is NULL); boundary entries set to 0 when Dirichlet rows
+ * are on.  f_elem: DEVICE [n_cells] caller order or NULL; b: DEVICE [n_dofs].
+ * Asynchronous.
+ */
+DOGIP_API int dogip_load(dogip_ctx* ctx, const double* f_elem, double* b, void* cuda_stream);
+
+/* ------------------------------------------------------------------- solve */
+typedef struct {
+  int mode;           /* DOGIP_SOLVE_FP64 or DOGIP_SOLVE_MIXED                */
+  double tol;         /* target ||b - K u||_2 / ||b||_2 (FP64), per rhs        */
+  int maxiter;        /* FP64 mode: PCG iterations; mixed: total inner ones    */
+  double inner_tol;   /* mixed: relative residual reduction per inner solve   */
+  int inner_maxiter;  /* mixed: iteration limit of one inner solve             */
+  int max_outer;      /* mixed: refinement steps                               */
+  int scatter;        /* -1 context default, else DOGIP_SCATTER_*              */
+  int check_every;    /* iterations per device-resident chunk between host
+                         convergence checks (>= 1)                             */
+  int use_x0;         /* 1: u holds the initial guess; 0: start from u = 0     */
+  double timeout_ms;  /* host wall-clock limit, <= 0 for none                  */
+} dogip_solve_opts;
+
+typedef struct {
+  int status;           /* same as the return value                          */
+  int iterations;       /* FP64 PCG iterations, or total inner iterations    */
+  int outer;            /* refinement steps (mixed)                          */
+  double rel_residual;  /* max over rhs of the final FP64 true relative residual */
+  double seconds;       /* host wall time of the call                        */
+} dogip_solve_info;
+
+DOGIP_API int dogip_solve_opts_default(dogip_solve_opts* o);
+
+/*
+ * Solve K u = b (K with Dirichlet rows when on; Jacobi preconditioner from
+ * A_T).  b, u: DEVICE double [n_dofs x nrhs]; nrhs in {1, 2, 4, 8, 16, 32}.
+ * FP64 mode: PCG until the recursive residual reaches tol, then the true
+ * residual is evaluated in FP64.  Mixed mode: r = b - K u, norms and the
+ * update u += s d in FP64; inner PCG on K d = r / s entirely in FP32.
+ * rel_residual_per_rhs: host [nrhs] or NULL.  Returns ENOTCONV (u written)
+ * when the limits are reached first.  Synchronises cuda_stream.
+ */
+DOGIP_API int dogip_solve(dogip_ctx* ctx, const double* b, double* u, int nrhs,
+                const dogip_solve_opts* o, dogip_solve_info* info,
+                double* rel_residual_per_rhs, void* cuda_stream);
+
+/*
+ * dogip_solve with HOST b and u (pageable or pinned): copies b in, solves,
+ * copies u out, all on cuda_stream.  Same arguments and errors otherwise.
+ */
+DOGIP_API int dogip_solve_host(dogip_ctx* ctx, const double* b_host, double* u_host,
+                     int nrhs, const dogip_solve_opts* o,
+                     dogip_solve_info* info, double* rel_residual_per_rhs,
+                     void* cuda_stream);
+
+/* ---------------------------------------------------------------- gradient */
+/*
+ * Gradient of the compliance-type functional J = lambda^T K(A) u with respect
+ * to the element coefficients: for J = b^T u with K u = b, the adjoint gives
+ * dJ/dA = -(dK/dA)[u, lambda] with lambda = u.  Per cell (caller order):
+ *   elliptic, tensor : dA[T,p,q] = -sum_j om_j (grad lambda)(x_j)_p (grad u)(x_j)_q
+ *   elliptic, scalar : dA[T]     = -sum_j om_j  grad lambda(x_j) . grad u(x_j)
+ *   projection       : dA[T]     = -sum_j om_j  lambda(x_j) u(x_j)
+ * om_j = |det R_T| w_j, x_j the W nodes (eqs. wp_dogip_mul / ep_dogip_mul with
+ * the coefficient factored out).  Boundary dofs are masked as in dogip_apply.
+ * u, lam: DEVICE double [n_dofs]; dA: DEVICE double [n_cells (x dim x dim)].
+ * Asynchronous.
+ */
+DOGIP_API int dogip_grad_coef(dogip_ctx* ctx, const double* u, const double* lam,
+                    double* dA, void* cuda_stream);
+
+/* ------------------------------------------------------------------ errors */
+DOGIP_API const char* dogip_last_error(void); /* thread-local, never NULL */
+DOGIP_API int dogip_version(void);            /* major * 10000 + minor * 100 + patch */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DOGIP_H */

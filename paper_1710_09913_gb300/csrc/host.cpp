@@ -1,0 +1,841 @@
+// Host side of the DoGIP library: mesh topology (dof map l_T, boundary set,
+// colouring), context construction, queries, the solve driver and the C ABI.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace dogip {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void fail(int code, const std::string& msg) { throw Failure{code, msg}; }
+
+void cuda_check(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(e == cudaErrorMemoryAllocation ? DOGIP_ENOMEM : DOGIP_ECUDA,
+         std::string(what) + ": " + cudaGetErrorString(e));
+  }
+}
+
+namespace {
+
+// ---------------------------------------------------------------- hashing
+// Open-addressing table from a key of up to four 64-bit words to an int32.
+struct KeyTable {
+  static constexpr uint64_t kEmpty = ~0ull;
+  std::vector<uint64_t> keys;  // 4 words per slot
+  std::vector<int32_t> vals;
+  size_t mask = 0, count = 0;
+
+  explicit KeyTable(size_t expect) { init(expect); }
+  void init(size_t expect) {
+    size_t cap = 16;
+    while (cap < 2 * expect + 16) cap <<= 1;
+    keys.assign(cap * 4, kEmpty);
+    vals.assign(cap, -1);
+    mask = cap - 1;
+    count = 0;
+  }
+  static uint64_t mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+  static uint64_t hash(const uint64_t* k) {
+    return mix(k[0] ^ mix(k[1] ^ mix(k[2] ^ mix(k[3] + 0x9E3779B97F4A7C15ull))));
+  }
+  // Returns the value for k, inserting `fresh` if absent (then *inserted = true).
+  int32_t find_or_insert(const uint64_t* k, int32_t fresh, bool* inserted) {
+    if (2 * (count + 1) > mask + 1) grow();
+    size_t h = hash(k) & mask;
+    while (true) {
+      uint64_t* s = &keys[h * 4];
+      if (s[0] == kEmpty) {
+        std::memcpy(s, k, 32);
+        vals[h] = fresh;
+        ++count;
+        *inserted = true;
+        return fresh;
+      }
+      if (s[0] == k[0] && s[1] == k[1] && s[2] == k[2] && s[3] == k[3]) {
+        *inserted = false;
+        return vals[h];
+      }
+      h = (h + 1) & mask;
+    }
+  }
+  void grow() {
+    std::vector<uint64_t> ok;
+    std::vector<int32_t> ov;
+    ok.swap(keys);
+    ov.swap(vals);
+    const size_t oldcap = ov.size();
+    keys.assign(oldcap * 2 * 4, kEmpty);
+    vals.assign(oldcap * 2, -1);
+    mask = oldcap * 2 - 1;
+    for (size_t i = 0; i < oldcap; ++i) {
+      if (ok[i * 4] == kEmpty) continue;
+      size_t h = hash(&ok[i * 4]) & mask;
+      while (keys[h * 4] != kEmpty) h = (h + 1) & mask;
+      std::memcpy(&keys[h * 4], &ok[i * 4], 32);
+      vals[h] = ov[i];
+    }
+  }
+};
+
+// Multi-indices |alpha| <= q in product order (last coordinate fastest).
+std::vector<std::vector<int>> multi_indices(int d, int q) {
+  std::vector<std::vector<int>> out;
+  std::vector<int> a(d, 0);
+  int lim = q + 1, tot = 1;
+  for (int i = 0; i < d; ++i) tot *= lim;
+  for (int c = 0; c < tot; ++c) {
+    int t = c, s = 0;
+    for (int i = d - 1; i >= 0; --i) {
+      a[i] = t % lim;
+      t /= lim;
+      s += a[i];
+    }
+    if (s <= q) out.push_back(a);
+  }
+  return out;
+}
+
+// Barycentric multi-indices (p - |alpha|, alpha) of the local P_p nodes.
+std::vector<std::vector<int>> local_betas(int d, int p) {
+  std::vector<std::vector<int>> out;
+  for (auto& a : multi_indices(d, p)) {
+    std::vector<int> b(d + 1);
+    int s = 0;
+    for (int i = 0; i < d; ++i) {
+      b[i + 1] = a[i];
+      s += a[i];
+    }
+    b[0] = p - s;
+    out.push_back(b);
+  }
+  return out;
+}
+
+// Dof map by first appearance: node identity = multiset {(v_i, beta_i): beta_i > 0}.
+void build_dofmap(Ctx& c, const int32_t* cells) {
+  const int d = c.d, V = c.VT;
+  auto betas = local_betas(d, c.p);
+  c.dofmap.assign((size_t)c.E * V, 0);
+  KeyTable tab((size_t)c.E * V / 2 + 64);
+  int32_t next = 0;
+  uint64_t key[4];
+  std::pair<uint64_t, int> pr[4];
+  for (int64_t e = 0; e < c.E; ++e) {
+    const int32_t* cv = cells + e * (d + 1);
+    for (int l = 0; l < V; ++l) {
+      int m = 0;
+      for (int i = 0; i <= d; ++i)
+        if (betas[l][i] > 0) pr[m++] = {(uint64_t)(uint32_t)cv[i], betas[l][i]};
+      std::sort(pr, pr + m);
+      for (int k = 0; k < 4; ++k) key[k] = k < m ? ((pr[k].first << 8) | (uint64_t)pr[k].second) : KeyTable::kEmpty - 1;
+      bool ins = false;
+      const int32_t id = tab.find_or_insert(key, next, &ins);
+      if (ins) {
+        if (next == (int32_t)kIdMask) fail(DOGIP_EINVAL, "too many dofs (>= 2^30)");
+        ++next;
+      }
+      c.dofmap[(size_t)e * V + l] = id;
+    }
+  }
+  c.n = next;
+}
+
+// Boundary dofs: nodes with beta_i = 0 for a local facet i (opposite vertex i)
+// that belongs to exactly one cell.
+void build_boundary(Ctx& c, const int32_t* cells) {
+  const int d = c.d, V = c.VT;
+  auto betas = local_betas(d, c.p);
+  c.bmask.assign(c.n, 0);
+  if (!c.dirichlet) return;
+  KeyTable tab((size_t)c.E * (d + 1) / 2 + 64);
+  std::vector<int32_t> fid((size_t)c.E * (d + 1));
+  std::vector<int32_t> cnt;
+  uint64_t key[4];
+  for (int64_t e = 0; e < c.E; ++e) {
+    const int32_t* cv = cells + e * (d + 1);
+    for (int i = 0; i <= d; ++i) {
+      uint64_t f[3];
+      int m = 0;
+      for (int k = 0; k <= d; ++k)
+        if (k != i) f[m++] = (uint64_t)(uint32_t)cv[k];
+      std::sort(f, f + m);
+      for (int k = 0; k < 4; ++k) key[k] = k < m ? f[k] : KeyTable::kEmpty - 1;
+      bool ins = false;
+      const int32_t id = tab.find_or_insert(key, (int32_t)cnt.size(), &ins);
+      if (ins) cnt.push_back(0);
+      cnt[id] += 1;
+      fid[(size_t)e * (d + 1) + i] = id;
+    }
+  }
+  for (int64_t e = 0; e < c.E; ++e)
+    for (int i = 0; i <= d; ++i)
+      if (cnt[fid[(size_t)e * (d + 1) + i]] == 1)
+        for (int l = 0; l < V; ++l)
+          if (betas[l][i] == 0) c.bmask[c.dofmap[(size_t)e * V + l]] = 1;
+}
+
+// Greedy colouring: cells in order take the smallest colour not used by an
+// earlier cell sharing a vertex.
+void build_colouring(Ctx& c, const int32_t* cells) {
+  const int d = c.d;
+  std::vector<int64_t> start(c.nv + 1, 0);
+  for (int64_t k = 0; k < c.E * (d + 1); ++k) start[cells[k] + 1]++;
+  for (int64_t v = 0; v < c.nv; ++v) start[v + 1] += start[v];
+  std::vector<int32_t> inc(c.E * (d + 1));
+  std::vector<int64_t> fill(start.begin(), start.end() - 1);
+  for (int64_t e = 0; e < c.E; ++e)
+    for (int i = 0; i <= d; ++i) inc[fill[cells[e * (d + 1) + i]]++] = (int32_t)e;
+  c.colour.assign(c.E, -1);
+  std::vector<int64_t> stamp(64, -1);
+  int ncol = 0;
+  for (int64_t e = 0; e < c.E; ++e) {
+    for (int i = 0; i <= d; ++i) {
+      const int32_t v = cells[e * (d + 1) + i];
+      for (int64_t k = start[v]; k < start[v + 1]; ++k) {
+        const int32_t f = inc[k];
+        if (f >= e) break;  // incidence lists are in increasing cell order
+        const int cf = c.colour[f];
+        if (cf >= (int)stamp.size()) stamp.resize(cf * 2 + 1, -1);
+        stamp[cf] = e;
+      }
+    }
+    int col = 0;
+    while (col < (int)stamp.size() && stamp[col] == e) ++col;
+    if (col >= (int)stamp.size()) stamp.resize(col * 2 + 1, -1);
+    c.colour[e] = col;
+    ncol = std::max(ncol, col + 1);
+  }
+  c.ncolours = ncol;
+}
+
+template <typename T>
+T* dev_alloc(size_t count) {
+  if (count == 0) count = 1;
+  T* p = nullptr;
+  if (cudaMalloc((void**)&p, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    fail(DOGIP_ENOMEM, "device allocation failed");
+  }
+  return p;
+}
+
+void free_ctx(Ctx* c) {
+  if (!c) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  vec_free(c->work);
+  for (void* p : {(void*)c->d_coords, (void*)c->d_cells, (void*)c->d_perm, (void*)c->d_conn,
+                  (void*)c->d_A64, (void*)c->d_A32, (void*)c->d_geo, (void*)c->d_diag,
+                  (void*)c->d_dinv64, (void*)c->d_dinv32, (void*)c->d_bnd, (void*)c->d_coef,
+                  (void*)c->d_err})
+    if (p) cudaFree(p);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
+  cudaSetDevice(cur);
+  delete c;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cuda_check(cudaSetDevice(dev), "cudaSetDevice");
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+void check_coef_status(Ctx& c, cudaStream_t s) {
+  int err = 0;
+  cuda_check(cudaMemcpyAsync(&err, c.d_err, sizeof(int), cudaMemcpyDeviceToHost, s), "read flags");
+  cuda_check(cudaStreamSynchronize(s), "setup kernels");
+  if (err) {
+    std::string m = "invalid input:";
+    if (err & kErrGeometry) m += " degenerate or non-finite cell;";
+    if (err & kErrNonFinite) m += " non-finite coefficient;";
+    if (err & kErrSymmetry) m += " non-symmetric coefficient tensor;";
+    if (err & kErrNotPos) m += " coefficient not positive (definite);";
+    fail(DOGIP_EINVAL, m);
+  }
+}
+
+Ctx* setup(const dogip_mesh* m, int p, int form, int coef_kind, const double* coef,
+           const dogip_opts* opts) {
+  if (!m || !coef) fail(DOGIP_EINVAL, "mesh and coefficients are required");
+  if (m->dim != 2 && m->dim != 3) fail(DOGIP_EINVAL, "dim must be 2 or 3");
+  if (form != DOGIP_PROJECTION && form != DOGIP_ELLIPTIC) fail(DOGIP_EINVAL, "unknown form");
+  if (coef_kind != DOGIP_COEF_ELEM_SCALAR && coef_kind != DOGIP_COEF_ELEM_TENSOR)
+    fail(DOGIP_EINVAL, "unknown coefficient kind");
+  if (form == DOGIP_PROJECTION && coef_kind != DOGIP_COEF_ELEM_SCALAR)
+    fail(DOGIP_EINVAL, "the weighted projection takes a scalar coefficient");
+  if (m->n_vertices <= 0 || m->n_cells <= 0 || !m->coords || !m->cells)
+    fail(DOGIP_EINVAL, "empty mesh");
+  if (m->n_vertices >= (int64_t)1 << 31) fail(DOGIP_EINVAL, "too many vertices");
+  if (p < 1) fail(DOGIP_EINVAL, "p must be >= 1");
+  dogip_opts o;
+  dogip_opts_default(&o);
+  if (opts) o = *opts;
+  int NB, W, V;
+  long long nnz, nnz1;
+  if (!table_info(m->dim, p, form, &NB, &W, &V, &nnz, &nnz1))
+    fail(DOGIP_EUNSUPPORTED, "p outside the compiled range (1..4)");
+  const int d = m->dim;
+  for (int64_t k = 0; k < m->n_cells * (d + 1); ++k)
+    if (m->cells[k] < 0 || m->cells[k] >= m->n_vertices)
+      fail(DOGIP_EINVAL, "cell vertex id out of range");
+  for (int64_t k = 0; k < m->n_vertices * d; ++k)
+    if (!std::isfinite(m->coords[k])) fail(DOGIP_EINVAL, "non-finite vertex coordinate");
+
+  int dev = o.device;
+  if (dev < 0) cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+  DeviceGuard guard(dev);
+
+  Ctx* c = new Ctx();  // Ctx is the ABI's dogip_ctx
+  try {
+    c->device = dev;
+    c->d = d;
+    c->p = p;
+    c->form = form;
+    c->coef_kind = coef_kind;
+    c->NB = NB;
+    c->WT = W;
+    c->VT = V;
+    c->NS = form == DOGIP_ELLIPTIC ? d * (d + 1) / 2 : 1;
+    c->nnzb = nnz;
+    c->nnzb1 = nnz1;
+    c->dirichlet = o.dirichlet < 0 ? form == DOGIP_ELLIPTIC : o.dirichlet != 0;
+    c->scatter = o.scatter == DOGIP_SCATTER_COLOUR ? DOGIP_SCATTER_COLOUR : DOGIP_SCATTER_ATOMIC;
+    c->keep32 = o.keep_fp32 != 0;
+    c->E = m->n_cells;
+    c->Epad = (c->E + kTile - 1) / kTile * kTile;
+    c->nv = m->n_vertices;
+
+    build_dofmap(*c, m->cells);
+    build_boundary(*c, m->cells);
+    build_colouring(*c, m->cells);
+
+    // processing order: colour-sorted (stable) for colour scatter, else identity
+    c->perm.resize(c->E);
+    std::iota(c->perm.begin(), c->perm.end(), 0);
+    if (c->scatter == DOGIP_SCATTER_COLOUR) {
+      std::stable_sort(c->perm.begin(), c->perm.end(),
+                       [&](int64_t a, int64_t b) { return c->colour[a] < c->colour[b]; });
+      c->colour_start.assign(c->ncolours + 1, 0);
+      for (int64_t e = 0; e < c->E; ++e) c->colour_start[c->colour[e] + 1]++;
+      for (int k = 0; k < c->ncolours; ++k) c->colour_start[k + 1] += c->colour_start[k];
+    } else {
+      c->colour_start = {0, c->E};
+    }
+
+    std::vector<int32_t> bnd;
+    for (int64_t i = 0; i < c->n; ++i)
+      if (c->bmask[i]) bnd.push_back((int32_t)i);
+    c->nbnd = (int64_t)bnd.size();
+
+    std::vector<uint32_t> conn((size_t)c->Epad * V, 0u);
+    std::vector<int32_t> pcells((size_t)c->E * (d + 1));
+    for (int64_t pos = 0; pos < c->E; ++pos) {
+      const int64_t e = c->perm[pos];
+      for (int l = 0; l < V; ++l) {
+        const int32_t id = c->dofmap[(size_t)e * V + l];
+        conn[(size_t)(pos / kTile) * V * kTile + (size_t)l * kTile + pos % kTile] =
+            (uint32_t)id | (c->bmask[id] ? kBndBit : 0u);
+      }
+      for (int i = 0; i <= d; ++i) pcells[(size_t)pos * (d + 1) + i] = m->cells[e * (d + 1) + i];
+    }
+
+    cuda_check(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking), "stream");
+    cuda_check(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming), "event");
+    cuda_check(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming), "event");
+    const size_t ncoef = (size_t)c->E * (coef_kind == DOGIP_COEF_ELEM_TENSOR ? d * d : 1);
+    c->d_coords = dev_alloc<double>((size_t)c->nv * d);
+    c->d_cells = dev_alloc<int32_t>(pcells.size());
+    c->d_perm = dev_alloc<int64_t>(c->E);
+    c->d_conn = dev_alloc<uint32_t>(conn.size());
+    c->d_A64 = dev_alloc<double>((size_t)c->Epad * W * c->NS);
+    if (c->keep32) c->d_A32 = dev_alloc<float>((size_t)c->Epad * W * c->NS);
+    c->d_geo = dev_alloc<double>((size_t)c->E * (d * d + 1));
+    c->d_diag = dev_alloc<double>(c->n);
+    c->d_dinv64 = dev_alloc<double>(c->n);
+    c->d_dinv32 = dev_alloc<float>(c->n);
+    c->d_bnd = dev_alloc<int32_t>(bnd.size());
+    c->d_coef = dev_alloc<double>(ncoef);
+    c->d_err = dev_alloc<int>(1);
+    cudaStream_t s = c->stream;
+    cuda_check(cudaMemcpyAsync(c->d_coords, m->coords, sizeof(double) * c->nv * d,
+                               cudaMemcpyHostToDevice, s), "upload coords");
+    cuda_check(cudaMemcpyAsync(c->d_cells, pcells.data(), sizeof(int32_t) * pcells.size(),
+                               cudaMemcpyHostToDevice, s), "upload cells");
+    cuda_check(cudaMemcpyAsync(c->d_perm, c->perm.data(), sizeof(int64_t) * c->E,
+                               cudaMemcpyHostToDevice, s), "upload perm");
+    cuda_check(cudaMemcpyAsync(c->d_conn, conn.data(), sizeof(uint32_t) * conn.size(),
+                               cudaMemcpyHostToDevice, s), "upload conn");
+    if (!bnd.empty())
+      cuda_check(cudaMemcpyAsync(c->d_bnd, bnd.data(), sizeof(int32_t) * bnd.size(),
+                                 cudaMemcpyHostToDevice, s), "upload boundary");
+    cuda_check(cudaMemcpyAsync(c->d_coef, coef, sizeof(double) * ncoef, cudaMemcpyHostToDevice, s),
+               "upload coefficients");
+    // padding of A_T stays zero
+    cuda_check(cudaMemsetAsync(c->d_A64, 0, sizeof(double) * c->Epad * W * c->NS, s), "memset A");
+    if (c->keep32)
+      cuda_check(cudaMemsetAsync(c->d_A32, 0, sizeof(float) * c->Epad * W * c->NS, s), "memset A32");
+    cuda_check(cudaMemsetAsync(c->d_err, 0, sizeof(int), s), "memset err");
+    launch_ahat(*c, c->d_coef, coef_kind, s);
+    check_coef_status(*c, s);
+  } catch (...) {
+    free_ctx(c);
+    throw;
+  }
+  return c;
+}
+
+void set_coef(Ctx& c, int coef_kind, const double* coef, cudaStream_t s) {
+  if (!coef) fail(DOGIP_EINVAL, "coefficients are required");
+  if (c.form == DOGIP_PROJECTION && coef_kind != DOGIP_COEF_ELEM_SCALAR)
+    fail(DOGIP_EINVAL, "the weighted projection takes a scalar coefficient");
+  if (coef_kind != DOGIP_COEF_ELEM_SCALAR && coef_kind != DOGIP_COEF_ELEM_TENSOR)
+    fail(DOGIP_EINVAL, "unknown coefficient kind");
+  DeviceGuard guard(c.device);
+  c.coef_kind = coef_kind;
+  cuda_check(cudaMemsetAsync(c.d_err, 0, sizeof(int), s), "memset err");
+  launch_ahat(c, coef, coef_kind, s);
+  check_coef_status(c, s);
+}
+
+// ------------------------------------------------------------------- solve
+
+bool r_ok(int R) { return R == 1 || R == 2 || R == 4 || R == 8 || R == 16 || R == 32; }
+
+// One chunk of `k` CG iterations on the solver stream, captured once as a CUDA
+// graph and replayed; ends with a copy of the flags and scalars to pinned host.
+void run_chunk(Ctx& c, int prec, int scatter, double* x64, int k) {
+  SolveWork& w = c.work;
+  cudaStream_t s = c.stream;
+  const void* key0 = prec == DOGIP_FP64 ? (const void*)x64 : (const void*)w.x32;
+  const bool hit = w.graph && w.graph_prec == prec && w.graph_scatter == scatter &&
+                   w.graph_chunk == k && w.graph_key[0] == key0 && w.graph_key[1] == (void*)w.p64;
+  if (!hit) {
+    if (w.graph) cudaGraphExecDestroy(w.graph);
+    w.graph = nullptr;
+    cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
+    try {
+      for (int it = 0; it < k; ++it) {
+        if (prec == DOGIP_FP64) {
+          launch_apply(c, w.p64, w.q64, w.R, DOGIP_FP64, scatter, s, w.flags);
+          vec_cg_step(w, DOGIP_FP64, x64, c.d_dinv64, s);
+        } else {
+          launch_apply(c, w.p32, w.q32, w.R, DOGIP_FP32, scatter, s, w.flags);
+          vec_cg_step(w, DOGIP_FP32, nullptr, c.d_dinv32, s);
+        }
+      }
+      cuda_check(cudaMemcpyAsync(w.h_flags, w.flags, sizeof(int) * 2, cudaMemcpyDeviceToHost, s),
+                 "flags copy");
+      cuda_check(cudaMemcpyAsync(w.h_scal, w.scal, sizeof(CGScal) * w.R, cudaMemcpyDeviceToHost, s),
+                 "scal copy");
+    } catch (...) {
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(s, &g);
+      if (g) cudaGraphDestroy(g);
+      throw;
+    }
+    cudaGraph_t g = nullptr;
+    cuda_check(cudaStreamEndCapture(s, &g), "end capture");
+    cudaError_t e = cudaGraphInstantiate(&w.graph, g, 0);
+    cudaGraphDestroy(g);
+    cuda_check(e, "graph instantiate");
+    w.graph_prec = prec;
+    w.graph_scatter = scatter;
+    w.graph_chunk = k;
+    w.graph_key[0] = key0;
+    w.graph_key[1] = w.p64;
+  }
+  cuda_check(cudaGraphLaunch(w.graph, s), "graph launch");
+  cuda_check(cudaStreamSynchronize(s), "cg chunk");
+}
+
+void read_scal(Ctx& c) {
+  SolveWork& w = c.work;
+  cuda_check(cudaMemcpyAsync(w.h_scal, w.scal, sizeof(CGScal) * w.R, cudaMemcpyDeviceToHost, c.stream),
+             "scal copy");
+  cuda_check(cudaMemcpyAsync(w.h_flags, w.flags, sizeof(int) * 2, cudaMemcpyDeviceToHost, c.stream),
+             "flags copy");
+  cuda_check(cudaStreamSynchronize(c.stream), "scal sync");
+}
+
+int solve(Ctx& c, const double* b, double* u, int R, const dogip_solve_opts* opts,
+          dogip_solve_info* info, double* rel_out, cudaStream_t user) {
+  const auto t0 = std::chrono::steady_clock::now();
+  dogip_solve_opts o;
+  dogip_solve_opts_default(&o);
+  if (opts) o = *opts;
+  if (!b || !u) fail(DOGIP_EINVAL, "b and u are required");
+  if (!r_ok(R)) fail(DOGIP_EINVAL, "nrhs must be 1, 2, 4, 8, 16 or 32 for solves");
+  if (o.mode != DOGIP_SOLVE_FP64 && o.mode != DOGIP_SOLVE_MIXED) fail(DOGIP_EINVAL, "unknown mode");
+  if (o.mode == DOGIP_SOLVE_MIXED && !c.keep32) fail(DOGIP_EINVAL, "mixed mode needs keep_fp32");
+  if (!(o.tol > 0.0)) fail(DOGIP_EINVAL, "tol must be positive");
+  int scatter = o.scatter < 0 ? c.scatter : o.scatter;
+  if (scatter == DOGIP_SCATTER_COLOUR && c.scatter != DOGIP_SCATTER_COLOUR)
+    fail(DOGIP_EINVAL, "colour scatter needs a context set up with scatter = COLOUR");
+  const int chunk = std::max(1, o.check_every);
+  DeviceGuard guard(c.device);
+  vec_alloc(c.work, c.n, R);
+  SolveWork& w = c.work;
+  cudaStream_t s = c.stream;
+  cuda_check(cudaEventRecord(c.ev_in, user), "event record");
+  cuda_check(cudaStreamWaitEvent(s, c.ev_in, 0), "stream wait");
+  auto timed_out = [&]() {
+    if (o.timeout_ms <= 0) return false;
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return ms > o.timeout_ms;
+  };
+  int status = DOGIP_OK;
+  int iters = 0, outer = 0;
+  const size_t bytes = sizeof(double) * c.n * R;
+  if (!o.use_x0) cuda_check(cudaMemsetAsync(u, 0, bytes, s), "zero u");
+  if (o.mode == DOGIP_SOLVE_FP64) {
+    // PCG on the recursively updated residual; when it reports convergence the
+    // true residual b - K u is evaluated in FP64, and PCG restarts from it if
+    // the recursion drifted (at most a few restarts).
+    if (o.use_x0) launch_apply(c, u, w.q64, R, DOGIP_FP64, scatter, s, nullptr);
+    else cuda_check(cudaMemsetAsync(w.q64, 0, bytes, s), "zero q");
+    vec_residual64(w, b, w.q64, true, o.tol, s);
+    for (int restart = 0;; ++restart) {
+      read_scal(c);
+      bool all = true;
+      for (int r = 0; r < R; ++r) all = all && w.h_scal[r].odone;
+      if (all) break;
+      if (iters >= o.maxiter || restart > 8) { status = DOGIP_ENOTCONV; break; }
+      if (timed_out()) { status = DOGIP_ETIMEOUT; break; }
+      vec_init64(w, c.d_dinv64, o.tol, s);
+      read_scal(c);
+      int done_here = 0;
+      while (!w.h_flags[0]) {
+        if (iters + done_here >= o.maxiter) break;
+        if (timed_out()) break;
+        const int k = std::min(chunk, o.maxiter - iters - done_here);
+        run_chunk(c, DOGIP_FP64, scatter, u, k);
+        done_here = 0;
+        for (int r = 0; r < R; ++r) done_here = std::max(done_here, w.h_scal[r].iters);
+        if (w.h_flags[1]) break;
+      }
+      iters += done_here;
+      const bool brk = w.h_flags[1];
+      launch_apply(c, u, w.q64, R, DOGIP_FP64, scatter, s, nullptr);
+      vec_residual64(w, b, w.q64, false, o.tol, s);
+      if (brk) {
+        read_scal(c);
+        status = DOGIP_EBREAKDOWN;
+        break;
+      }
+    }
+  } else {
+    int budget = o.maxiter;
+    for (outer = 0;; ++outer) {
+      if (outer == 0 && !o.use_x0) cuda_check(cudaMemsetAsync(w.q64, 0, bytes, s), "zero q");
+      else launch_apply(c, u, w.q64, R, DOGIP_FP64, scatter, s, nullptr);
+      vec_residual64(w, b, w.q64, outer == 0, o.tol, s);
+      read_scal(c);
+      bool all = true;
+      for (int r = 0; r < R; ++r) all = all && w.h_scal[r].odone;
+      if (all) break;
+      if (outer >= o.max_outer) { status = DOGIP_ENOTCONV; break; }
+      if (budget <= 0) { status = DOGIP_ENOTCONV; break; }
+      if (timed_out()) { status = DOGIP_ETIMEOUT; break; }
+      vec_inner_init32(w, c.d_dinv32, o.inner_tol, s);
+      read_scal(c);
+      int inner = 0;
+      const int lim = std::min(o.inner_maxiter, budget);
+      while (!w.h_flags[0] && inner < lim) {
+        if (timed_out()) break;
+        const int k = std::min(chunk, lim - inner);
+        run_chunk(c, DOGIP_FP32, scatter, nullptr, k);
+        inner = 0;
+        for (int r = 0; r < R; ++r) inner = std::max(inner, w.h_scal[r].iters);
+        if (w.h_flags[1]) break;
+      }
+      iters += inner;
+      budget -= inner;
+      if (w.h_flags[1] && inner == 0) { status = DOGIP_EBREAKDOWN; break; }
+      vec_correct(w, u, s);
+    }
+  }
+  double worst = 0.0;
+  for (int r = 0; r < R; ++r) {
+    worst = std::max(worst, w.h_scal[r].rel);
+    if (rel_out) rel_out[r] = w.h_scal[r].rel;
+  }
+  if (status == DOGIP_OK && worst > o.tol) status = DOGIP_ENOTCONV;
+  cuda_check(cudaEventRecord(c.ev_out, s), "event record");
+  cuda_check(cudaStreamWaitEvent(user, c.ev_out, 0), "stream wait");
+  if (info) {
+    info->status = status;
+    info->iterations = iters;
+    info->outer = outer;
+    info->rel_residual = worst;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return status;
+}
+
+template <typename F>
+int guarded(F&& f) {
+  try {
+    return f();
+  } catch (const Failure& e) {
+    g_last_error = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return DOGIP_ENOMEM;
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    return DOGIP_EINVAL;
+  }
+}
+
+}  // namespace
+}  // namespace dogip
+
+using dogip::Ctx;
+using dogip::fail;
+using dogip::guarded;
+
+extern "C" {
+
+int dogip_version(void) { return 100; }
+
+const char* dogip_last_error(void) { return dogip::g_last_error.c_str(); }
+
+int dogip_opts_default(dogip_opts* o) {
+  if (!o) return DOGIP_EINVAL;
+  o->dirichlet = -1;
+  o->scatter = DOGIP_SCATTER_ATOMIC;
+  o->keep_fp32 = 1;
+  o->device = -1;
+  return DOGIP_OK;
+}
+
+int dogip_solve_opts_default(dogip_solve_opts* o) {
+  if (!o) return DOGIP_EINVAL;
+  o->mode = DOGIP_SOLVE_FP64;
+  o->tol = 1e-8;
+  o->maxiter = 100000;
+  o->inner_tol = 1e-4;
+  o->inner_maxiter = 100000;
+  o->max_outer = 30;
+  o->scatter = -1;
+  o->check_every = 16;
+  o->use_x0 = 0;
+  o->timeout_ms = 0.0;
+  return DOGIP_OK;
+}
+
+int dogip_setup(const dogip_mesh* m, int p, int form, int coef_kind, const double* coef,
+                const dogip_opts* o, dogip_ctx** out) {
+  return guarded([&] {
+    if (!out) fail(DOGIP_EINVAL, "out is required");
+    *out = nullptr;
+    *out = dogip::setup(m, p, form, coef_kind, coef, o);
+    return DOGIP_OK;
+  });
+}
+
+void dogip_destroy(dogip_ctx* ctx) { dogip::free_ctx(ctx); }
+
+int dogip_set_coef(dogip_ctx* ctx, int coef_kind, const double* coef, void* stream) {
+  return guarded([&] {
+    if (!ctx) fail(DOGIP_EINVAL, "ctx is required");
+    dogip::set_coef(*ctx, coef_kind, coef, (cudaStream_t)stream);
+    return DOGIP_OK;
+  });
+}
+
+int dogip_get_info(const dogip_ctx* c, dogip_info* i) {
+  return guarded([&] {
+    if (!c || !i) fail(DOGIP_EINVAL, "ctx and info are required");
+    i->dim = c->d;
+    i->p = c->p;
+    i->form = c->form;
+    i->coef_kind = c->coef_kind;
+    i->dirichlet = c->dirichlet;
+    i->scatter = c->scatter;
+    i->n_cells = c->E;
+    i->n_dofs = c->n;
+    i->n_boundary = c->nbnd;
+    i->v_loc = c->VT;
+    i->w_loc = c->WT;
+    i->n_sym = c->NS;
+    i->n_colours = c->ncolours;
+    i->nnz_b = c->nnzb;
+    i->nnz_pm1_b = c->nnzb1;
+    i->bytes_ahat_fp64 = (int64_t)c->E * c->WT * c->NS * 8;
+    i->bytes_ahat_fp32 = (int64_t)c->E * c->WT * c->NS * 4;
+    i->bytes_conn = (int64_t)c->E * c->VT * 4;
+    return DOGIP_OK;
+  });
+}
+
+int64_t dogip_ndofs(const dogip_ctx* c) { return c ? c->n : -1; }
+
+int dogip_get_dofmap(const dogip_ctx* c, int32_t* out) {
+  return guarded([&] {
+    if (!c || !out) fail(DOGIP_EINVAL, "ctx and output are required");
+    std::memcpy(out, c->dofmap.data(), sizeof(int32_t) * c->dofmap.size());
+    return DOGIP_OK;
+  });
+}
+
+int dogip_get_colouring(const dogip_ctx* c, int32_t* out, int* ncol) {
+  return guarded([&] {
+    if (!c) fail(DOGIP_EINVAL, "ctx is required");
+    if (out) std::memcpy(out, c->colour.data(), sizeof(int32_t) * c->colour.size());
+    if (ncol) *ncol = c->ncolours;
+    return DOGIP_OK;
+  });
+}
+
+int dogip_get_boundary(const dogip_ctx* c, uint8_t* out) {
+  return guarded([&] {
+    if (!c || !out) fail(DOGIP_EINVAL, "ctx and output are required");
+    std::memcpy(out, c->bmask.data(), c->bmask.size());
+    return DOGIP_OK;
+  });
+}
+
+int dogip_get_ahat(const dogip_ctx* c, double* out, void* stream) {
+  return guarded([&] {
+    if (!c || !out) fail(DOGIP_EINVAL, "ctx and output are required");
+    dogip::DeviceGuard g(c->device);
+    dogip::launch_export_ahat(*c, out, (cudaStream_t)stream);
+    return DOGIP_OK;
+  });
+}
+
+int dogip_get_diag(const dogip_ctx* c, double* out, void* stream) {
+  return guarded([&] {
+    if (!c || !out) fail(DOGIP_EINVAL, "ctx and output are required");
+    dogip::DeviceGuard g(c->device);
+    dogip::cuda_check(cudaMemcpyAsync(out, c->d_diag, sizeof(double) * c->n,
+                                      cudaMemcpyDeviceToDevice, (cudaStream_t)stream),
+                      "diag copy");
+    return DOGIP_OK;
+  });
+}
+
+int dogip_get_tables(int dim, int p, int form, double* bhat, double* what, int* sizes) {
+  return guarded([&] {
+    int NB, W, V;
+    long long nnz, nnz1;
+    if (!dogip::table_info(dim, p, form, &NB, &W, &V, &nnz, &nnz1))
+      fail(DOGIP_EUNSUPPORTED, "no compiled table for this (dim, p, form)");
+    if (sizes) {
+      sizes[0] = NB;
+      sizes[1] = W;
+      sizes[2] = V;
+    }
+    dogip::table_copy(dim, p, form, bhat, what, nullptr);
+    return DOGIP_OK;
+  });
+}
+
+int dogip_apply(dogip_ctx* c, const void* u, void* y, int nrhs, int prec, int scatter,
+                void* stream) {
+  return guarded([&] {
+    if (!c || !u || !y) fail(DOGIP_EINVAL, "ctx, u and y are required");
+    if (nrhs < 1) fail(DOGIP_EINVAL, "nrhs must be >= 1");
+    if (prec != DOGIP_FP64 && prec != DOGIP_FP32) fail(DOGIP_EINVAL, "unknown precision");
+    if (prec == DOGIP_FP32 && !c->keep32) fail(DOGIP_EINVAL, "context has no FP32 copy");
+    if (scatter < 0) scatter = c->scatter;
+    if (scatter != DOGIP_SCATTER_ATOMIC && scatter != DOGIP_SCATTER_COLOUR)
+      fail(DOGIP_EINVAL, "unknown scatter");
+    if (scatter == DOGIP_SCATTER_COLOUR && c->scatter != DOGIP_SCATTER_COLOUR)
+      fail(DOGIP_EINVAL, "colour scatter needs a context set up with scatter = COLOUR");
+    dogip::DeviceGuard g(c->device);
+    dogip::launch_apply(*c, u, y, nrhs, prec, scatter, (cudaStream_t)stream, nullptr);
+    return DOGIP_OK;
+  });
+}
+
+int dogip_load(dogip_ctx* c, const double* f, double* b, void* stream) {
+  return guarded([&] {
+    if (!c || !b) fail(DOGIP_EINVAL, "ctx and b are required");
+    dogip::DeviceGuard g(c->device);
+    dogip::launch_load(*c, f, b, (cudaStream_t)stream);
+    return DOGIP_OK;
+  });
+}
+
+int dogip_solve(dogip_ctx* c, const double* b, double* u, int nrhs, const dogip_solve_opts* o,
+                dogip_solve_info* info, double* rel, void* stream) {
+  return guarded([&] {
+    if (!c) fail(DOGIP_EINVAL, "ctx is required");
+    return dogip::solve(*c, b, u, nrhs, o, info, rel, (cudaStream_t)stream);
+  });
+}
+
+int dogip_solve_host(dogip_ctx* c, const double* bh, double* uh, int nrhs,
+                     const dogip_solve_opts* o, dogip_solve_info* info, double* rel,
+                     void* stream) {
+  return guarded([&] {
+    if (!c || !bh || !uh) fail(DOGIP_EINVAL, "ctx, b and u are required");
+    if (!dogip::r_ok(nrhs)) fail(DOGIP_EINVAL, "nrhs must be 1, 2, 4, 8, 16 or 32 for solves");
+    dogip::DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = sizeof(double) * c->n * nrhs;
+    double *db = nullptr, *du = nullptr;
+    dogip::cuda_check(cudaMallocAsync((void**)&db, bytes, s), "staging allocation");
+    if (cudaMallocAsync((void**)&du, bytes, s) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFreeAsync(db, s);
+      fail(DOGIP_ENOMEM, "staging allocation");
+    }
+    int st = DOGIP_OK;
+    try {
+      dogip::cuda_check(cudaMemcpyAsync(db, bh, bytes, cudaMemcpyHostToDevice, s), "upload b");
+      if (o && o->use_x0)
+        dogip::cuda_check(cudaMemcpyAsync(du, uh, bytes, cudaMemcpyHostToDevice, s), "upload x0");
+      st = dogip::solve(*c, db, du, nrhs, o, info, rel, s);
+      dogip::cuda_check(cudaMemcpyAsync(uh, du, bytes, cudaMemcpyDeviceToHost, s), "download u");
+    } catch (...) {
+      cudaFreeAsync(db, s);
+      cudaFreeAsync(du, s);
+      throw;
+    }
+    dogip::cuda_check(cudaFreeAsync(db, s), "staging free");
+    dogip::cuda_check(cudaFreeAsync(du, s), "staging free");
+    dogip::cuda_check(cudaStreamSynchronize(s), "solve_host sync");
+    return st;
+  });
+}
+
+int dogip_grad_coef(dogip_ctx* c, const double* u, const double* lam, double* dA, void* stream) {
+  return guarded([&] {
+    if (!c || !u || !lam || !dA) fail(DOGIP_EINVAL, "ctx, u, lam and dA are required");
+    dogip::DeviceGuard g(c->device);
+    dogip::launch_grad(*c, u, lam, dA, (cudaStream_t)stream);
+    return DOGIP_OK;
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,141 @@
+// Internal state of a DoGIP context and the launch interface between the host
+// driver (host.cpp) and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "dogip.h"
+
+namespace dogip {
+
+// conn entry: bits 0..29 global dof id, bit 31 = dof on a Dirichlet boundary
+// (gather reads 0 there, scatter skips it).
+constexpr uint32_t kBndBit = 0x80000000u;
+constexpr uint32_t kIdMask = 0x3FFFFFFFu;
+constexpr int kTile = 32;  // elements per AoSoA tile (one warp)
+
+// Validation flags raised by the setup kernel.
+constexpr int kErrGeometry = 1;   // |det R_T| not positive or not finite
+constexpr int kErrNonFinite = 2;  // coefficient not finite
+constexpr int kErrSymmetry = 4;   // tensor not symmetric
+constexpr int kErrNotPos = 8;     // coefficient not positive (definite)
+
+// Per-rhs scalars of a CG iteration (device memory).
+struct CGScal {
+  double rho, pq, alpha, beta, rr, r0, bb, s, rel, tol, otol;
+  int done, iters, brk, odone;
+};
+
+struct SolveWork {
+  int R = 0;
+  int64_t n = 0;
+  // FP64 vectors [n x R]
+  double *x64 = nullptr, *r64 = nullptr, *p64 = nullptr, *q64 = nullptr;
+  // FP32 vectors [n x R]
+  float *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+  // reductions
+  double* partial = nullptr;     // [kMaxRedBlocks x 32 x 2]
+  unsigned int* counter = nullptr;
+  CGScal* scal = nullptr;        // [R]
+  int* flags = nullptr;          // [0] all_done, [1] any_breakdown
+  int* h_flags = nullptr;        // pinned host mirror of flags + iters
+  CGScal* h_scal = nullptr;      // pinned host mirror of scal
+  // graph cache of the inner iteration chunk
+  cudaGraphExec_t graph = nullptr;
+  const void* graph_key[4] = {nullptr, nullptr, nullptr, nullptr};
+  int graph_chunk = 0, graph_prec = -1, graph_scatter = -1;
+};
+
+constexpr int kMaxRedBlocks = 1024;
+constexpr int kRedThreads = 256;
+
+}  // namespace dogip
+
+// The opaque context of the C ABI.
+struct dogip_ctx {
+  int d = 0, p = 0, form = 0, coef_kind = 0;
+  int VT = 0, WT = 0, NB = 0, NS = 0;
+  bool dirichlet = false, keep32 = true;
+  int scatter = DOGIP_SCATTER_ATOMIC;
+  int device = 0;
+  int64_t E = 0, Epad = 0, n = 0, nv = 0, nbnd = 0;
+  int ncolours = 0;
+  long long nnzb = 0, nnzb1 = 0;
+  std::vector<int64_t> colour_start;  // processing-order ranges [ncolours + 1]
+  std::vector<int32_t> dofmap;        // caller order [E x VT]
+  std::vector<int32_t> colour;        // caller order [E]
+  std::vector<uint8_t> bmask;         // [n]
+  std::vector<int64_t> perm;          // processing position -> caller cell
+  // device memory (processing order unless noted)
+  double* d_coords = nullptr;  // [nv x d]
+  int32_t* d_cells = nullptr;  // [E x (d+1)]
+  int64_t* d_perm = nullptr;   // [E]
+  uint32_t* d_conn = nullptr;  // AoSoA [Epad/32][VT][32]
+  double* d_A64 = nullptr;     // AoSoA [Epad/32][WT*NS][32]
+  float* d_A32 = nullptr;
+  double* d_geo = nullptr;     // [E][d*d + 1]: R^-1 row-major, |det R|
+  double* d_diag = nullptr;    // [n]
+  double* d_dinv64 = nullptr;  // [n]
+  float* d_dinv32 = nullptr;   // [n]
+  int32_t* d_bnd = nullptr;    // [nbnd] boundary dof list
+  double* d_coef = nullptr;    // caller order copy of the setup coefficients
+  int* d_err = nullptr;        // validation flags
+  dogip::SolveWork work;
+  cudaStream_t stream = nullptr;  // private stream for graph-captured solves
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+};
+
+namespace dogip {
+
+using Ctx = ::dogip_ctx;
+
+// Thrown inside the library, turned into a status code at the ABI.
+struct Failure {
+  int code;
+  std::string msg;
+};
+
+[[noreturn]] void fail(int code, const std::string& msg);
+void cuda_check(cudaError_t e, const char* what);
+
+// ---- kernel launchers (implemented in the .cu translation units) ----------
+// All take the processing-order state of ctx and enqueue on `s`.
+void launch_ahat(Ctx& c, const double* coef, int coef_kind, cudaStream_t s);
+void launch_apply(Ctx& c, const void* u, void* y, int R, int prec, int scatter,
+                  cudaStream_t s, const int* skip);
+void launch_load(Ctx& c, const double* f, double* b, cudaStream_t s);
+void launch_grad(Ctx& c, const double* u, const double* lam, double* dA,
+                 cudaStream_t s);
+void launch_export_ahat(const Ctx& c, double* out, cudaStream_t s);
+void launch_dirichlet_copy(const Ctx& c, const void* u, void* y, int R, int prec,
+                           cudaStream_t s, const int* skip);
+void launch_diag_finish(Ctx& c, cudaStream_t s);
+
+// Static table access for the host (dogip_get_tables, info).
+bool table_info(int d, int p, int form, int* NB, int* W, int* V, long long* nnz,
+                long long* nnz1);
+bool table_copy(int d, int p, int form, double* B, double* w, double* iv);
+
+// ---- solver vector kernels (vec.cu) -----------------------------------------
+void vec_alloc(SolveWork& w, int64_t n, int R);
+void vec_free(SolveWork& w);
+// r64 <- b - Kx (FP64) with per-rhs ||r||^2 (and ||b||^2 when first); sets
+// rel = ||r||/||b||, s = ||r||, odone = rel <= otol.
+void vec_residual64(SolveWork& w, const double* b, const double* Kx, bool first,
+                    double otol, cudaStream_t st);
+// Inner FP32 start: r32 = r64 / s (0 for finished rhs), x32 = 0, p = Dinv r,
+// rho = r.z, r0 = ||r32||, tol = inner_tol.
+void vec_inner_init32(SolveWork& w, const float* dinv, double inner_tol, cudaStream_t st);
+// FP64 PCG start from r64 = b - K x0: p = Dinv r, rho, r0 = ||b||, tol.
+void vec_init64(SolveWork& w, const double* dinv, double tol, cudaStream_t st);
+// The CG iteration after q = K p: alpha = rho / p.q, x += alpha p, r -= alpha q,
+// rho' = r.Dinv r, beta, p = Dinv r + beta p; per-rhs convergence test.
+void vec_cg_step(SolveWork& w, int prec, double* x64, const void* dinv, cudaStream_t st);
+// x64 += s * x32 for rhs still refining.
+void vec_correct(SolveWork& w, double* x64, cudaStream_t st);
+
+}  // namespace dogip

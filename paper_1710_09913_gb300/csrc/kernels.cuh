@@ -1,0 +1,506 @@
+// Device code of the DoGIP element kernels, templated on (dimension D, order P,
+// form FORM).  The reference tables B (interpolation of P_P values or reference
+// gradients onto the W nodes) are compile-time constants from tables_gen.h, so
+// every zero entry of B costs nothing and every +-1 entry costs an add -- the
+// multiplication count of eq. comp_eff.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <type_traits>
+#include <utility>
+
+#include "internal.h"
+#include "tables_gen.h"
+
+namespace dogip {
+
+template <typename F, int... I>
+__host__ __device__ __forceinline__ void static_for_impl(F&& f, std::integer_sequence<int, I...>) {
+  (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, typename F>
+__host__ __device__ __forceinline__ void static_for(F&& f) {
+  static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+template <int D, int FORM>
+struct NSym {
+  static constexpr int value = FORM == DOGIP_ELLIPTIC ? D * (D + 1) / 2 : 1;
+};
+
+// Packed index of the symmetric pair (r, s): (00,01,11) in 2D, (00,01,02,11,12,22) in 3D.
+__host__ __device__ constexpr int sym_idx(int D, int r, int s) {
+  return r <= s ? r * (2 * D - r - 1) / 2 + s : s * (2 * D - s - 1) / 2 + r;
+}
+
+// First l with B[r][j][l] != 0 (row start), and whether (j, r) is the first
+// contribution to column l in the order the kernels visit (j outer, r inner).
+template <class TB>
+__host__ __device__ constexpr int row_first(int r, int j) {
+  for (int l = 0; l < TB::V; ++l)
+    if (TB::B[r][j][l] != 0.0) return l;
+  return -1;
+}
+template <class TB>
+__host__ __device__ constexpr bool col_first(int j, int r, int l) {
+  for (int jj = 0; jj < TB::W; ++jj)
+    for (int rr = 0; rr < TB::NB; ++rr) {
+      if (TB::B[rr][jj][l] != 0.0) return jj == j && rr == r;
+    }
+  return false;
+}
+template <class TB>
+__host__ __device__ constexpr bool col_empty(int l) {
+  for (int jj = 0; jj < TB::W; ++jj)
+    for (int rr = 0; rr < TB::NB; ++rr)
+      if (TB::B[rr][jj][l] != 0.0) return false;
+  return true;
+}
+
+// g_r = sum_l B[r][J][l] u_l for one W node J (interpolation, step "B u_T").
+template <class TB, int J, typename T>
+__device__ __forceinline__ void interp(const T (&ul)[TB::V], T (&g)[TB::NB]) {
+  static_for<TB::NB>([&](auto rc) {
+    constexpr int r = decltype(rc)::value;
+    constexpr int L0 = row_first<TB>(r, J);
+    if constexpr (L0 < 0) {
+      g[r] = T(0);
+    } else {
+      static_for<TB::V>([&](auto lc) {
+        constexpr int l = decltype(lc)::value;
+        constexpr double b = TB::B[r][J][l];
+        if constexpr (l == L0) {
+          if constexpr (b == 1.0) g[r] = ul[l];
+          else if constexpr (b == -1.0) g[r] = -ul[l];
+          else g[r] = T(b) * ul[l];
+        } else if constexpr (l > L0 && b != 0.0) {
+          if constexpr (b == 1.0) g[r] += ul[l];
+          else if constexpr (b == -1.0) g[r] -= ul[l];
+          else g[r] = fma(T(b), ul[l], g[r]);
+        }
+      });
+    }
+  });
+}
+
+// Y_l += sum_r B[r][J][l] h_r for one W node J (projection back, step "B^* h").
+template <class TB, int J, typename T>
+__device__ __forceinline__ void project(const T (&h)[TB::NB], T (&Y)[TB::V]) {
+  static_for<TB::NB>([&](auto rc) {
+    constexpr int r = decltype(rc)::value;
+    static_for<TB::V>([&](auto lc) {
+      constexpr int l = decltype(lc)::value;
+      constexpr double b = TB::B[r][J][l];
+      if constexpr (b != 0.0) {
+        if constexpr (col_first<TB>(J, r, l)) {
+          if constexpr (b == 1.0) Y[l] = h[r];
+          else if constexpr (b == -1.0) Y[l] = -h[r];
+          else Y[l] = T(b) * h[r];
+        } else {
+          if constexpr (b == 1.0) Y[l] += h[r];
+          else if constexpr (b == -1.0) Y[l] -= h[r];
+          else Y[l] = fma(T(b), h[r], Y[l]);
+        }
+      }
+    });
+  });
+}
+
+// h = A_j g with A_j the packed symmetric block (elliptic) or the scalar (projection).
+template <int D, int FORM, typename T>
+__device__ __forceinline__ void block_mul(const T* a, const T* g, T* h) {
+  if constexpr (FORM == DOGIP_PROJECTION) {
+    h[0] = a[0] * g[0];
+  } else {
+    static_for<D>([&](auto rc) {
+      constexpr int r = decltype(rc)::value;
+      h[r] = a[sym_idx(D, r, 0)] * g[0];
+      static_for<D - 1>([&](auto sc) {
+        constexpr int s = decltype(sc)::value + 1;
+        h[r] = fma(a[sym_idx(D, r, s)], g[s], h[r]);
+      });
+    });
+  }
+}
+
+template <typename T>
+struct ApplyArgs {
+  const T* A;            // AoSoA [Epad/32][W*NS][32]
+  const uint32_t* conn;  // AoSoA [Epad/32][V][32]
+  const T* u;            // [n x R]
+  T* y;                  // [n x R]
+  int64_t e0, e1;        // processing-order element range
+  int R;
+  const int* skip;       // device flag: return at once when set (may be null)
+};
+
+// Algorithm 1 for one (element, rhs) per thread: gather u_T, then per W node
+// interpolate (B u_T), multiply by A_T,j, project back (B^*), and finally
+// scatter-add Y into y.  The W-node loop is fused, so B u_T is never stored.
+template <int D, int P, int FORM, typename T, bool ATOMIC, bool MULTI>
+__global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> a) {
+  using TB = dogip_tab::Tab<D, P, FORM>;
+  constexpr int V = TB::V, W = TB::W, NB = TB::NB, NS = NSym<D, FORM>::value;
+  if (a.skip != nullptr && *a.skip) return;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t e;
+  int r = 0;
+  if constexpr (MULTI) {
+    const int64_t q = t / a.R;
+    e = a.e0 + q;
+    r = (int)(t - q * a.R);
+  } else {
+    e = a.e0 + t;
+  }
+  if (e >= a.e1) return;
+  const int64_t tile = e >> 5;
+  const int lane = (int)(e & 31);
+  const uint32_t* ct = a.conn + tile * (V * kTile) + lane;
+  const T* At = a.A + tile * ((int64_t)W * NS * kTile) + lane;
+  const int R = MULTI ? a.R : 1;
+
+  uint32_t c[V];
+  T ul[V], Y[V];
+  static_for<V>([&](auto lc) {
+    constexpr int l = decltype(lc)::value;
+    c[l] = __ldg(ct + l * kTile);
+  });
+  static_for<V>([&](auto lc) {
+    constexpr int l = decltype(lc)::value;
+    ul[l] = (c[l] & kBndBit) ? T(0) : __ldg(a.u + (int64_t)(c[l] & kIdMask) * R + r);
+    if constexpr (col_empty<TB>(l)) Y[l] = T(0);
+  });
+  static_for<W>([&](auto jc) {
+    constexpr int j = decltype(jc)::value;
+    T g[NB], h[NB], aj[NS];
+    static_for<NS>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      aj[k] = __ldg(At + (j * NS + k) * kTile);
+    });
+    interp<TB, j>(ul, g);
+    block_mul<D, FORM>(aj, g, h);
+    project<TB, j>(h, Y);
+  });
+  static_for<V>([&](auto lc) {
+    constexpr int l = decltype(lc)::value;
+    if (!(c[l] & kBndBit)) {
+      T* dst = a.y + (int64_t)(c[l] & kIdMask) * R + r;
+      if constexpr (ATOMIC) atomicAdd(dst, Y[l]);
+      else *dst += Y[l];
+    }
+  });
+}
+
+// ------------------------------------------------------------------ setup
+
+struct AhatArgs {
+  const double* coords;   // [nv x D]
+  const int32_t* cells;   // [E x (D+1)] processing order
+  const int64_t* perm;    // processing position -> caller cell
+  const double* coef;     // caller order
+  int coef_kind;
+  const uint32_t* conn;
+  double* A64;
+  float* A32;             // may be null
+  double* geo;            // [E][D*D+1]
+  double* diag;           // [n], accumulated (must be zeroed)
+  int* err;
+  int64_t E;
+};
+
+template <int D>
+__device__ __forceinline__ double det_inv(const double (&R)[D][D], double (&Ri)[D][D]) {
+  if constexpr (D == 2) {
+    const double det = R[0][0] * R[1][1] - R[0][1] * R[1][0];
+    const double id = 1.0 / det;
+    Ri[0][0] = R[1][1] * id;
+    Ri[0][1] = -R[0][1] * id;
+    Ri[1][0] = -R[1][0] * id;
+    Ri[1][1] = R[0][0] * id;
+    return det;
+  } else {
+    const double c00 = R[1][1] * R[2][2] - R[1][2] * R[2][1];
+    const double c01 = R[1][2] * R[2][0] - R[1][0] * R[2][2];
+    const double c02 = R[1][0] * R[2][1] - R[1][1] * R[2][0];
+    const double det = R[0][0] * c00 + R[0][1] * c01 + R[0][2] * c02;
+    const double id = 1.0 / det;
+    Ri[0][0] = c00 * id;
+    Ri[1][0] = c01 * id;
+    Ri[2][0] = c02 * id;
+    Ri[0][1] = (R[0][2] * R[2][1] - R[0][1] * R[2][2]) * id;
+    Ri[1][1] = (R[0][0] * R[2][2] - R[0][2] * R[2][0]) * id;
+    Ri[2][1] = (R[0][1] * R[2][0] - R[0][0] * R[2][1]) * id;
+    Ri[0][2] = (R[0][1] * R[1][2] - R[0][2] * R[1][1]) * id;
+    Ri[1][2] = (R[0][2] * R[1][0] - R[0][0] * R[1][2]) * id;
+    Ri[2][2] = (R[0][0] * R[1][1] - R[0][1] * R[1][0]) * id;
+    return det;
+  }
+}
+
+// Step a8: A_T,j = |det R_T| w_j R_T^-1 M_T R_T^-T (elliptic) or m_T |det R_T| w_j
+// (projection), written in FP64 (and FP32), plus the element geometry and the
+// Jacobi diagonal sum_j B_{.jl}^T A_T,j B_{.jl} scattered into diag.
+template <int D, int P, int FORM>
+__global__ void __launch_bounds__(128) k_ahat(AhatArgs a) {
+  using TB = dogip_tab::Tab<D, P, FORM>;
+  constexpr int V = TB::V, W = TB::W, NB = TB::NB, NS = NSym<D, FORM>::value;
+  const int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (pos >= a.E) return;
+  double X[D + 1][D];
+  static_for<D + 1>([&](auto ic) {
+    constexpr int i = decltype(ic)::value;
+    const int64_t v = a.cells[pos * (D + 1) + i];
+    static_for<D>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      X[i][k] = a.coords[v * D + k];
+    });
+  });
+  double R[D][D], Ri[D][D];
+  static_for<D>([&](auto ic) {
+    constexpr int i = decltype(ic)::value;
+    static_for<D>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      R[i][k] = X[k + 1][i] - X[0][i];  // column k = v_{k+1} - v_0
+    });
+  });
+  const double det = det_inv<D>(R, Ri);
+  const double vol = fabs(det);
+  int err = 0;
+  if (!(vol > 0.0) || !isfinite(det)) err |= kErrGeometry;
+  const int64_t user = a.perm[pos];
+  double K[NS];
+  if constexpr (FORM == DOGIP_PROJECTION) {
+    const double m = a.coef[user];
+    if (!isfinite(m)) err |= kErrNonFinite;
+    if (!(m > 0.0)) err |= kErrNotPos;
+    K[0] = m * vol;
+  } else {
+    double M[D][D];
+    if (a.coef_kind == DOGIP_COEF_ELEM_SCALAR) {
+      const double m = a.coef[user];
+      if (!isfinite(m)) err |= kErrNonFinite;
+      if (!(m > 0.0)) err |= kErrNotPos;
+      static_for<D>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        static_for<D>([&](auto kc) {
+          constexpr int k = decltype(kc)::value;
+          M[i][k] = i == k ? m : 0.0;
+        });
+      });
+    } else {
+      const double* mp = a.coef + user * D * D;
+      double mx = 0.0;
+      static_for<D>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        static_for<D>([&](auto kc) {
+          constexpr int k = decltype(kc)::value;
+          M[i][k] = mp[i * D + k];
+          if (!isfinite(M[i][k])) err |= kErrNonFinite;
+          mx = fmax(mx, fabs(M[i][k]));
+        });
+      });
+      static_for<D>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        static_for<D>([&](auto kc) {
+          constexpr int k = decltype(kc)::value;
+          if (fabs(M[i][k] - M[k][i]) > 1e-14 * mx) err |= kErrSymmetry;
+        });
+      });
+      // positive definiteness by leading principal minors
+      if (!(M[0][0] > 0.0)) err |= kErrNotPos;
+      const double m2 = M[0][0] * M[1][1] - M[0][1] * M[1][0];
+      if (!(m2 > 0.0)) err |= kErrNotPos;
+      if constexpr (D == 3) {
+        const double m3 = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+                          M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                          M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+        if (!(m3 > 0.0)) err |= kErrNotPos;
+      }
+    }
+    // K = vol * R^-1 M R^-T, symmetric part, packed
+    static_for<D>([&](auto rc) {
+      constexpr int r = decltype(rc)::value;
+      static_for<D>([&](auto sc) {
+        constexpr int s = decltype(sc)::value;
+        if constexpr (r <= s) {
+          double acc = 0.0;
+          static_for<D>([&](auto pc) {
+            constexpr int p = decltype(pc)::value;
+            static_for<D>([&](auto qc) {
+              constexpr int q = decltype(qc)::value;
+              acc += Ri[r][p] * 0.5 * (M[p][q] + M[q][p]) * Ri[s][q];
+            });
+          });
+          K[sym_idx(D, r, s)] = vol * acc;
+        }
+      });
+    });
+  }
+  if (err) atomicOr(a.err, err);
+  const int64_t tile = pos >> 5;
+  const int lane = (int)(pos & 31);
+  double* At = a.A64 + tile * ((int64_t)W * NS * kTile) + lane;
+  float* At32 = a.A32 ? a.A32 + tile * ((int64_t)W * NS * kTile) + lane : nullptr;
+  static_for<W>([&](auto jc) {
+    constexpr int j = decltype(jc)::value;
+    static_for<NS>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      constexpr double wj = TB::w[j];
+      const double v = wj * K[k];
+      At[(j * NS + k) * kTile] = v;
+      if (At32) At32[(j * NS + k) * kTile] = (float)v;
+    });
+  });
+  double* g = a.geo + pos * (D * D + 1);
+  static_for<D>([&](auto ic) {
+    constexpr int i = decltype(ic)::value;
+    static_for<D>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      g[i * D + k] = Ri[i][k];
+    });
+  });
+  g[D * D] = vol;
+  // Jacobi diagonal contributions: sum_j w_j B_{.jl}^T K B_{.jl}
+  const uint32_t* ct = a.conn + tile * (V * kTile) + lane;
+  static_for<V>([&](auto lc) {
+    constexpr int l = decltype(lc)::value;
+    const uint32_t cl = ct[l * kTile];
+    if (!(cl & kBndBit)) {
+      double acc = 0.0;
+      static_for<W>([&](auto jc) {
+        constexpr int j = decltype(jc)::value;
+        double q = 0.0;
+        static_for<NB>([&](auto rc) {
+          constexpr int r = decltype(rc)::value;
+          static_for<NB>([&](auto sc) {
+            constexpr int s = decltype(sc)::value;
+            constexpr double br = TB::B[r][j][l], bs = TB::B[s][j][l];
+            if constexpr (br != 0.0 && bs != 0.0) q += br * bs * K[sym_idx(D, r, s)];
+          });
+        });
+        constexpr double wj = TB::w[j];
+        acc += wj * q;
+      });
+      atomicAdd(a.diag + (cl & kIdMask), acc);
+    }
+  });
+}
+
+struct LoadArgs {
+  const double* geo;
+  const int64_t* perm;
+  const double* f;  // caller order or null (f = 1)
+  const uint32_t* conn;
+  double* b;
+  int64_t E;
+};
+
+// b_l += f_T |det R_T| int_That phi_l (element-wise constant source).
+template <int D, int P, int FORM>
+__global__ void __launch_bounds__(128) k_load(LoadArgs a) {
+  using TB = dogip_tab::Tab<D, P, FORM>;
+  constexpr int V = TB::V;
+  const int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (pos >= a.E) return;
+  const double fv = (a.f ? a.f[a.perm[pos]] : 1.0) * a.geo[pos * (D * D + 1) + D * D];
+  const int64_t tile = pos >> 5;
+  const int lane = (int)(pos & 31);
+  const uint32_t* ct = a.conn + tile * (V * kTile) + lane;
+  static_for<V>([&](auto lc) {
+    constexpr int l = decltype(lc)::value;
+    const uint32_t cl = ct[l * kTile];
+    constexpr double ivl = TB::iv[l];
+    if (!(cl & kBndBit)) atomicAdd(a.b + (cl & kIdMask), fv * ivl);
+  });
+}
+
+struct GradArgs {
+  const double* geo;
+  const int64_t* perm;
+  const uint32_t* conn;
+  const double* u;
+  const double* lam;
+  double* dA;  // caller order
+  int coef_kind;
+  int64_t E;
+};
+
+// dJ/dA_T = -sum_j om_j (grad lam)(x_j) (x) (grad u)(x_j) (elliptic, physical
+// gradients R^-T B u_T) or -sum_j om_j lam(x_j) u(x_j) (projection).
+template <int D, int P, int FORM>
+__global__ void __launch_bounds__(128) k_grad(GradArgs a) {
+  using TB = dogip_tab::Tab<D, P, FORM>;
+  constexpr int V = TB::V, W = TB::W, NB = TB::NB;
+  const int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (pos >= a.E) return;
+  const int64_t tile = pos >> 5;
+  const int lane = (int)(pos & 31);
+  const uint32_t* ct = a.conn + tile * (V * kTile) + lane;
+  double uT[V], lT[V];
+  static_for<V>([&](auto lc) {
+    constexpr int l = decltype(lc)::value;
+    const uint32_t cl = ct[l * kTile];
+    const bool bnd = cl & kBndBit;
+    uT[l] = bnd ? 0.0 : a.u[cl & kIdMask];
+    lT[l] = bnd ? 0.0 : a.lam[cl & kIdMask];
+  });
+  const double* g = a.geo + pos * (D * D + 1);
+  const double vol = g[D * D];
+  double G[NB][NB];
+  static_for<NB>([&](auto pc) {
+    static_for<NB>([&](auto qc) { G[decltype(pc)::value][decltype(qc)::value] = 0.0; });
+  });
+  static_for<W>([&](auto jc) {
+    constexpr int j = decltype(jc)::value;
+    double gu[NB], gl[NB];
+    interp<TB, j>(uT, gu);
+    interp<TB, j>(lT, gl);
+    double pu[NB], pl[NB];
+    if constexpr (FORM == DOGIP_ELLIPTIC) {
+      static_for<D>([&](auto pc) {
+        constexpr int p = decltype(pc)::value;
+        pu[p] = 0.0;
+        pl[p] = 0.0;
+        static_for<D>([&](auto sc) {
+          constexpr int s = decltype(sc)::value;
+          pu[p] += g[s * D + p] * gu[s];  // (R^-T g)_p = sum_s Ri[s][p] g_s
+          pl[p] += g[s * D + p] * gl[s];
+        });
+      });
+    } else {
+      pu[0] = gu[0];
+      pl[0] = gl[0];
+    }
+    constexpr double wj = TB::w[j];
+    const double om = vol * wj;
+    static_for<NB>([&](auto pc) {
+      constexpr int p = decltype(pc)::value;
+      static_for<NB>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        G[p][q] += om * pl[p] * pu[q];
+      });
+    });
+  });
+  const int64_t user = a.perm[pos];
+  if (FORM == DOGIP_ELLIPTIC && a.coef_kind == DOGIP_COEF_ELEM_TENSOR) {
+    static_for<NB>([&](auto pc) {
+      constexpr int p = decltype(pc)::value;
+      static_for<NB>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        a.dA[user * D * D + p * D + q] = -G[p][q];
+      });
+    });
+  } else {
+    double tr = 0.0;
+    static_for<NB>([&](auto pc) { tr += G[decltype(pc)::value][decltype(pc)::value]; });
+    a.dA[user] = -tr;
+  }
+}
+
+// A_T (AoSoA, processing order) -> [E][W][NS] caller order; nsw = W * NS.
+__global__ void k_export_ahat(const double* A, const int64_t* perm, double* out, int64_t E,
+                              int nsw);
+
+}  // namespace dogip

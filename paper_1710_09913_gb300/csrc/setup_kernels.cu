@@ -1,0 +1,211 @@
+// Launchers of the setup-side element kernels (A_T precompute, load, gradient,
+// export) and of the apply dispatcher, plus host access to the static tables.
+#include <cstring>
+
+#include "kernels.cuh"
+
+namespace dogip {
+
+bool apply_d2(const Ctx&, const void*, void*, int, int, bool, int64_t, int64_t, cudaStream_t,
+              const int*);
+bool apply_d3a(const Ctx&, const void*, void*, int, int, bool, int64_t, int64_t, cudaStream_t,
+               const int*);
+bool apply_d3b(const Ctx&, const void*, void*, int, int, bool, int64_t, int64_t, cudaStream_t,
+               const int*);
+
+__global__ void k_export_ahat(const double* A, const int64_t* perm, double* out, int64_t E,
+                              int nsw) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= E * nsw) return;
+  const int64_t pos = t / nsw;
+  const int k = (int)(t - pos * nsw);
+  out[perm[pos] * nsw + k] = A[(pos >> 5) * ((int64_t)nsw * kTile) + k * kTile + (pos & 31)];
+}
+
+template <typename T>
+__global__ void k_dirichlet_copy(const T* u, T* y, const int32_t* bnd, int64_t nb, int R,
+                                 const int* skip) {
+  if (skip != nullptr && *skip) return;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nb * R) return;
+  const int64_t i = (int64_t)bnd[t / R] * R + (t % R);
+  y[i] = u[i];
+}
+
+__global__ void k_diag_finish(double* diag, double* dinv64, float* dinv32, const int32_t* bnd,
+                              int64_t nb, int64_t n) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < nb) diag[bnd[t]] = 1.0;
+}
+
+__global__ void k_diag_inv(const double* diag, double* dinv64, float* dinv32, int64_t n) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const double v = 1.0 / diag[t];
+  dinv64[t] = v;
+  dinv32[t] = (float)v;
+}
+
+namespace {
+
+template <int D, int P, int FORM>
+void ahat_one(Ctx& c, const double* coef, int coef_kind, cudaStream_t s) {
+  AhatArgs a{c.d_coords, c.d_cells, c.d_perm, coef, coef_kind, c.d_conn, c.d_A64,
+             c.keep32 ? c.d_A32 : nullptr, c.d_geo, c.d_diag, c.d_err, c.E};
+  const unsigned nb = (unsigned)((c.E + 127) / 128);
+  k_ahat<D, P, FORM><<<nb, 128, 0, s>>>(a);
+}
+
+template <int D, int P, int FORM>
+void load_one(Ctx& c, const double* f, double* b, cudaStream_t s) {
+  LoadArgs a{c.d_geo, c.d_perm, f, c.d_conn, b, c.E};
+  k_load<D, P, FORM><<<(unsigned)((c.E + 127) / 128), 128, 0, s>>>(a);
+}
+
+template <int D, int P, int FORM>
+void grad_one(Ctx& c, const double* u, const double* lam, double* dA, cudaStream_t s) {
+  GradArgs a{c.d_geo, c.d_perm, c.d_conn, u, lam, dA, c.coef_kind, c.E};
+  k_grad<D, P, FORM><<<(unsigned)((c.E + 127) / 128), 128, 0, s>>>(a);
+}
+
+template <int D, int P, int FORM>
+void info_one(int* NB, int* W, int* V, long long* nnz, long long* nnz1) {
+  using TB = dogip_tab::Tab<D, P, FORM>;
+  *NB = TB::NB;
+  *W = TB::W;
+  *V = TB::V;
+  *nnz = TB::NNZ;
+  *nnz1 = TB::NNZ1;
+}
+
+template <int D, int P, int FORM>
+void copy_one(double* B, double* w, double* iv) {
+  using TB = dogip_tab::Tab<D, P, FORM>;
+  if (B) std::memcpy(B, TB::B, sizeof(TB::B));
+  if (w) std::memcpy(w, TB::w, sizeof(TB::w));
+  if (iv) std::memcpy(iv, TB::iv, sizeof(TB::iv));
+}
+
+// Calls F<D,P,FORM>::run(args...) for the runtime triple; false if not compiled.
+#define DOGIP_DISPATCH(d, p, form, CALL)                                    \
+  do {                                                                     \
+    const int key_ = (d) * 100 + (p) * 2 + (form);                         \
+    switch (key_) {                                                        \
+      case 202: CALL(2, 1, 0); break;                                      \
+      case 203: CALL(2, 1, 1); break;                                      \
+      case 204: CALL(2, 2, 0); break;                                      \
+      case 205: CALL(2, 2, 1); break;                                      \
+      case 206: CALL(2, 3, 0); break;                                      \
+      case 207: CALL(2, 3, 1); break;                                      \
+      case 208: CALL(2, 4, 0); break;                                      \
+      case 209: CALL(2, 4, 1); break;                                      \
+      case 302: CALL(3, 1, 0); break;                                      \
+      case 303: CALL(3, 1, 1); break;                                      \
+      case 304: CALL(3, 2, 0); break;                                      \
+      case 305: CALL(3, 2, 1); break;                                      \
+      case 306: CALL(3, 3, 0); break;                                      \
+      case 307: CALL(3, 3, 1); break;                                      \
+      default: ok_ = false;                                                \
+    }                                                                      \
+  } while (0)
+
+}  // namespace
+
+void launch_ahat(Ctx& c, const double* coef, int coef_kind, cudaStream_t s) {
+  bool ok_ = true;
+  cuda_check(cudaMemsetAsync(c.d_diag, 0, sizeof(double) * c.n, s), "memset diag");
+#define CALL(D, P, F) ahat_one<D, P, F>(c, coef, coef_kind, s)
+  DOGIP_DISPATCH(c.d, c.p, c.form, CALL);
+#undef CALL
+  if (!ok_) fail(DOGIP_EUNSUPPORTED, "no compiled instance for this (dim, p, form)");
+  cuda_check(cudaGetLastError(), "ahat kernel launch");
+  launch_diag_finish(c, s);
+}
+
+void launch_diag_finish(Ctx& c, cudaStream_t s) {
+  if (c.nbnd > 0)
+    k_diag_finish<<<(unsigned)((c.nbnd + 255) / 256), 256, 0, s>>>(c.d_diag, c.d_dinv64,
+                                                                  c.d_dinv32, c.d_bnd, c.nbnd,
+                                                                  c.n);
+  k_diag_inv<<<(unsigned)((c.n + 255) / 256), 256, 0, s>>>(c.d_diag, c.d_dinv64, c.d_dinv32, c.n);
+  cuda_check(cudaGetLastError(), "diag kernels launch");
+}
+
+void launch_load(Ctx& c, const double* f, double* b, cudaStream_t s) {
+  bool ok_ = true;
+  cuda_check(cudaMemsetAsync(b, 0, sizeof(double) * c.n, s), "memset load");
+#define CALL(D, P, F) load_one<D, P, F>(c, f, b, s)
+  DOGIP_DISPATCH(c.d, c.p, c.form, CALL);
+#undef CALL
+  if (!ok_) fail(DOGIP_EUNSUPPORTED, "no compiled instance for this (dim, p, form)");
+  cuda_check(cudaGetLastError(), "load kernel launch");
+}
+
+void launch_grad(Ctx& c, const double* u, const double* lam, double* dA, cudaStream_t s) {
+  bool ok_ = true;
+#define CALL(D, P, F) grad_one<D, P, F>(c, u, lam, dA, s)
+  DOGIP_DISPATCH(c.d, c.p, c.form, CALL);
+#undef CALL
+  if (!ok_) fail(DOGIP_EUNSUPPORTED, "no compiled instance for this (dim, p, form)");
+  cuda_check(cudaGetLastError(), "gradient kernel launch");
+}
+
+void launch_export_ahat(const Ctx& c, double* out, cudaStream_t s) {
+  const int nsw = c.WT * c.NS;
+  const int64_t tot = c.E * nsw;
+  if (tot == 0) return;
+  k_export_ahat<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(c.d_A64, c.d_perm, out, c.E, nsw);
+  cuda_check(cudaGetLastError(), "export kernel launch");
+}
+
+void launch_dirichlet_copy(const Ctx& c, const void* u, void* y, int R, int prec, cudaStream_t s,
+                           const int* skip) {
+  if (c.nbnd == 0) return;
+  const int64_t tot = c.nbnd * R;
+  const unsigned nb = (unsigned)((tot + 255) / 256);
+  if (prec == DOGIP_FP64)
+    k_dirichlet_copy<double><<<nb, 256, 0, s>>>((const double*)u, (double*)y, c.d_bnd, c.nbnd, R,
+                                                 skip);
+  else
+    k_dirichlet_copy<float><<<nb, 256, 0, s>>>((const float*)u, (float*)y, c.d_bnd, c.nbnd, R,
+                                                skip);
+}
+
+void launch_apply(Ctx& c, const void* u, void* y, int R, int prec, int scatter, cudaStream_t s,
+                  const int* skip) {
+  const size_t es = prec == DOGIP_FP64 ? sizeof(double) : sizeof(float);
+  cuda_check(cudaMemsetAsync(y, 0, es * c.n * R, s), "memset y");
+  auto run = [&](bool atomic, int64_t e0, int64_t e1) {
+    bool ok;
+    if (c.d == 2) ok = apply_d2(c, u, y, R, prec, atomic, e0, e1, s, skip);
+    else if (c.p <= 2) ok = apply_d3a(c, u, y, R, prec, atomic, e0, e1, s, skip);
+    else if (c.p == 3) ok = apply_d3b(c, u, y, R, prec, atomic, e0, e1, s, skip);
+    else ok = false;
+    if (!ok) fail(DOGIP_EUNSUPPORTED, "no compiled apply instance for this (dim, p, form)");
+  };
+  if (scatter == DOGIP_SCATTER_COLOUR) {
+    for (int k = 0; k < c.ncolours; ++k) run(false, c.colour_start[k], c.colour_start[k + 1]);
+  } else {
+    run(true, 0, c.E);
+  }
+  if (c.dirichlet) launch_dirichlet_copy(c, u, y, R, prec, s, skip);
+  cuda_check(cudaGetLastError(), "apply kernel launch");
+}
+
+bool table_info(int d, int p, int form, int* NB, int* W, int* V, long long* nnz, long long* nnz1) {
+  bool ok_ = true;
+#define CALL(D, P, F) info_one<D, P, F>(NB, W, V, nnz, nnz1)
+  DOGIP_DISPATCH(d, p, form, CALL);
+#undef CALL
+  return ok_;
+}
+
+bool table_copy(int d, int p, int form, double* B, double* w, double* iv) {
+  bool ok_ = true;
+#define CALL(D, P, F) copy_one<D, P, F>(B, w, iv)
+  DOGIP_DISPATCH(d, p, form, CALL);
+#undef CALL
+  return ok_;
+}
+
+}  // namespace dogip

@@ -1,0 +1,385 @@
+// Vector kernels of the Jacobi-PCG and of the iterative refinement loop.  Every
+// reduction is fused into the kernel that produces its terms: each block writes
+// its partial sums, and the last block to finish (atomic ticket) adds the
+// partials in block order and updates the per-rhs CG scalars on the device, so
+// no host round trip is needed inside an iteration.  Vectors are dof-major
+// [n x R] with R in {1, 2, 4, 8, 16, 32}: a grid stride that is a multiple of 32
+// keeps every lane on one rhs, so warp reductions use xor shuffles over lanes
+// with equal lane % R.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "internal.h"
+
+namespace dogip {
+
+namespace {
+
+constexpr int kNV = 2;  // values reduced per rhs
+
+struct Red {
+  double* partial;
+  unsigned int* counter;
+  CGScal* scal;
+  int* flags;
+};
+
+template <int R>
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int off = 16; off >= R; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// Block-reduce acc[0..NV) per rhs, then let the last block combine all partials
+// into tot[r * NV + k] (shared) and return true in that block only.
+template <int R, int NV>
+__device__ bool grid_reduce(const Red& rd, double (&acc)[NV], double* tot) {
+  __shared__ double sm[kRedThreads / 32][R * NV];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    const double v = warp_sum<R>(acc[k]);
+    if (lane < R) sm[wid][lane * NV + k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < R * NV) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kRedThreads / 32; ++w) s += sm[w][threadIdx.x];
+    rd.partial[(size_t)blockIdx.x * 64 + threadIdx.x] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(rd.counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  if (threadIdx.x < R * NV) {
+    double s = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(rd.partial + (size_t)b * 64 + threadIdx.x);
+    tot[threadIdx.x] = s;
+  }
+  __syncthreads();
+  return true;
+}
+
+__device__ __forceinline__ void set_all_done(const Red& rd, int R) {
+  int all = 1, brk = 0;
+  for (int r = 0; r < R; ++r) {
+    all &= rd.scal[r].done;
+    brk |= rd.scal[r].brk;
+  }
+  rd.flags[0] = all;
+  rd.flags[1] = brk;
+  *rd.counter = 0u;
+}
+
+unsigned red_blocks(int64_t N) {
+  int64_t b = (N + kRedThreads - 1) / kRedThreads;
+  if (b > kMaxRedBlocks) b = kMaxRedBlocks;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+// alpha_r = rho_r / (p.q)_r
+template <typename T, int R>
+__global__ void __launch_bounds__(kRedThreads) k_pq(const T* __restrict__ p, const T* __restrict__ q,
+                                                    int64_t N, Red rd) {
+  if (rd.flags[0]) return;
+  double acc[1] = {0.0};
+  T a = T(0);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += stride)
+    a += p[i] * q[i];
+  acc[0] = (double)a;
+  __shared__ double tot[R];
+  if (!grid_reduce<R, 1>(rd, acc, tot)) return;
+  if (threadIdx.x < R) {
+    CGScal& s = rd.scal[threadIdx.x];
+    const double v = tot[threadIdx.x];
+    if (s.done) {
+      s.alpha = 0.0;
+    } else if (!(v > 0.0) || !isfinite(v)) {
+      s.brk = 1;
+      s.done = 1;
+      s.alpha = 0.0;
+    } else {
+      s.pq = v;
+      s.alpha = s.rho / v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) set_all_done(rd, R);
+}
+
+// x += alpha p, r -= alpha q, rho' = r.(Dinv r), rr = r.r, beta = rho'/rho.
+template <typename T, int R>
+__global__ void __launch_bounds__(kRedThreads) k_update(T* __restrict__ x, T* __restrict__ r,
+                                                        const T* __restrict__ p,
+                                                        const T* __restrict__ q,
+                                                        const T* __restrict__ dinv, int64_t N,
+                                                        Red rd) {
+  if (rd.flags[0]) return;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const T al = (T)rd.scal[t0 % R].alpha;
+  T a0 = T(0), a1 = T(0);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = t0; i < N; i += stride) {
+    x[i] += al * p[i];
+    const T ri = r[i] - al * q[i];
+    r[i] = ri;
+    a0 += ri * (dinv[i / R] * ri);
+    a1 += ri * ri;
+  }
+  double acc[2] = {(double)a0, (double)a1};
+  __shared__ double tot[R * 2];
+  if (!grid_reduce<R, 2>(rd, acc, tot)) return;
+  if (threadIdx.x < R) {
+    CGScal& s = rd.scal[threadIdx.x];
+    if (!s.done) {
+      const double rz = tot[threadIdx.x * 2], rr = tot[threadIdx.x * 2 + 1];
+      s.beta = rz / s.rho;
+      s.rho = rz;
+      s.rr = rr;
+      s.iters += 1;
+      if (sqrt(rr) <= s.tol * s.r0) s.done = 1;
+    } else {
+      s.beta = 0.0;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) set_all_done(rd, R);
+}
+
+// p = Dinv r + beta p
+template <typename T, int R>
+__global__ void __launch_bounds__(kRedThreads) k_pupdate(T* __restrict__ p, const T* __restrict__ r,
+                                                         const T* __restrict__ dinv, int64_t N,
+                                                         const CGScal* scal, const int* flags) {
+  if (flags[0]) return;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const CGScal& s = scal[t0 % R];
+  if (s.done) return;
+  const T be = (T)s.beta;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = t0; i < N; i += stride) p[i] = dinv[i / R] * r[i] + be * p[i];
+}
+
+// Start of a PCG run from the residual r: p = Dinv r, rho = r.p, r0.
+template <typename T, int R>
+__global__ void __launch_bounds__(kRedThreads) k_init(const T* __restrict__ r, T* __restrict__ p,
+                                                      T* __restrict__ x, const T* __restrict__ dinv,
+                                                      int64_t N, double tol, int r0_from_bb,
+                                                      int zero_x, Red rd) {
+  T a0 = T(0), a1 = T(0);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += stride) {
+    const T ri = r[i];
+    const T zi = dinv[i / R] * ri;
+    p[i] = zi;
+    if (zero_x) x[i] = T(0);
+    a0 += ri * zi;
+    a1 += ri * ri;
+  }
+  double acc[2] = {(double)a0, (double)a1};
+  __shared__ double tot[R * 2];
+  if (!grid_reduce<R, 2>(rd, acc, tot)) return;
+  if (threadIdx.x < R) {
+    CGScal& s = rd.scal[threadIdx.x];
+    s.rho = tot[threadIdx.x * 2];
+    s.rr = tot[threadIdx.x * 2 + 1];
+    s.r0 = r0_from_bb ? sqrt(s.bb) : sqrt(s.rr);
+    s.tol = tol;
+    s.alpha = s.beta = s.pq = 0.0;
+    s.iters = 0;
+    s.brk = 0;
+    s.done = (s.rr == 0.0 || sqrt(s.rr) <= tol * s.r0) ? 1 : 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) set_all_done(rd, R);
+}
+
+// r = b - Kx in FP64 with ||r||^2 (and ||b||^2).
+template <int R>
+__global__ void __launch_bounds__(kRedThreads) k_residual64(const double* __restrict__ b,
+                                                            const double* __restrict__ Kx,
+                                                            double* __restrict__ r, int64_t N,
+                                                            int first, double otol, Red rd) {
+  double a0 = 0.0, a1 = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += stride) {
+    const double bi = b[i];
+    const double ri = bi - Kx[i];
+    r[i] = ri;
+    a0 += ri * ri;
+    if (first) a1 += bi * bi;
+  }
+  double acc[2] = {a0, a1};
+  __shared__ double tot[R * 2];
+  if (!grid_reduce<R, 2>(rd, acc, tot)) return;
+  if (threadIdx.x < R) {
+    CGScal& s = rd.scal[threadIdx.x];
+    const double rr = tot[threadIdx.x * 2];
+    if (first) s.bb = tot[threadIdx.x * 2 + 1];
+    s.rr = rr;
+    s.s = sqrt(rr);
+    s.rel = s.bb > 0.0 ? sqrt(rr / s.bb) : 0.0;
+    s.otol = otol;
+    s.odone = s.rel <= otol ? 1 : 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *rd.counter = 0u;
+}
+
+template <int R>
+__global__ void k_to32(const double* __restrict__ r64, float* __restrict__ r32, float* __restrict__ x32,
+                       int64_t N, const CGScal* scal) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const CGScal& s = scal[t0 % R];
+  const double inv = (s.odone || s.s == 0.0) ? 0.0 : 1.0 / s.s;
+  for (int64_t i = t0; i < N; i += stride) {
+    r32[i] = (float)(r64[i] * inv);
+    x32[i] = 0.0f;
+  }
+}
+
+template <int R>
+__global__ void k_correct(double* __restrict__ x64, const float* __restrict__ x32, int64_t N,
+                          const CGScal* scal) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const CGScal& s = scal[t0 % R];
+  if (s.odone) return;
+  for (int64_t i = t0; i < N; i += stride) x64[i] += s.s * (double)x32[i];
+}
+
+Red red_of(SolveWork& w) { return Red{w.partial, w.counter, w.scal, w.flags}; }
+
+#define DOGIP_R_SWITCH(R, CALL) \
+  switch (R) {                  \
+    case 1: CALL(1); break;     \
+    case 2: CALL(2); break;     \
+    case 4: CALL(4); break;     \
+    case 8: CALL(8); break;     \
+    case 16: CALL(16); break;   \
+    case 32: CALL(32); break;   \
+    default: fail(DOGIP_EINVAL, "nrhs must be 1, 2, 4, 8, 16 or 32 for solves"); \
+  }
+
+}  // namespace
+
+void vec_alloc(SolveWork& w, int64_t n, int R) {
+  if (w.R == R && w.n == n) return;
+  vec_free(w);
+  const size_t N = (size_t)n * R;
+  auto dm = [&](void** p, size_t bytes) {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      fail(DOGIP_ENOMEM, "device allocation of solver workspace failed");
+    }
+  };
+  dm((void**)&w.x64, N * 8);
+  dm((void**)&w.r64, N * 8);
+  dm((void**)&w.p64, N * 8);
+  dm((void**)&w.q64, N * 8);
+  dm((void**)&w.x32, N * 4);
+  dm((void**)&w.r32, N * 4);
+  dm((void**)&w.p32, N * 4);
+  dm((void**)&w.q32, N * 4);
+  dm((void**)&w.partial, sizeof(double) * kMaxRedBlocks * 64);
+  dm((void**)&w.counter, sizeof(unsigned int) * 4);
+  dm((void**)&w.scal, sizeof(CGScal) * 32);
+  dm((void**)&w.flags, sizeof(int) * 4);
+  cuda_check(cudaMemset(w.counter, 0, sizeof(unsigned int) * 4), "memset counter");
+  cuda_check(cudaMemset(w.scal, 0, sizeof(CGScal) * 32), "memset scal");
+  cuda_check(cudaMemset(w.flags, 0, sizeof(int) * 4), "memset flags");
+  if (cudaMallocHost((void**)&w.h_flags, sizeof(int) * 4) != cudaSuccess ||
+      cudaMallocHost((void**)&w.h_scal, sizeof(CGScal) * 32) != cudaSuccess) {
+    cudaGetLastError();
+    fail(DOGIP_ENOMEM, "pinned host allocation failed");
+  }
+  w.R = R;
+  w.n = n;
+}
+
+void vec_free(SolveWork& w) {
+  if (w.graph) cudaGraphExecDestroy(w.graph);
+  w.graph = nullptr;
+  for (void* p : {(void*)w.x64, (void*)w.r64, (void*)w.p64, (void*)w.q64, (void*)w.x32,
+                  (void*)w.r32, (void*)w.p32, (void*)w.q32, (void*)w.partial, (void*)w.counter,
+                  (void*)w.scal, (void*)w.flags})
+    if (p) cudaFree(p);
+  if (w.h_flags) cudaFreeHost(w.h_flags);
+  if (w.h_scal) cudaFreeHost(w.h_scal);
+  w = SolveWork{};
+}
+
+void vec_residual64(SolveWork& w, const double* b, const double* Kx, bool first, double otol,
+                    cudaStream_t st) {
+  const int64_t N = w.n * w.R;
+  Red rd = red_of(w);
+#define CALL(RR) k_residual64<RR><<<red_blocks(N), kRedThreads, 0, st>>>(b, Kx, w.r64, N, first, otol, rd)
+  DOGIP_R_SWITCH(w.R, CALL);
+#undef CALL
+  cuda_check(cudaGetLastError(), "residual kernel");
+}
+
+void vec_inner_init32(SolveWork& w, const float* dinv, double inner_tol, cudaStream_t st) {
+  const int64_t N = w.n * w.R;
+  Red rd = red_of(w);
+#define CALL(RR)                                                                              \
+  k_to32<RR><<<red_blocks(N), kRedThreads, 0, st>>>(w.r64, w.r32, w.x32, N, w.scal);          \
+  k_init<float, RR><<<red_blocks(N), kRedThreads, 0, st>>>(w.r32, w.p32, w.x32, dinv, N,       \
+                                                            inner_tol, 0, 0, rd)
+  DOGIP_R_SWITCH(w.R, CALL);
+#undef CALL
+  cuda_check(cudaGetLastError(), "inner init kernels");
+}
+
+void vec_init64(SolveWork& w, const double* dinv, double tol, cudaStream_t st) {
+  const int64_t N = w.n * w.R;
+  Red rd = red_of(w);
+#define CALL(RR) \
+  k_init<double, RR><<<red_blocks(N), kRedThreads, 0, st>>>(w.r64, w.p64, w.x64, dinv, N, tol, 1, 0, rd)
+  DOGIP_R_SWITCH(w.R, CALL);
+#undef CALL
+  cuda_check(cudaGetLastError(), "init kernel");
+}
+
+void vec_cg_step(SolveWork& w, int prec, double* x64, const void* dinv, cudaStream_t st) {
+  const int64_t N = w.n * w.R;
+  Red rd = red_of(w);
+  const unsigned nb = red_blocks(N);
+  if (prec == DOGIP_FP64) {
+    const double* di = (const double*)dinv;
+#define CALL(RR)                                                                           \
+  k_pq<double, RR><<<nb, kRedThreads, 0, st>>>(w.p64, w.q64, N, rd);                       \
+  k_update<double, RR><<<nb, kRedThreads, 0, st>>>(x64, w.r64, w.p64, w.q64, di, N, rd);   \
+  k_pupdate<double, RR><<<nb, kRedThreads, 0, st>>>(w.p64, w.r64, di, N, w.scal, w.flags)
+    DOGIP_R_SWITCH(w.R, CALL);
+#undef CALL
+  } else {
+    const float* di = (const float*)dinv;
+#define CALL(RR)                                                                           \
+  k_pq<float, RR><<<nb, kRedThreads, 0, st>>>(w.p32, w.q32, N, rd);                        \
+  k_update<float, RR><<<nb, kRedThreads, 0, st>>>(w.x32, w.r32, w.p32, w.q32, di, N, rd);  \
+  k_pupdate<float, RR><<<nb, kRedThreads, 0, st>>>(w.p32, w.r32, di, N, w.scal, w.flags)
+    DOGIP_R_SWITCH(w.R, CALL);
+#undef CALL
+  }
+  cuda_check(cudaGetLastError(), "cg step kernels");
+}
+
+void vec_correct(SolveWork& w, double* x64, cudaStream_t st) {
+  const int64_t N = w.n * w.R;
+#define CALL(RR) k_correct<RR><<<red_blocks(N), kRedThreads, 0, st>>>(x64, w.x32, N, w.scal)
+  DOGIP_R_SWITCH(w.R, CALL);
+#undef CALL
+  cuda_check(cudaGetLastError(), "correct kernel");
+}
+
+}  // namespace dogip
