@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""DoGIP benchmark on one GB300: apply throughput inside Jacobi-PCG solves to 1e-8,
+mixed precision (FP32 inner PCG + FP64 iterative refinement) against FP64 PCG.
+
+Workload: 2D scalar elliptic problem -div(A grad u) = 1, zero Dirichlet data, on the
+unit square cut into a 512 x 512 grid of squares, 2 triangles each (524,288
+triangles), interior vertices jittered by up to 0.2 h; A is a per-element SPD 2x2
+tensor (eigenvalues lognormal(0, 1), rotation uniform in [0, pi)); P_p Lagrange
+elements for p = 1, 2, 3, 4 (263,169 / 1,050,625 / 2,362,369 / 4,198,401 dofs).
+
+One step = one pass of the whole hot path over that sweep: for every p the element
+factors A_T are recomputed from the coefficients (A_T precompute and Jacobi diagonal),
+the load of f = 1 is assembled, and K u = b is solved to a true FP64 relative residual
+of 1e-8 in mixed precision.  value = effective DoGIP apply throughput of the step:
+sum over p of n_p x (operator applies in the solve) / step time, in GDoF/s.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "DoGIP apply GDoF/s & PCG time-to-1e-8: mixed vs FP64 on 1 GB300, % roofline"
+N_GRID, JITTER, SIGMA, SEED, TOL = 512, 0.2, 1.0, 2, 1e-8
+P_LIST = (1, 2, 3, 4)
+WORKLOAD = ("2D scalar elliptic, unit square, 512x512 grid x 2 triangles (524,288 cells), "
+            "interior vertices jittered 0.2h, per-element SPD tensor A (lognormal(0,1) "
+            "eigenvalues, uniform rotation), f = 1, zero Dirichlet; P1-P4 sweep; "
+            "mixed FP32 PCG + FP64 refinement to 1e-8")
+L2_FLUSH_BYTES = 512 << 20
+
+
+def mesh_and_coef():
+    from paper_1710_09913_gb300 import inputs
+    coords, cells = inputs.lattice_mesh(2, N_GRID, JITTER, seed=SEED)
+    A = inputs.coef_tensor_lognormal(len(cells), 2, SIGMA, seed=SEED)
+    return coords, cells, A
+
+
+# ------------------------------------------------------------------ clocks
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- helpers
+
+
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ----------------------------------------------------------- oracle (CPU)
+
+
+def oracle_sample(coords, cells, A, p_list, inner_iters):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload: for
+    every p, one refinement step with `inner_iters` emulated-FP32 PCG iterations.
+    Returns (dof-applies, seconds, description)."""
+    from oracle import dogip as od
+    from oracle import solvers as osol
+    work, secs = 0, 0.0
+    for p in p_list:
+        P = od.Problem("elliptic", p, coords, cells, A)
+        b = od.load_const(2, p, coords, cells, P.conn, P.n, np.ones(len(cells)))
+        b[P.bmask] = 0.0
+        dinv = 1.0 / P.diag()
+        Ah32 = P.Ah.astype(np.float32).astype(np.float64)
+        count = [0]
+
+        def a64(v, P=P):
+            count[0] += 1
+            return P.apply(v)
+
+        def a32(v, P=P, Ah32=Ah32):
+            count[0] += 1
+            return od.apply("elliptic", P.Bh, Ah32, P.conn, v.astype(np.float64), P.bmask)
+
+        t = time.perf_counter()
+        osol.iterative_refinement(a64, a32, b, dinv, tol=TOL, inner_maxiter=inner_iters, max_outer=1)
+        secs += time.perf_counter() - t
+        work += P.n * count[0]
+    desc = (f"numpy oracle, P{p_list[0]}-P{p_list[-1]} on the full 524,288-cell mesh, one refinement "
+            f"step with {inner_iters} inner PCG iterations per p (every operator apply counted)")
+    return work, secs, desc
+
+
+def run_reference(args):
+    """--impl reference: the oracle timed on the host cores on bounded samples."""
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    coords, cells, A = mesh_and_coef()
+    for _ in range(args.warmup):
+        oracle_sample(coords, cells, A, P_LIST, 1)
+    work, secs = 0, 0.0
+    desc = ""
+    for _ in range(args.steps):
+        w, s, desc = oracle_sample(coords, cells, A, P_LIST, 1)
+        work += w
+        secs += s
+    value = work / secs / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GDoF/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64/f32 (numpy)", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "GDoF/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------- GPU arm
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="dogip", choices=["dogip", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solves")
+    ap.add_argument("--check-every", type=int, default=32)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    from paper_1710_09913_gb300 import build
+    build.build()
+    from paper_1710_09913_gb300 import binding as B
+
+    coords, cells, A = mesh_and_coef()
+    E = len(cells)
+    A_dev = torch.tensor(A, device="cuda")
+    ctxs, bs, us = {}, {}, {}
+    for p in P_LIST:
+        ctxs[p] = B.Context(coords, cells, p, "elliptic", A)
+        bs[p] = torch.empty(ctxs[p].n, dtype=torch.float64, device="cuda")
+        us[p] = torch.zeros(ctxs[p].n, dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(record):
+        applies = 0
+        for p in P_LIST:
+            c = ctxs[p]
+            c.set_coef(A_dev)
+            c.load(None, bs[p])
+            _, info = c.solve(bs[p], us[p], mode="mixed", tol=TOL, check_every=args.check_every)
+            if info["status"] != 0:
+                raise RuntimeError(f"P{p} mixed solve failed: {info}")
+            n_app = info["iterations"] + info["outer"]
+            applies += c.n * n_app
+            if record is not None:
+                record[p] = info
+        return applies
+
+    for _ in range(args.warmup):
+        step(None)
+    torch.cuda.synchronize()
+    barrier(ws)
+
+    launches0 = sum(c.launches() for c in ctxs.values())
+    infos = {}
+    total_ms, work = 0.0, 0
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()  # evict L2 between steps (512 MiB write > 129 MB L2)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            work += step(infos)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            total_ms += ev0.elapsed_time(ev1)
+    barrier(ws)
+    launches = sum(c.launches() for c in ctxs.values()) - launches0
+    total_ms = max_over_ranks(total_ms, ws)
+    work_all = work * ws
+    value = work_all / (total_ms * 1e-3) / 1e9
+    clocks = clk.summary()
+
+    # time-to-tolerance per p: mixed (from the timed steps' last solve) and FP64 PCG
+    t2t = {"mixed_ms": {}, "fp64_ms": {}, "mixed_iters": {}, "fp64_iters": {}, "mixed_outer": {}}
+    for p in P_LIST:
+        c = ctxs[p]
+        for mode in (["mixed"] + ([] if args.no_fp64 else ["fp64"])):
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            _, info = c.solve(bs[p], us[p], mode=mode, tol=TOL, check_every=args.check_every,
+                              allow_notconv=True)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            t2t[f"{mode}_ms"][f"P{p}"] = round(ev0.elapsed_time(ev1), 3)
+            t2t[f"{mode}_iters"][f"P{p}"] = info["iterations"]
+            if mode == "mixed":
+                t2t["mixed_outer"][f"P{p}"] = info["outer"]
+            t2t.setdefault(f"{mode}_rel_residual", {})[f"P{p}"] = info["rel_residual"]
+
+    # apply throughput and roofline of the dominant kernel (FP32 apply)
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    applies = {}
+    for p in P_LIST:
+        c = ctxs[p]
+        inf = c.info
+        for prec, dt, s in (("fp32", torch.float32, 4), ("fp64", torch.float64, 8)):
+            u = torch.randn(c.n, dtype=dt, device="cuda")
+            y = torch.empty_like(u)
+            for _ in range(3):
+                c.apply(u, y, prec=prec)
+            reps = 30 if prec == "fp32" else 10
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(reps):
+                c.apply(u, y, prec=prec)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1) / reps
+            bytes_alg = E * inf.w_loc * inf.n_sym * s + E * inf.v_loc * 4 + 2 * c.n * s
+            flops_alg = E * (2 * inf.nnz_b + 2 * (inf.nnz_b - inf.nnz_pm1_b) + (2 * 4 - 2) * inf.w_loc)
+            applies[f"P{p}_{prec}"] = {"ms": round(ms, 4), "gdofs": round(c.n / ms / 1e6, 3),
+                                       "GBps": round(bytes_alg / ms / 1e6, 1),
+                                       "TFLOPs": round(flops_alg / ms / 1e9, 3),
+                                       "alg_bytes": int(bytes_alg), "alg_flops": int(flops_alg)}
+    dom = applies["P4_fp32"]
+    roofline = {"bound": "hbm", "achieved": dom["GBps"], "peak": hbm, "unit": "GB/s",
+                "frac": round(dom["GBps"] / hbm, 4), "traffic": None,
+                "kernel": "k_apply<2,4,ELLIPTIC,float,atomic> (dogip_apply call: memset + kernel "
+                          "+ boundary copy), 2D P4, 524,288 cells",
+                "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
+                "alg_bytes_per_launch": dom["alg_bytes"]}
+
+    # end to end through the public API with host buffers
+    A_host = torch.tensor(A).pin_memory()
+    u_host = {p: torch.empty(ctxs[p].n, dtype=torch.float64).pin_memory() for p in P_LIST}
+    e2e_ms, e2e_work = 0.0, 0
+    h2d = A_host.numel() * 8
+    d2h = sum(ctxs[p].n * 8 for p in P_LIST)
+    for it in range(max(1, min(args.steps, 3))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        A_dev.copy_(A_host, non_blocking=True)
+        for p in P_LIST:
+            c = ctxs[p]
+            c.set_coef(A_dev)
+            c.load(None, bs[p])
+            _, info = c.solve(bs[p], us[p], mode="mixed", tol=TOL, check_every=args.check_every)
+            u_host[p].copy_(us[p], non_blocking=True)
+            e2e_work += c.n * (info["iterations"] + info["outer"])
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms += ev0.elapsed_time(ev1)
+    e2e_ms = max_over_ranks(e2e_ms, ws)
+    e2e = {"value": e2e_work * ws / (e2e_ms * 1e-3) / 1e9, "unit": "GDoF/s",
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        w, s, desc = oracle_sample(coords, cells, A, P_LIST, 1)
+        cpu = {"value": w / s / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32 inner / f64 refinement", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "cells": E, "p": list(P_LIST),
+                           "dofs": {f"P{p}": ctxs[p].n for p in P_LIST}, "tol": TOL,
+                           "l2": "flushed between steps (512 MiB write)",
+                           "parallelism": "replicas (independent problems per GPU)"},
+                "value_definition": "sum_p n_p x operator applies / step time (applies inside the "
+                                    "mixed solves, FP32 inner and FP64 residual)",
+                "time_to_tol": t2t, "apply": applies, "roofline": roofline,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -143,6 +143,8 @@ typedef struct {
   int n_colours;
   int64_t nnz_b, nnz_pm1_b; /* nonzero / +-1 entries of B (eq. comp_eff)     */
   int64_t bytes_ahat_fp64, bytes_ahat_fp32, bytes_conn;
+  int64_t kernel_launches; /* kernels this context has launched so far,
+                              counting every node of replayed CUDA graphs   */
 } dogip_info;
 
 DOGIP_API int dogip_get_info(const dogip_ctx* ctx, dogip_info* info);

@@ -61,7 +61,8 @@ class Info(C.Structure):
                 ("n_dofs", C.c_int64), ("n_boundary", C.c_int64), ("v_loc", C.c_int),
                 ("w_loc", C.c_int), ("n_sym", C.c_int), ("n_colours", C.c_int),
                 ("nnz_b", C.c_int64), ("nnz_pm1_b", C.c_int64), ("bytes_ahat_fp64", C.c_int64),
-                ("bytes_ahat_fp32", C.c_int64), ("bytes_conn", C.c_int64)]
+                ("bytes_ahat_fp32", C.c_int64), ("bytes_conn", C.c_int64),
+                ("kernel_launches", C.c_int64)]
 
 
 class SolveOpts(C.Structure):
@@ -188,6 +189,11 @@ class Context:
     close = __del__
 
     # ------------------------------------------------------------ queries
+    def launches(self):
+        """Kernels this context has launched so far (graph nodes included)."""
+        _check(lib.dogip_get_info(self._h, C.byref(self.info)))
+        return self.info.kernel_launches
+
     def dofmap(self):
         out = np.zeros((self.E, self.info.v_loc), dtype=np.int32)
         _check(lib.dogip_get_dofmap(self._h, out.ctypes.data_as(_vp)))

@@ -438,15 +438,16 @@ void run_chunk(Ctx& c, int prec, int scatter, double* x64, int k) {
   if (!hit) {
     if (w.graph) cudaGraphExecDestroy(w.graph);
     w.graph = nullptr;
+    const int64_t launches_before = c.launches;  // captured launches run only on replay
     cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
     try {
       for (int it = 0; it < k; ++it) {
         if (prec == DOGIP_FP64) {
           launch_apply(c, w.p64, w.q64, w.R, DOGIP_FP64, scatter, s, w.flags);
-          vec_cg_step(w, DOGIP_FP64, x64, c.d_dinv64, s);
+          c.launches += vec_cg_step(w, DOGIP_FP64, x64, c.d_dinv64, s);
         } else {
           launch_apply(c, w.p32, w.q32, w.R, DOGIP_FP32, scatter, s, w.flags);
-          vec_cg_step(w, DOGIP_FP32, nullptr, c.d_dinv32, s);
+          c.launches += vec_cg_step(w, DOGIP_FP32, nullptr, c.d_dinv32, s);
         }
       }
       cuda_check(cudaMemcpyAsync(w.h_flags, w.flags, sizeof(int) * 2, cudaMemcpyDeviceToHost, s),
@@ -459,8 +460,19 @@ void run_chunk(Ctx& c, int prec, int scatter, double* x64, int k) {
       if (g) cudaGraphDestroy(g);
       throw;
     }
+    c.launches = launches_before;
     cudaGraph_t g = nullptr;
     cuda_check(cudaStreamEndCapture(s, &g), "end capture");
+    size_t nn = 0;
+    cuda_check(cudaGraphGetNodes(g, nullptr, &nn), "graph nodes");
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cuda_check(cudaGraphGetNodes(g, nodes.data(), &nn), "graph nodes");
+    w.graph_kernels = 0;
+    for (auto nd : nodes) {
+      cudaGraphNodeType ty;
+      cuda_check(cudaGraphNodeGetType(nd, &ty), "graph node type");
+      if (ty == cudaGraphNodeTypeKernel) ++w.graph_kernels;
+    }
     cudaError_t e = cudaGraphInstantiate(&w.graph, g, 0);
     cudaGraphDestroy(g);
     cuda_check(e, "graph instantiate");
@@ -471,6 +483,7 @@ void run_chunk(Ctx& c, int prec, int scatter, double* x64, int k) {
     w.graph_key[1] = w.p64;
   }
   cuda_check(cudaGraphLaunch(w.graph, s), "graph launch");
+  c.launches += w.graph_kernels;
   cuda_check(cudaStreamSynchronize(s), "cg chunk");
 }
 
@@ -519,7 +532,7 @@ int solve(Ctx& c, const double* b, double* u, int R, const dogip_solve_opts* opt
     // the recursion drifted (at most a few restarts).
     if (o.use_x0) launch_apply(c, u, w.q64, R, DOGIP_FP64, scatter, s, nullptr);
     else cuda_check(cudaMemsetAsync(w.q64, 0, bytes, s), "zero q");
-    vec_residual64(w, b, w.q64, true, o.tol, s);
+    c.launches += vec_residual64(w, b, w.q64, true, o.tol, s);
     for (int restart = 0;; ++restart) {
       read_scal(c);
       bool all = true;
@@ -527,7 +540,7 @@ int solve(Ctx& c, const double* b, double* u, int R, const dogip_solve_opts* opt
       if (all) break;
       if (iters >= o.maxiter || restart > 8) { status = DOGIP_ENOTCONV; break; }
       if (timed_out()) { status = DOGIP_ETIMEOUT; break; }
-      vec_init64(w, c.d_dinv64, o.tol, s);
+      c.launches += vec_init64(w, c.d_dinv64, o.tol, s);
       read_scal(c);
       int done_here = 0;
       while (!w.h_flags[0]) {
@@ -542,7 +555,7 @@ int solve(Ctx& c, const double* b, double* u, int R, const dogip_solve_opts* opt
       iters += done_here;
       const bool brk = w.h_flags[1];
       launch_apply(c, u, w.q64, R, DOGIP_FP64, scatter, s, nullptr);
-      vec_residual64(w, b, w.q64, false, o.tol, s);
+      c.launches += vec_residual64(w, b, w.q64, false, o.tol, s);
       if (brk) {
         read_scal(c);
         status = DOGIP_EBREAKDOWN;
@@ -554,7 +567,7 @@ int solve(Ctx& c, const double* b, double* u, int R, const dogip_solve_opts* opt
     for (outer = 0;; ++outer) {
       if (outer == 0 && !o.use_x0) cuda_check(cudaMemsetAsync(w.q64, 0, bytes, s), "zero q");
       else launch_apply(c, u, w.q64, R, DOGIP_FP64, scatter, s, nullptr);
-      vec_residual64(w, b, w.q64, outer == 0, o.tol, s);
+      c.launches += vec_residual64(w, b, w.q64, outer == 0, o.tol, s);
       read_scal(c);
       bool all = true;
       for (int r = 0; r < R; ++r) all = all && w.h_scal[r].odone;
@@ -562,7 +575,7 @@ int solve(Ctx& c, const double* b, double* u, int R, const dogip_solve_opts* opt
       if (outer >= o.max_outer) { status = DOGIP_ENOTCONV; break; }
       if (budget <= 0) { status = DOGIP_ENOTCONV; break; }
       if (timed_out()) { status = DOGIP_ETIMEOUT; break; }
-      vec_inner_init32(w, c.d_dinv32, o.inner_tol, s);
+      c.launches += vec_inner_init32(w, c.d_dinv32, o.inner_tol, s);
       read_scal(c);
       int inner = 0;
       const int lim = std::min(o.inner_maxiter, budget);
@@ -577,7 +590,7 @@ int solve(Ctx& c, const double* b, double* u, int R, const dogip_solve_opts* opt
       iters += inner;
       budget -= inner;
       if (w.h_flags[1] && inner == 0) { status = DOGIP_EBREAKDOWN; break; }
-      vec_correct(w, u, s);
+      c.launches += vec_correct(w, u, s);
     }
   }
   double worst = 0.0;
@@ -692,6 +705,7 @@ int dogip_get_info(const dogip_ctx* c, dogip_info* i) {
     i->bytes_ahat_fp64 = (int64_t)c->E * c->WT * c->NS * 8;
     i->bytes_ahat_fp32 = (int64_t)c->E * c->WT * c->NS * 4;
     i->bytes_conn = (int64_t)c->E * c->VT * 4;
+    i->kernel_launches = c->launches;
     return DOGIP_OK;
   });
 }

@@ -48,6 +48,7 @@ struct SolveWork {
   cudaGraphExec_t graph = nullptr;
   const void* graph_key[4] = {nullptr, nullptr, nullptr, nullptr};
   int graph_chunk = 0, graph_prec = -1, graph_scatter = -1;
+  int64_t graph_kernels = 0;  // kernel nodes in the captured chunk
 };
 
 constexpr int kMaxRedBlocks = 1024;
@@ -85,6 +86,7 @@ struct dogip_ctx {
   double* d_coef = nullptr;    // caller order copy of the setup coefficients
   int* d_err = nullptr;        // validation flags
   dogip::SolveWork work;
+  int64_t launches = 0;           // kernels launched (graph replays count every node)
   cudaStream_t stream = nullptr;  // private stream for graph-captured solves
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 };
@@ -120,22 +122,22 @@ bool table_info(int d, int p, int form, int* NB, int* W, int* V, long long* nnz,
                 long long* nnz1);
 bool table_copy(int d, int p, int form, double* B, double* w, double* iv);
 
-// ---- solver vector kernels (vec.cu) -----------------------------------------
+// ---- solver vector kernels (vec.cu); each returns the number of kernels it launched
 void vec_alloc(SolveWork& w, int64_t n, int R);
 void vec_free(SolveWork& w);
 // r64 <- b - Kx (FP64) with per-rhs ||r||^2 (and ||b||^2 when first); sets
 // rel = ||r||/||b||, s = ||r||, odone = rel <= otol.
-void vec_residual64(SolveWork& w, const double* b, const double* Kx, bool first,
+int vec_residual64(SolveWork& w, const double* b, const double* Kx, bool first,
                     double otol, cudaStream_t st);
 // Inner FP32 start: r32 = r64 / s (0 for finished rhs), x32 = 0, p = Dinv r,
 // rho = r.z, r0 = ||r32||, tol = inner_tol.
-void vec_inner_init32(SolveWork& w, const float* dinv, double inner_tol, cudaStream_t st);
+int vec_inner_init32(SolveWork& w, const float* dinv, double inner_tol, cudaStream_t st);
 // FP64 PCG start from r64 = b - K x0: p = Dinv r, rho, r0 = ||b||, tol.
-void vec_init64(SolveWork& w, const double* dinv, double tol, cudaStream_t st);
+int vec_init64(SolveWork& w, const double* dinv, double tol, cudaStream_t st);
 // The CG iteration after q = K p: alpha = rho / p.q, x += alpha p, r -= alpha q,
 // rho' = r.Dinv r, beta, p = Dinv r + beta p; per-rhs convergence test.
-void vec_cg_step(SolveWork& w, int prec, double* x64, const void* dinv, cudaStream_t st);
+int vec_cg_step(SolveWork& w, int prec, double* x64, const void* dinv, cudaStream_t st);
 // x64 += s * x32 for rhs still refining.
-void vec_correct(SolveWork& w, double* x64, cudaStream_t st);
+int vec_correct(SolveWork& w, double* x64, cudaStream_t st);
 
 }  // namespace dogip

@@ -119,6 +119,7 @@ void launch_ahat(Ctx& c, const double* coef, int coef_kind, cudaStream_t s) {
 #undef CALL
   if (!ok_) fail(DOGIP_EUNSUPPORTED, "no compiled instance for this (dim, p, form)");
   cuda_check(cudaGetLastError(), "ahat kernel launch");
+  c.launches += 1;
   launch_diag_finish(c, s);
 }
 
@@ -129,6 +130,7 @@ void launch_diag_finish(Ctx& c, cudaStream_t s) {
                                                                   c.n);
   k_diag_inv<<<(unsigned)((c.n + 255) / 256), 256, 0, s>>>(c.d_diag, c.d_dinv64, c.d_dinv32, c.n);
   cuda_check(cudaGetLastError(), "diag kernels launch");
+  c.launches += (c.nbnd > 0 ? 2 : 1);
 }
 
 void launch_load(Ctx& c, const double* f, double* b, cudaStream_t s) {
@@ -139,6 +141,7 @@ void launch_load(Ctx& c, const double* f, double* b, cudaStream_t s) {
 #undef CALL
   if (!ok_) fail(DOGIP_EUNSUPPORTED, "no compiled instance for this (dim, p, form)");
   cuda_check(cudaGetLastError(), "load kernel launch");
+  c.launches += 1;
 }
 
 void launch_grad(Ctx& c, const double* u, const double* lam, double* dA, cudaStream_t s) {
@@ -148,6 +151,7 @@ void launch_grad(Ctx& c, const double* u, const double* lam, double* dA, cudaStr
 #undef CALL
   if (!ok_) fail(DOGIP_EUNSUPPORTED, "no compiled instance for this (dim, p, form)");
   cuda_check(cudaGetLastError(), "gradient kernel launch");
+  c.launches += 1;
 }
 
 void launch_export_ahat(const Ctx& c, double* out, cudaStream_t s) {
@@ -185,10 +189,15 @@ void launch_apply(Ctx& c, const void* u, void* y, int R, int prec, int scatter, 
   };
   if (scatter == DOGIP_SCATTER_COLOUR) {
     for (int k = 0; k < c.ncolours; ++k) run(false, c.colour_start[k], c.colour_start[k + 1]);
+    c.launches += c.ncolours;
   } else {
     run(true, 0, c.E);
+    c.launches += 1;
   }
-  if (c.dirichlet) launch_dirichlet_copy(c, u, y, R, prec, s, skip);
+  if (c.dirichlet && c.nbnd > 0) {
+    launch_dirichlet_copy(c, u, y, R, prec, s, skip);
+    c.launches += 1;
+  }
   cuda_check(cudaGetLastError(), "apply kernel launch");
 }
 

@@ -318,7 +318,7 @@ void vec_free(SolveWork& w) {
   w = SolveWork{};
 }
 
-void vec_residual64(SolveWork& w, const double* b, const double* Kx, bool first, double otol,
+int vec_residual64(SolveWork& w, const double* b, const double* Kx, bool first, double otol,
                     cudaStream_t st) {
   const int64_t N = w.n * w.R;
   Red rd = red_of(w);
@@ -326,9 +326,10 @@ void vec_residual64(SolveWork& w, const double* b, const double* Kx, bool first,
   DOGIP_R_SWITCH(w.R, CALL);
 #undef CALL
   cuda_check(cudaGetLastError(), "residual kernel");
+  return 1;
 }
 
-void vec_inner_init32(SolveWork& w, const float* dinv, double inner_tol, cudaStream_t st) {
+int vec_inner_init32(SolveWork& w, const float* dinv, double inner_tol, cudaStream_t st) {
   const int64_t N = w.n * w.R;
   Red rd = red_of(w);
 #define CALL(RR)                                                                              \
@@ -338,9 +339,10 @@ void vec_inner_init32(SolveWork& w, const float* dinv, double inner_tol, cudaStr
   DOGIP_R_SWITCH(w.R, CALL);
 #undef CALL
   cuda_check(cudaGetLastError(), "inner init kernels");
+  return 2;
 }
 
-void vec_init64(SolveWork& w, const double* dinv, double tol, cudaStream_t st) {
+int vec_init64(SolveWork& w, const double* dinv, double tol, cudaStream_t st) {
   const int64_t N = w.n * w.R;
   Red rd = red_of(w);
 #define CALL(RR) \
@@ -348,9 +350,10 @@ void vec_init64(SolveWork& w, const double* dinv, double tol, cudaStream_t st) {
   DOGIP_R_SWITCH(w.R, CALL);
 #undef CALL
   cuda_check(cudaGetLastError(), "init kernel");
+  return 1;
 }
 
-void vec_cg_step(SolveWork& w, int prec, double* x64, const void* dinv, cudaStream_t st) {
+int vec_cg_step(SolveWork& w, int prec, double* x64, const void* dinv, cudaStream_t st) {
   const int64_t N = w.n * w.R;
   Red rd = red_of(w);
   const unsigned nb = red_blocks(N);
@@ -372,14 +375,16 @@ void vec_cg_step(SolveWork& w, int prec, double* x64, const void* dinv, cudaStre
 #undef CALL
   }
   cuda_check(cudaGetLastError(), "cg step kernels");
+  return 3;
 }
 
-void vec_correct(SolveWork& w, double* x64, cudaStream_t st) {
+int vec_correct(SolveWork& w, double* x64, cudaStream_t st) {
   const int64_t N = w.n * w.R;
 #define CALL(RR) k_correct<RR><<<red_blocks(N), kRedThreads, 0, st>>>(x64, w.x32, N, w.scal)
   DOGIP_R_SWITCH(w.R, CALL);
 #undef CALL
   cuda_check(cudaGetLastError(), "correct kernel");
+  return 1;
 }
 
 }  // namespace dogip
