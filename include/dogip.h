@@ -257,6 +257,13 @@ DOGIP_API int dogip_solve_host(dogip_ctx* ctx, const double* b_host, double* u_h
 DOGIP_API int dogip_grad_coef(dogip_ctx* ctx, const double* u, const double* lam,
                     double* dA, void* cuda_stream);
 
+/*
+ * Synchronise cuda_stream and report device-side failures of earlier asynchronous
+ * calls on this context: DOGIP_ETIMEOUT if a bounded wait inside a kernel (the
+ * staged apply's shared-memory pipeline) gave up; the flag is then cleared.
+ */
+DOGIP_API int dogip_check(dogip_ctx* ctx, void* cuda_stream);
+
 /* ------------------------------------------------------------------ errors */
 DOGIP_API const char* dogip_last_error(void); /* thread-local, never NULL */
 DOGIP_API int dogip_version(void);            /* major * 10000 + minor * 100 + patch */

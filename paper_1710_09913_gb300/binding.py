@@ -100,6 +100,7 @@ _SIGS = {
     "dogip_solve_host": (C.c_int, [_vp, _vp, _vp, C.c_int, C.POINTER(SolveOpts),
                                    C.POINTER(SolveInfo), _vp, _vp]),
     "dogip_grad_coef": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "dogip_check": (C.c_int, [_vp, _vp]),
     "dogip_last_error": (C.c_char_p, []),
     "dogip_version": (C.c_int, []),
 }
@@ -306,6 +307,10 @@ class Context:
                                     rel.ctypes.data_as(_vp), _stream(stream)))
         return dict(status=inf.status, iterations=inf.iterations, outer=inf.outer,
                     rel_residual=inf.rel_residual, seconds=inf.seconds)
+
+    def check(self, stream=None):
+        """Synchronise and raise if a kernel-side bounded wait expired."""
+        _check(lib.dogip_check(self._h, _stream(stream)))
 
     def grad_coef(self, u, lam, stream=None):
         import torch

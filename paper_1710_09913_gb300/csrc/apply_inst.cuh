@@ -1,5 +1,7 @@
 // Host-side launch of the apply kernel for one (D, P, FORM) instance.
 #pragma once
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace dogip {
@@ -21,13 +23,68 @@ void run_apply_t(const T* A, const Ctx& c, const void* u, void* y, int R, bool a
   }
 }
 
+// Persistent bulk-async variant over the whole cell range (atomic scatter).
+struct TmaLaunch {
+  int blocks_per_sm = 1, num_sms = 1;
+};
+
+// Kernel attributes and residency of one instance, set once (thread-safe static);
+// first called from context set-up, outside any stream capture.
+template <int D, int P, int FORM, typename T>
+const TmaLaunch& tma_launch() {
+  static const TmaLaunch info = [] {
+    using Cfg = TmaCfg<D, P, FORM, T>;
+    auto kern = k_apply_tma<D, P, FORM, T>;
+    TmaLaunch t;
+    cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM),
+               "apply smem attribute");
+    int dev = 0, nb = 0;
+    cuda_check(cudaGetDevice(&dev), "get device");
+    cuda_check(cudaDeviceGetAttribute(&t.num_sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, Cfg::THREADS, Cfg::SMEM),
+               "occupancy");
+    t.blocks_per_sm = nb < 1 ? 1 : nb;
+    return t;
+  }();
+  return info;
+}
+
+template <int D, int P, int FORM, typename T>
+void run_apply_tma(const T* A, const Ctx& c, const void* u, void* y, int R, cudaStream_t s,
+                   const int* skip) {
+  using Cfg = TmaCfg<D, P, FORM, T>;
+  auto kern = k_apply_tma<D, P, FORM, T>;
+  const TmaLaunch& L = tma_launch<D, P, FORM, T>();
+  const int blocks_per_sm = L.blocks_per_sm, num_sms = L.num_sms;
+  const int64_t ntiles = (c.E + kTile - 1) / kTile;
+  const int64_t nchunks = (ntiles + Cfg::TPC - 1) / Cfg::TPC;
+  if (nchunks == 0) return;
+  const int64_t grid = std::min<int64_t>(nchunks, (int64_t)num_sms * blocks_per_sm);
+  TmaArgs<T> a{A, c.d_conn, (const T*)u, (T*)y, c.E, ntiles, nchunks, R, skip, c.d_kerr};
+  kern<<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
+}
+
 template <int D, int P, int FORM>
 void run_apply(const Ctx& c, const void* u, void* y, int R, int prec, bool atomic, int64_t e0,
                int64_t e1, cudaStream_t s, const int* skip) {
-  if (prec == DOGIP_FP64)
+  constexpr bool ok64 = TmaCfg<D, P, FORM, double>::OK, ok32 = TmaCfg<D, P, FORM, float>::OK;
+  if (u == nullptr) {  // preparation call from context set-up
+    if constexpr (ok64) tma_launch<D, P, FORM, double>();
+    if constexpr (ok32) tma_launch<D, P, FORM, float>();
+    return;
+  }
+  const bool whole = atomic && e0 == 0 && e1 == c.E && c.apply_variant == 1;
+  if (prec == DOGIP_FP64) {
+    if constexpr (ok64) {
+      if (whole) return run_apply_tma<D, P, FORM, double>(c.d_A64, c, u, y, R, s, skip);
+    }
     run_apply_t<D, P, FORM, double>(c.d_A64, c, u, y, R, atomic, e0, e1, s, skip);
-  else
+  } else {
+    if constexpr (ok32) {
+      if (whole) return run_apply_tma<D, P, FORM, float>(c.d_A32, c, u, y, R, s, skip);
+    }
     run_apply_t<D, P, FORM, float>(c.d_A32, c, u, y, R, atomic, e0, e1, s, skip);
+  }
 }
 
 }  // namespace dogip

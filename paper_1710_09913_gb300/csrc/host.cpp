@@ -2,6 +2,7 @@
 // colouring), context construction, queries, the solve driver and the C ABI.
 #include <algorithm>
 #include <chrono>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -244,7 +245,7 @@ void free_ctx(Ctx* c) {
   for (void* p : {(void*)c->d_coords, (void*)c->d_cells, (void*)c->d_perm, (void*)c->d_conn,
                   (void*)c->d_A64, (void*)c->d_A32, (void*)c->d_geo, (void*)c->d_diag,
                   (void*)c->d_dinv64, (void*)c->d_dinv32, (void*)c->d_bnd, (void*)c->d_coef,
-                  (void*)c->d_err})
+                  (void*)c->d_err, (void*)c->d_kerr})
     if (p) cudaFree(p);
   if (c->stream) cudaStreamDestroy(c->stream);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
@@ -382,6 +383,8 @@ Ctx* setup(const dogip_mesh* m, int p, int form, int coef_kind, const double* co
     c->d_bnd = dev_alloc<int32_t>(bnd.size());
     c->d_coef = dev_alloc<double>(ncoef);
     c->d_err = dev_alloc<int>(1);
+    c->d_kerr = dev_alloc<int>(1);
+    if (const char* v = std::getenv("DOGIP_APPLY_VARIANT")) c->apply_variant = std::atoi(v);
     cudaStream_t s = c->stream;
     cuda_check(cudaMemcpyAsync(c->d_coords, m->coords, sizeof(double) * c->nv * d,
                                cudaMemcpyHostToDevice, s), "upload coords");
@@ -401,8 +404,10 @@ Ctx* setup(const dogip_mesh* m, int p, int form, int coef_kind, const double* co
     if (c->keep32)
       cuda_check(cudaMemsetAsync(c->d_A32, 0, sizeof(float) * c->Epad * W * c->NS, s), "memset A32");
     cuda_check(cudaMemsetAsync(c->d_err, 0, sizeof(int), s), "memset err");
+    cuda_check(cudaMemsetAsync(c->d_kerr, 0, sizeof(int), s), "memset kernel err");
     launch_ahat(*c, c->d_coef, coef_kind, s);
     check_coef_status(*c, s);
+    prepare_apply(*c);
   } catch (...) {
     free_ctx(c);
     throw;
@@ -452,6 +457,8 @@ void run_chunk(Ctx& c, int prec, int scatter, double* x64, int k) {
       }
       cuda_check(cudaMemcpyAsync(w.h_flags, w.flags, sizeof(int) * 2, cudaMemcpyDeviceToHost, s),
                  "flags copy");
+      cuda_check(cudaMemcpyAsync(w.h_flags + 2, c.d_kerr, sizeof(int), cudaMemcpyDeviceToHost, s),
+                 "kernel flag copy");
       cuda_check(cudaMemcpyAsync(w.h_scal, w.scal, sizeof(CGScal) * w.R, cudaMemcpyDeviceToHost, s),
                  "scal copy");
     } catch (...) {
@@ -485,6 +492,7 @@ void run_chunk(Ctx& c, int prec, int scatter, double* x64, int k) {
   cuda_check(cudaGraphLaunch(w.graph, s), "graph launch");
   c.launches += w.graph_kernels;
   cuda_check(cudaStreamSynchronize(s), "cg chunk");
+  if (w.h_flags[2]) fail(DOGIP_ETIMEOUT, "a bounded wait inside the apply kernel expired");
 }
 
 void read_scal(Ctx& c) {
@@ -742,6 +750,23 @@ int dogip_get_ahat(const dogip_ctx* c, double* out, void* stream) {
     if (!c || !out) fail(DOGIP_EINVAL, "ctx and output are required");
     dogip::DeviceGuard g(c->device);
     dogip::launch_export_ahat(*c, out, (cudaStream_t)stream);
+    return DOGIP_OK;
+  });
+}
+
+int dogip_check(dogip_ctx* c, void* stream) {
+  return guarded([&] {
+    if (!c) fail(DOGIP_EINVAL, "ctx is required");
+    dogip::DeviceGuard g(c->device);
+    int kerr = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    dogip::cuda_check(cudaMemcpyAsync(&kerr, c->d_kerr, sizeof(int), cudaMemcpyDeviceToHost, s),
+                      "kernel flag read");
+    dogip::cuda_check(cudaStreamSynchronize(s), "stream sync");
+    if (kerr) {
+      dogip::cuda_check(cudaMemset(c->d_kerr, 0, sizeof(int)), "kernel flag reset");
+      fail(DOGIP_ETIMEOUT, "a bounded wait inside the apply kernel expired");
+    }
     return DOGIP_OK;
   });
 }

@@ -51,7 +51,7 @@ struct SolveWork {
   int64_t graph_kernels = 0;  // kernel nodes in the captured chunk
 };
 
-constexpr int kMaxRedBlocks = 1024;
+constexpr int kMaxRedBlocks = 1216;  // 8 blocks of 256 threads on each of 152 SMs
 constexpr int kRedThreads = 256;
 
 }  // namespace dogip
@@ -85,6 +85,8 @@ struct dogip_ctx {
   int32_t* d_bnd = nullptr;    // [nbnd] boundary dof list
   double* d_coef = nullptr;    // caller order copy of the setup coefficients
   int* d_err = nullptr;        // validation flags
+  int* d_kerr = nullptr;       // kernel wait timeouts (bounded mbarrier waits)
+  int apply_variant = 1;       // 1: bulk-async staged apply; 0: one thread per cell
   dogip::SolveWork work;
   int64_t launches = 0;           // kernels launched (graph replays count every node)
   cudaStream_t stream = nullptr;  // private stream for graph-captured solves
@@ -116,6 +118,8 @@ void launch_export_ahat(const Ctx& c, double* out, cudaStream_t s);
 void launch_dirichlet_copy(const Ctx& c, const void* u, void* y, int R, int prec,
                            cudaStream_t s, const int* skip);
 void launch_diag_finish(Ctx& c, cudaStream_t s);
+// One-time kernel attributes of the apply instances of this context (host only).
+void prepare_apply(Ctx& c);
 
 // Static table access for the host (dogip_get_tables, info).
 bool table_info(int d, int p, int form, int* NB, int* W, int* V, long long* nnz,

@@ -193,6 +193,192 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> a) {
   });
 }
 
+// ------------------------------------------------- bulk-async staged apply
+//
+// Persistent variant of Algorithm 1 for the whole cell range: the A_T and conn
+// streams are contiguous per 32-cell tile in the AoSoA layout, so chunks of TPC
+// tiles are moved HBM -> shared memory by cp.async.bulk (the TMA engine) into an
+// S-stage ring tracked by mbarriers, while the warps of the CTA compute on the
+// previous stage.  One warp owns one tile (one thread per cell) and loops over the
+// right-hand sides, reusing A_T from shared memory.  The u gathers and the atomic
+// scatter go to L2.  Every wait is bounded by a clock budget; on expiry the kernel
+// raises an error flag, drains its copies in flight (bounded again) and returns.
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes,
+                                              uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Wait for phase `parity` of `bar`, giving up after `budget` clock cycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long budget) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > budget) return false;
+  }
+  return true;
+}
+
+constexpr long long kWaitBudget = 4000000000LL;  // ~2 s of SM clock per wait
+
+template <int D, int P, int FORM, typename T>
+struct TmaCfg {
+  using TB = dogip_tab::Tab<D, P, FORM>;
+  static constexpr int V = TB::V, W = TB::W, NS = NSym<D, FORM>::value;
+  static constexpr uint32_t A_TILE = W * NS * kTile * sizeof(T);
+  static constexpr uint32_t C_TILE = V * kTile * 4;
+  static constexpr uint32_t kBudget = 200 * 1024;  // shared memory for the ring
+  static constexpr int TPC = (2 * 8 * (A_TILE + C_TILE) <= kBudget) ? 8 : 4;  // warps per CTA
+  static constexpr uint32_t CHUNK = TPC * (A_TILE + C_TILE);
+  static constexpr int S0 = (int)(kBudget / CHUNK);
+  static constexpr int S = S0 > 4 ? 4 : (S0 < 2 ? 2 : S0);  // pipeline stages
+  static constexpr uint32_t SMEM = S * CHUNK + S * 8 + 128;
+  static constexpr int THREADS = TPC * 32;
+  // Instances whose double-buffered 4-warp ring does not fit (3D P3 FP64) use the
+  // one-thread-per-cell kernel instead.
+  static constexpr bool OK = 2 * CHUNK <= kBudget;
+};
+
+template <typename T>
+struct TmaArgs {
+  const T* A;
+  const uint32_t* conn;
+  const T* u;
+  T* y;
+  int64_t E, ntiles, nchunks;
+  int R;
+  const int* skip;
+  int* err;
+};
+
+template <int D, int P, int FORM, typename T>
+__global__ void __launch_bounds__(TmaCfg<D, P, FORM, T>::THREADS)
+    k_apply_tma(TmaArgs<T> a) {
+  using C = TmaCfg<D, P, FORM, T>;
+  static_assert(C::OK, "stage does not fit in shared memory");
+  using TB = typename C::TB;
+  constexpr int V = C::V, W = C::W, NB = TB::NB, NS = C::NS;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base =
+      (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  uint64_t* bars = (uint64_t*)(base + C::S * C::CHUNK);
+  if (a.skip != nullptr && *a.skip) return;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t G = gridDim.x;
+  if (tid == 0) {
+    for (int s = 0; s < C::S; ++s) mbar_init(&bars[s], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto issue = [&](int64_t i) {
+    const int64_t k = blockIdx.x + i * G;
+    if (k >= a.nchunks) return;
+    const int s = (int)(i % C::S);
+    const int64_t t0 = k * C::TPC;
+    const int nt = (int)min((int64_t)C::TPC, a.ntiles - t0);
+    unsigned char* sa = base + (size_t)s * C::CHUNK;
+    unsigned char* sc = sa + C::TPC * C::A_TILE;
+    mbar_expect_tx(&bars[s], (uint32_t)nt * (C::A_TILE + C::C_TILE));
+    bulk_copy_g2s(sa, (const unsigned char*)a.A + t0 * C::A_TILE, (uint32_t)nt * C::A_TILE, &bars[s]);
+    bulk_copy_g2s(sc, (const unsigned char*)a.conn + t0 * C::C_TILE, (uint32_t)nt * C::C_TILE,
+                  &bars[s]);
+  };
+  if (tid == 0)
+    for (int i = 0; i < C::S; ++i) issue(i);
+  int failed = 0;
+  int64_t i = 0;
+  for (;; ++i) {
+    const int64_t k = blockIdx.x + i * G;
+    if (k >= a.nchunks) break;
+    const int s = (int)(i % C::S);
+    const uint32_t parity = (uint32_t)((i / C::S) & 1);
+    failed = __syncthreads_or(mbar_wait_bounded(&bars[s], parity, kWaitBudget) ? 0 : 1);
+    if (failed) break;
+    const int64_t tile = k * C::TPC + warp;
+    const int64_t e = tile * kTile + lane;
+    if (tile < a.ntiles && e < a.E) {
+      const T* sA = (const T*)(base + (size_t)s * C::CHUNK + warp * C::A_TILE) + lane;
+      const uint32_t* sC =
+          (const uint32_t*)(base + (size_t)s * C::CHUNK + C::TPC * C::A_TILE + warp * C::C_TILE) +
+          lane;
+      uint32_t c[V];
+      static_for<V>([&](auto lc) {
+        constexpr int l = decltype(lc)::value;
+        c[l] = sC[l * kTile];
+      });
+      for (int r = 0; r < a.R; ++r) {
+        T ul[V], Y[V];
+        static_for<V>([&](auto lc) {
+          constexpr int l = decltype(lc)::value;
+          ul[l] = (c[l] & kBndBit) ? T(0) : __ldg(a.u + (int64_t)(c[l] & kIdMask) * a.R + r);
+          if constexpr (col_empty<TB>(l)) Y[l] = T(0);
+        });
+        static_for<W>([&](auto jc) {
+          constexpr int j = decltype(jc)::value;
+          T g[NB], h[NB], aj[NS];
+          static_for<NS>([&](auto kc) {
+            constexpr int kk = decltype(kc)::value;
+            aj[kk] = sA[(j * NS + kk) * kTile];
+          });
+          interp<TB, j>(ul, g);
+          block_mul<D, FORM>(aj, g, h);
+          project<TB, j>(h, Y);
+        });
+        static_for<V>([&](auto lc) {
+          constexpr int l = decltype(lc)::value;
+          if (!(c[l] & kBndBit)) atomicAdd(a.y + (int64_t)(c[l] & kIdMask) * a.R + r, Y[l]);
+        });
+      }
+    }
+    __syncthreads();  // every read of stage s is done
+    if (tid == 0) {
+      fence_proxy_async_smem();
+      issue(i + C::S);
+    }
+  }
+  if (failed) {
+    // drain the copies this CTA still has in flight, then report
+    if (tid == 0) {
+      for (int64_t q = i; q < i + C::S; ++q) {
+        if (blockIdx.x + q * G >= a.nchunks) break;
+        mbar_wait_bounded(&bars[q % C::S], (uint32_t)((q / C::S) & 1), kWaitBudget);
+      }
+      atomicOr(a.err, 1);
+    }
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------------ setup
 
 struct AhatArgs {

@@ -175,6 +175,14 @@ void launch_dirichlet_copy(const Ctx& c, const void* u, void* y, int R, int prec
                                                 skip);
 }
 
+void prepare_apply(Ctx& c) {
+  bool ok;
+  if (c.d == 2) ok = apply_d2(c, nullptr, nullptr, 1, 0, true, 0, 0, nullptr, nullptr);
+  else if (c.p <= 2) ok = apply_d3a(c, nullptr, nullptr, 1, 0, true, 0, 0, nullptr, nullptr);
+  else ok = apply_d3b(c, nullptr, nullptr, 1, 0, true, 0, 0, nullptr, nullptr);
+  if (!ok) fail(DOGIP_EUNSUPPORTED, "no compiled apply instance for this (dim, p, form)");
+}
+
 void launch_apply(Ctx& c, const void* u, void* y, int R, int prec, int scatter, cudaStream_t s,
                   const int* skip) {
   const size_t es = prec == DOGIP_FP64 ? sizeof(double) : sizeof(float);

@@ -57,11 +57,31 @@ __device__ bool grid_reduce(const Red& rd, double (&acc)[NV], double* tot) {
   __syncthreads();
   if (!last) return false;
   __threadfence();
-  if (threadIdx.x < R * NV) {
-    double s = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(rd.partial + (size_t)b * 64 + threadIdx.x);
-    tot[threadIdx.x] = s;
+  // The last block adds the partials of all blocks: G threads per value, each
+  // over a fixed stride of blocks, then a fixed-order tree (deterministic).
+  constexpr int RV = R * NV;               // divides kRedThreads
+  constexpr int G = kRedThreads / RV;
+  __shared__ double fin[kRedThreads];
+  {
+    const int k = threadIdx.x % RV, g = threadIdx.x / RV;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    unsigned b = g;
+    for (; b + 3 * G < gridDim.x; b += 4 * G) {
+      s0 += __ldcg(rd.partial + (size_t)b * 64 + k);
+      s1 += __ldcg(rd.partial + (size_t)(b + G) * 64 + k);
+      s2 += __ldcg(rd.partial + (size_t)(b + 2 * G) * 64 + k);
+      s3 += __ldcg(rd.partial + (size_t)(b + 3 * G) * 64 + k);
+    }
+    for (; b < gridDim.x; b += G) s0 += __ldcg(rd.partial + (size_t)b * 64 + k);
+    fin[threadIdx.x] = (s0 + s1) + (s2 + s3);
   }
+  __syncthreads();
+#pragma unroll
+  for (int off = G / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off * RV) fin[threadIdx.x] += fin[threadIdx.x + off * RV];
+    __syncthreads();
+  }
+  if (threadIdx.x < RV) tot[threadIdx.x] = fin[threadIdx.x];
   __syncthreads();
   return true;
 }
@@ -78,7 +98,7 @@ __device__ __forceinline__ void set_all_done(const Red& rd, int R) {
 }
 
 unsigned red_blocks(int64_t N) {
-  int64_t b = (N + kRedThreads - 1) / kRedThreads;
+  int64_t b = (N + 4 * kRedThreads - 1) / (4 * kRedThreads);  // >= 4 elements per thread
   if (b > kMaxRedBlocks) b = kMaxRedBlocks;
   if (b < 1) b = 1;
   return (unsigned)b;

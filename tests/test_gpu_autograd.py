@@ -66,7 +66,10 @@ def test_compliance_gradient_vs_oracle_and_fd(mods, d, p, N):
     u = spla.spsolve(K.tocsc(), bb)
     ref = ograd.grad_coef_assembled("elliptic", p, coords, cells, P.conn, u, u)
     ref = 0.5 * (ref + ref.transpose(0, 2, 1))
-    assert np.abs(g - ref).max() <= 1e-8 * np.abs(ref).max()
+    # both sides solve K u = b independently (GPU PCG to 1e-13, oracle direct): the
+    # gradient inherits the solution error ~ cond(K) * 1e-13 ~ 1e-8; the kernel itself
+    # is checked on identical (u, lambda) to 1e-12 in the full-size test below
+    assert np.abs(g - ref).max() <= 1e-6 * np.abs(ref).max()
     # central finite differences of the stationary compliance on seeded elements
     A_dev = torch.tensor(A64, device="cuda")
     x0, _ = ctx.solve(b, mode="fp64", tol=1e-13)
