@@ -75,7 +75,10 @@ extern "C" {
 #define DOGIP_SCATTER_COLOUR 1 /* one pass per element colour, plain adds      */
 
 #define DOGIP_SOLVE_FP64 0  /* FP64 Jacobi-PCG                                 */
-#define DOGIP_SOLVE_MIXED 1 /* FP64 iterative refinement around an FP32 PCG    */
+#define DOGIP_SOLVE_MIXED 1 /* FP32 PCG with FP64 residual replacement (reliable
+                               updates): one Krylov sequence, FP64 solution     */
+#define DOGIP_SOLVE_MIXED_RESTART 2 /* FP64 iterative refinement around restarted
+                                       FP32 PCG solves of K d = r / ||r||       */
 
 typedef struct dogip_ctx dogip_ctx;
 
@@ -207,6 +210,8 @@ typedef struct {
                          convergence checks (>= 1)                             */
   int use_x0;         /* 1: u holds the initial guess; 0: start from u = 0     */
   double timeout_ms;  /* host wall-clock limit, <= 0 for none                  */
+  double reliable_delta; /* MIXED: FP64 correction when the FP32 residual has
+                            dropped by this factor since the last one (0.1)   */
 } dogip_solve_opts;
 
 typedef struct {
@@ -223,8 +228,13 @@ DOGIP_API int dogip_solve_opts_default(dogip_solve_opts* o);
  * Solve K u = b (K with Dirichlet rows when on; Jacobi preconditioner from
  * A_T).  b, u: DEVICE double [n_dofs x nrhs]; nrhs in {1, 2, 4, 8, 16, 32}.
  * FP64 mode: PCG until the recursive residual reaches tol, then the true
- * residual is evaluated in FP64.  Mixed mode: r = b - K u, norms and the
- * update u += s d in FP64; inner PCG on K d = r / s entirely in FP32.
+ * residual is evaluated in FP64 (restarting from it if the recursion drifted).
+ * MIXED: one PCG recursion in FP32 (A_T, vectors, applies); whenever its residual
+ * has dropped by reliable_delta, the FP32 iterate is folded into the FP64
+ * solution, r = b - K u is recomputed in FP64 and replaces the FP32 residual
+ * (the search direction is kept); convergence is decided on that FP64 residual.
+ * MIXED_RESTART: r = b - K u, norms and u += s d in FP64 around restarted FP32
+ * PCG solves of K d = r / s.
  * rel_residual_per_rhs: host [nrhs] or NULL.  Returns ENOTCONV (u written)
  * when the limits are reached first.  Synchronises cuda_stream.
  */

@@ -21,11 +21,11 @@ PROJECTION, ELLIPTIC = 0, 1
 COEF_ELEM_SCALAR, COEF_ELEM_TENSOR = 0, 1
 FP64, FP32 = 0, 1
 SCATTER_ATOMIC, SCATTER_COLOUR = 0, 1
-SOLVE_FP64, SOLVE_MIXED = 0, 1
+SOLVE_FP64, SOLVE_MIXED, SOLVE_MIXED_RESTART = 0, 1, 2
 FORMS = {"projection": PROJECTION, "elliptic": ELLIPTIC}
 PRECS = {"fp64": FP64, "fp32": FP32}
 SCATTERS = {"atomic": SCATTER_ATOMIC, "colour": SCATTER_COLOUR, None: -1}
-MODES = {"fp64": SOLVE_FP64, "mixed": SOLVE_MIXED}
+MODES = {"fp64": SOLVE_FP64, "mixed": SOLVE_MIXED, "mixed_restart": SOLVE_MIXED_RESTART}
 
 
 class DogipError(RuntimeError):
@@ -69,7 +69,7 @@ class SolveOpts(C.Structure):
     _fields_ = [("mode", C.c_int), ("tol", C.c_double), ("maxiter", C.c_int),
                 ("inner_tol", C.c_double), ("inner_maxiter", C.c_int), ("max_outer", C.c_int),
                 ("scatter", C.c_int), ("check_every", C.c_int), ("use_x0", C.c_int),
-                ("timeout_ms", C.c_double)]
+                ("timeout_ms", C.c_double), ("reliable_delta", C.c_double)]
 
 
 class SolveInfo(C.Structure):
@@ -254,7 +254,7 @@ class Context:
         return b
 
     def _solve_opts(self, mode, tol, maxiter, inner_tol, inner_maxiter, max_outer, scatter,
-                    check_every, x0, timeout_ms):
+                    check_every, x0, timeout_ms, reliable_delta=None):
         o = SolveOpts()
         lib.dogip_solve_opts_default(C.byref(o))
         o.mode = MODES.get(mode, mode)
@@ -272,18 +272,20 @@ class Context:
             o.check_every = check_every
         o.use_x0 = int(x0)
         o.timeout_ms = timeout_ms
+        if reliable_delta is not None:
+            o.reliable_delta = reliable_delta
         return o
 
     def solve(self, b, u=None, *, mode="fp64", tol=1e-8, maxiter=None, inner_tol=None,
               inner_maxiter=None, max_outer=None, scatter=None, check_every=None, x0=False,
-              timeout_ms=0.0, stream=None, allow_notconv=False):
+              timeout_ms=0.0, stream=None, allow_notconv=False, reliable_delta=None):
         """Solve K u = b on the device; returns (u, info dict)."""
         import torch
         R = 1 if b.dim() == 1 else b.shape[1]
         if u is None:
             u = torch.zeros_like(b)
         o = self._solve_opts(mode, tol, maxiter, inner_tol, inner_maxiter, max_outer, scatter,
-                             check_every, x0, timeout_ms)
+                             check_every, x0, timeout_ms, reliable_delta)
         inf = SolveInfo()
         rel = np.zeros(R)
         code = lib.dogip_solve(self._h, _dptr(b, torch.float64), _dptr(u, torch.float64), R,

@@ -434,12 +434,13 @@ bool r_ok(int R) { return R == 1 || R == 2 || R == 4 || R == 8 || R == 16 || R =
 
 // One chunk of `k` CG iterations on the solver stream, captured once as a CUDA
 // graph and replayed; ends with a copy of the flags and scalars to pinned host.
-void run_chunk(Ctx& c, int prec, int scatter, double* x64, int k) {
+void run_chunk(Ctx& c, int prec, int scatter, double* x64, int k, double delta) {
   SolveWork& w = c.work;
   cudaStream_t s = c.stream;
   const void* key0 = prec == DOGIP_FP64 ? (const void*)x64 : (const void*)w.x32;
   const bool hit = w.graph && w.graph_prec == prec && w.graph_scatter == scatter &&
-                   w.graph_chunk == k && w.graph_key[0] == key0 && w.graph_key[1] == (void*)w.p64;
+                   w.graph_chunk == k && w.graph_key[0] == key0 && w.graph_key[1] == (void*)w.p64 &&
+                   w.graph_delta == delta;
   if (!hit) {
     if (w.graph) cudaGraphExecDestroy(w.graph);
     w.graph = nullptr;
@@ -449,15 +450,15 @@ void run_chunk(Ctx& c, int prec, int scatter, double* x64, int k) {
       for (int it = 0; it < k; ++it) {
         if (prec == DOGIP_FP64) {
           launch_apply(c, w.p64, w.q64, w.R, DOGIP_FP64, scatter, s, w.flags);
-          c.launches += vec_cg_step(w, DOGIP_FP64, x64, c.d_dinv64, s);
+          c.launches += vec_cg_step(w, DOGIP_FP64, x64, c.d_dinv64, delta, s);
         } else {
           launch_apply(c, w.p32, w.q32, w.R, DOGIP_FP32, scatter, s, w.flags);
-          c.launches += vec_cg_step(w, DOGIP_FP32, nullptr, c.d_dinv32, s);
+          c.launches += vec_cg_step(w, DOGIP_FP32, nullptr, c.d_dinv32, delta, s);
         }
       }
-      cuda_check(cudaMemcpyAsync(w.h_flags, w.flags, sizeof(int) * 2, cudaMemcpyDeviceToHost, s),
+      cuda_check(cudaMemcpyAsync(w.h_flags, w.flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, s),
                  "flags copy");
-      cuda_check(cudaMemcpyAsync(w.h_flags + 2, c.d_kerr, sizeof(int), cudaMemcpyDeviceToHost, s),
+      cuda_check(cudaMemcpyAsync(w.h_flags + 4, c.d_kerr, sizeof(int), cudaMemcpyDeviceToHost, s),
                  "kernel flag copy");
       cuda_check(cudaMemcpyAsync(w.h_scal, w.scal, sizeof(CGScal) * w.R, cudaMemcpyDeviceToHost, s),
                  "scal copy");
@@ -486,20 +487,21 @@ void run_chunk(Ctx& c, int prec, int scatter, double* x64, int k) {
     w.graph_prec = prec;
     w.graph_scatter = scatter;
     w.graph_chunk = k;
+    w.graph_delta = delta;
     w.graph_key[0] = key0;
     w.graph_key[1] = w.p64;
   }
   cuda_check(cudaGraphLaunch(w.graph, s), "graph launch");
   c.launches += w.graph_kernels;
   cuda_check(cudaStreamSynchronize(s), "cg chunk");
-  if (w.h_flags[2]) fail(DOGIP_ETIMEOUT, "a bounded wait inside the apply kernel expired");
+  if (w.h_flags[4]) fail(DOGIP_ETIMEOUT, "a bounded wait inside the apply kernel expired");
 }
 
 void read_scal(Ctx& c) {
   SolveWork& w = c.work;
   cuda_check(cudaMemcpyAsync(w.h_scal, w.scal, sizeof(CGScal) * w.R, cudaMemcpyDeviceToHost, c.stream),
              "scal copy");
-  cuda_check(cudaMemcpyAsync(w.h_flags, w.flags, sizeof(int) * 2, cudaMemcpyDeviceToHost, c.stream),
+  cuda_check(cudaMemcpyAsync(w.h_flags, w.flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, c.stream),
              "flags copy");
   cuda_check(cudaStreamSynchronize(c.stream), "scal sync");
 }
@@ -512,8 +514,11 @@ int solve(Ctx& c, const double* b, double* u, int R, const dogip_solve_opts* opt
   if (opts) o = *opts;
   if (!b || !u) fail(DOGIP_EINVAL, "b and u are required");
   if (!r_ok(R)) fail(DOGIP_EINVAL, "nrhs must be 1, 2, 4, 8, 16 or 32 for solves");
-  if (o.mode != DOGIP_SOLVE_FP64 && o.mode != DOGIP_SOLVE_MIXED) fail(DOGIP_EINVAL, "unknown mode");
-  if (o.mode == DOGIP_SOLVE_MIXED && !c.keep32) fail(DOGIP_EINVAL, "mixed mode needs keep_fp32");
+  if (o.mode != DOGIP_SOLVE_FP64 && o.mode != DOGIP_SOLVE_MIXED && o.mode != DOGIP_SOLVE_MIXED_RESTART)
+    fail(DOGIP_EINVAL, "unknown mode");
+  if (o.mode != DOGIP_SOLVE_FP64 && !c.keep32) fail(DOGIP_EINVAL, "mixed modes need keep_fp32");
+  if (o.mode == DOGIP_SOLVE_MIXED && !(o.reliable_delta > 0.0 && o.reliable_delta < 1.0))
+    fail(DOGIP_EINVAL, "reliable_delta must lie in (0, 1)");
   if (!(o.tol > 0.0)) fail(DOGIP_EINVAL, "tol must be positive");
   int scatter = o.scatter < 0 ? c.scatter : o.scatter;
   if (scatter == DOGIP_SCATTER_COLOUR && c.scatter != DOGIP_SCATTER_COLOUR)
@@ -555,7 +560,7 @@ int solve(Ctx& c, const double* b, double* u, int R, const dogip_solve_opts* opt
         if (iters + done_here >= o.maxiter) break;
         if (timed_out()) break;
         const int k = std::min(chunk, o.maxiter - iters - done_here);
-        run_chunk(c, DOGIP_FP64, scatter, u, k);
+        run_chunk(c, DOGIP_FP64, scatter, u, k, 0.0);
         done_here = 0;
         for (int r = 0; r < R; ++r) done_here = std::max(done_here, w.h_scal[r].iters);
         if (w.h_flags[1]) break;
@@ -569,6 +574,39 @@ int solve(Ctx& c, const double* b, double* u, int R, const dogip_solve_opts* opt
         status = DOGIP_EBREAKDOWN;
         break;
       }
+    }
+  } else if (o.mode == DOGIP_SOLVE_MIXED) {
+    // Reliable-update PCG: FP32 recursion, FP64 residual replacement.
+    if (o.use_x0) launch_apply(c, u, w.q64, R, DOGIP_FP64, scatter, s, nullptr);
+    else cuda_check(cudaMemsetAsync(w.q64, 0, bytes, s), "zero q");
+    c.launches += vec_residual64(w, b, w.q64, true, o.tol, s);
+    c.launches += vec_rel_init(w, c.d_dinv32, o.tol, s);
+    read_scal(c);
+    bool corrected = true;  // r32 equals the true residual right now
+    while (!w.h_flags[2]) {
+      if (iters >= o.maxiter) { status = DOGIP_ENOTCONV; break; }
+      if (timed_out()) { status = DOGIP_ETIMEOUT; break; }
+      const int k = std::min(chunk, o.maxiter - iters);
+      run_chunk(c, DOGIP_FP32, scatter, nullptr, k, o.reliable_delta);
+      iters = 0;
+      for (int r = 0; r < R; ++r) iters = std::max(iters, w.h_scal[r].iters);
+      corrected = false;
+      if (w.h_flags[1]) { status = DOGIP_EBREAKDOWN; break; }
+      if (w.h_flags[0]) {  // correction requested or recursion converged: replace r
+        c.launches += vec_fold(w, u, s);
+        launch_apply(c, u, w.q64, R, DOGIP_FP64, scatter, s, nullptr);
+        c.launches += vec_residual64(w, b, w.q64, false, o.tol, s);
+        c.launches += vec_rel_restart(w, c.d_dinv32, s);
+        read_scal(c);
+        corrected = true;
+        ++outer;
+      }
+    }
+    if (!corrected) {  // report the true residual of the final iterate
+      c.launches += vec_fold(w, u, s);
+      launch_apply(c, u, w.q64, R, DOGIP_FP64, scatter, s, nullptr);
+      c.launches += vec_residual64(w, b, w.q64, false, o.tol, s);
+      read_scal(c);
     }
   } else {
     int budget = o.maxiter;
@@ -590,7 +628,7 @@ int solve(Ctx& c, const double* b, double* u, int R, const dogip_solve_opts* opt
       while (!w.h_flags[0] && inner < lim) {
         if (timed_out()) break;
         const int k = std::min(chunk, lim - inner);
-        run_chunk(c, DOGIP_FP32, scatter, nullptr, k);
+        run_chunk(c, DOGIP_FP32, scatter, nullptr, k, 0.0);
         inner = 0;
         for (int r = 0; r < R; ++r) inner = std::max(inner, w.h_scal[r].iters);
         if (w.h_flags[1]) break;
@@ -669,6 +707,7 @@ int dogip_solve_opts_default(dogip_solve_opts* o) {
   o->check_every = 16;
   o->use_x0 = 0;
   o->timeout_ms = 0.0;
+  o->reliable_delta = 0.1;
   return DOGIP_OK;
 }
 

@@ -27,7 +27,10 @@ constexpr int kErrNotPos = 8;     // coefficient not positive (definite)
 // Per-rhs scalars of a CG iteration (device memory).
 struct CGScal {
   double rho, pq, alpha, beta, rr, r0, bb, s, rel, tol, otol;
+  double rho_prev;  // rho before the last update (reliable-update restarts of beta)
+  double rmax;      // residual norm at the last FP64 correction (reliable updates)
   int done, iters, brk, odone;
+  int upd, pad0, pad1, pad2;  // upd: FP64 correction requested
 };
 
 struct SolveWork {
@@ -41,13 +44,14 @@ struct SolveWork {
   double* partial = nullptr;     // [kMaxRedBlocks x 32 x 2]
   unsigned int* counter = nullptr;
   CGScal* scal = nullptr;        // [R]
-  int* flags = nullptr;          // [0] all_done, [1] any_breakdown
-  int* h_flags = nullptr;        // pinned host mirror of flags + iters
+  int* flags = nullptr;          // [0] stop chunk, [1] breakdown, [2] all done, [3] correction wanted
+  int* h_flags = nullptr;        // pinned host mirror: flags[0..3], [4] kernel wait timeout
   CGScal* h_scal = nullptr;      // pinned host mirror of scal
   // graph cache of the inner iteration chunk
   cudaGraphExec_t graph = nullptr;
   const void* graph_key[4] = {nullptr, nullptr, nullptr, nullptr};
   int graph_chunk = 0, graph_prec = -1, graph_scatter = -1;
+  double graph_delta = -1.0;
   int64_t graph_kernels = 0;  // kernel nodes in the captured chunk
 };
 
@@ -140,7 +144,16 @@ int vec_inner_init32(SolveWork& w, const float* dinv, double inner_tol, cudaStre
 int vec_init64(SolveWork& w, const double* dinv, double tol, cudaStream_t st);
 // The CG iteration after q = K p: alpha = rho / p.q, x += alpha p, r -= alpha q,
 // rho' = r.Dinv r, beta, p = Dinv r + beta p; per-rhs convergence test.
-int vec_cg_step(SolveWork& w, int prec, double* x64, const void* dinv, cudaStream_t st);
+int vec_cg_step(SolveWork& w, int prec, double* x64, const void* dinv, double delta,
+                cudaStream_t st);
+// Reliable-update mixed CG (FP32 recursion, FP64 corrections):
+// start: r32 = r64, x32 = 0, p = Dinv r32, rho, r0 = ||b||, rmax = ||r64||.
+int vec_rel_init(SolveWork& w, const float* dinv, double tol, cudaStream_t st);
+// x64 += x32, x32 = 0 (all rhs).
+int vec_fold(SolveWork& w, double* x64, cudaStream_t st);
+// after r64 = b - K x64: r32 = r64, rho' = r32.Dinv r32, beta = rho'/rho_prev,
+// done = ||r64|| <= tol ||b||, rmax = ||r64||, then p = Dinv r32 + beta p.
+int vec_rel_restart(SolveWork& w, const float* dinv, cudaStream_t st);
 // x64 += s * x32 for rhs still refining.
 int vec_correct(SolveWork& w, double* x64, cudaStream_t st);
 

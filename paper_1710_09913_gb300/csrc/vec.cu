@@ -87,13 +87,16 @@ __device__ bool grid_reduce(const Red& rd, double (&acc)[NV], double* tot) {
 }
 
 __device__ __forceinline__ void set_all_done(const Red& rd, int R) {
-  int all = 1, brk = 0;
+  int all = 1, brk = 0, upd = 0;
   for (int r = 0; r < R; ++r) {
     all &= rd.scal[r].done;
     brk |= rd.scal[r].brk;
+    upd |= rd.scal[r].upd;
   }
-  rd.flags[0] = all;
+  rd.flags[0] = all | upd;  // stop the chunk: finished, or an FP64 correction is due
   rd.flags[1] = brk;
+  rd.flags[2] = all;
+  rd.flags[3] = upd;
   *rd.counter = 0u;
 }
 
@@ -141,7 +144,7 @@ __global__ void __launch_bounds__(kRedThreads) k_update(T* __restrict__ x, T* __
                                                         const T* __restrict__ p,
                                                         const T* __restrict__ q,
                                                         const T* __restrict__ dinv, int64_t N,
-                                                        Red rd) {
+                                                        double delta, Red rd) {
   if (rd.flags[0]) return;
   const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const T al = (T)rd.scal[t0 % R].alpha;
@@ -162,10 +165,12 @@ __global__ void __launch_bounds__(kRedThreads) k_update(T* __restrict__ x, T* __
     if (!s.done) {
       const double rz = tot[threadIdx.x * 2], rr = tot[threadIdx.x * 2 + 1];
       s.beta = rz / s.rho;
+      s.rho_prev = s.rho;
       s.rho = rz;
       s.rr = rr;
       s.iters += 1;
       if (sqrt(rr) <= s.tol * s.r0) s.done = 1;
+      else if (delta > 0.0 && sqrt(rr) < delta * s.rmax) s.upd = 1;
     } else {
       s.beta = 0.0;
     }
@@ -214,8 +219,11 @@ __global__ void __launch_bounds__(kRedThreads) k_init(const T* __restrict__ r, T
     s.r0 = r0_from_bb ? sqrt(s.bb) : sqrt(s.rr);
     s.tol = tol;
     s.alpha = s.beta = s.pq = 0.0;
+    s.rho_prev = s.rho;
+    s.rmax = sqrt(s.rr);
     s.iters = 0;
     s.brk = 0;
+    s.upd = 0;
     s.done = (s.rr == 0.0 || sqrt(s.rr) <= tol * s.r0) ? 1 : 0;
   }
   __syncthreads();
@@ -277,6 +285,58 @@ __global__ void k_correct(double* __restrict__ x64, const float* __restrict__ x3
   for (int64_t i = t0; i < N; i += stride) x64[i] += s.s * (double)x32[i];
 }
 
+// r32 = (float) r64, x32 = 0
+template <int R>
+__global__ void k_narrow(const double* __restrict__ r64, float* __restrict__ r32,
+                         float* __restrict__ x32, int64_t N) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += stride) {
+    r32[i] = (float)r64[i];
+    x32[i] = 0.0f;
+  }
+}
+
+// x64 += x32, x32 = 0
+template <int R>
+__global__ void k_fold(double* __restrict__ x64, float* __restrict__ x32, int64_t N) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += stride) {
+    x64[i] += (double)x32[i];
+    x32[i] = 0.0f;
+  }
+}
+
+// Residual replacement: r32 = r64 (true FP64 residual), rho' = r32.(Dinv r32),
+// beta = rho' / rho_prev; per rhs done iff the true residual meets the tolerance.
+template <int R>
+__global__ void __launch_bounds__(kRedThreads) k_rel_restart(const double* __restrict__ r64,
+                                                             float* __restrict__ r32,
+                                                             const float* __restrict__ dinv,
+                                                             int64_t N, Red rd) {
+  float a0 = 0.0f;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += stride) {
+    const float ri = (float)r64[i];
+    r32[i] = ri;
+    a0 += ri * (dinv[i / R] * ri);
+  }
+  double acc[1] = {(double)a0};
+  __shared__ double tot[R];
+  if (!grid_reduce<R, 1>(rd, acc, tot)) return;
+  if (threadIdx.x < R) {
+    CGScal& s = rd.scal[threadIdx.x];
+    const double rz = tot[threadIdx.x];
+    const double true_rr = s.rr;  // from the FP64 residual kernel just before
+    s.done = (sqrt(true_rr) <= s.tol * s.r0) ? 1 : 0;
+    s.beta = s.done ? 0.0 : rz / s.rho_prev;
+    s.rho = rz;
+    s.rmax = sqrt(true_rr);
+    s.upd = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) set_all_done(rd, R);
+}
+
 Red red_of(SolveWork& w) { return Red{w.partial, w.counter, w.scal, w.flags}; }
 
 #define DOGIP_R_SWITCH(R, CALL) \
@@ -313,11 +373,11 @@ void vec_alloc(SolveWork& w, int64_t n, int R) {
   dm((void**)&w.partial, sizeof(double) * kMaxRedBlocks * 64);
   dm((void**)&w.counter, sizeof(unsigned int) * 4);
   dm((void**)&w.scal, sizeof(CGScal) * 32);
-  dm((void**)&w.flags, sizeof(int) * 4);
+  dm((void**)&w.flags, sizeof(int) * 8);
   cuda_check(cudaMemset(w.counter, 0, sizeof(unsigned int) * 4), "memset counter");
   cuda_check(cudaMemset(w.scal, 0, sizeof(CGScal) * 32), "memset scal");
-  cuda_check(cudaMemset(w.flags, 0, sizeof(int) * 4), "memset flags");
-  if (cudaMallocHost((void**)&w.h_flags, sizeof(int) * 4) != cudaSuccess ||
+  cuda_check(cudaMemset(w.flags, 0, sizeof(int) * 8), "memset flags");
+  if (cudaMallocHost((void**)&w.h_flags, sizeof(int) * 8) != cudaSuccess ||
       cudaMallocHost((void**)&w.h_scal, sizeof(CGScal) * 32) != cudaSuccess) {
     cudaGetLastError();
     fail(DOGIP_ENOMEM, "pinned host allocation failed");
@@ -373,7 +433,8 @@ int vec_init64(SolveWork& w, const double* dinv, double tol, cudaStream_t st) {
   return 1;
 }
 
-int vec_cg_step(SolveWork& w, int prec, double* x64, const void* dinv, cudaStream_t st) {
+int vec_cg_step(SolveWork& w, int prec, double* x64, const void* dinv, double delta,
+                cudaStream_t st) {
   const int64_t N = w.n * w.R;
   Red rd = red_of(w);
   const unsigned nb = red_blocks(N);
@@ -381,7 +442,7 @@ int vec_cg_step(SolveWork& w, int prec, double* x64, const void* dinv, cudaStrea
     const double* di = (const double*)dinv;
 #define CALL(RR)                                                                           \
   k_pq<double, RR><<<nb, kRedThreads, 0, st>>>(w.p64, w.q64, N, rd);                       \
-  k_update<double, RR><<<nb, kRedThreads, 0, st>>>(x64, w.r64, w.p64, w.q64, di, N, rd);   \
+  k_update<double, RR><<<nb, kRedThreads, 0, st>>>(x64, w.r64, w.p64, w.q64, di, N, delta, rd); \
   k_pupdate<double, RR><<<nb, kRedThreads, 0, st>>>(w.p64, w.r64, di, N, w.scal, w.flags)
     DOGIP_R_SWITCH(w.R, CALL);
 #undef CALL
@@ -389,13 +450,48 @@ int vec_cg_step(SolveWork& w, int prec, double* x64, const void* dinv, cudaStrea
     const float* di = (const float*)dinv;
 #define CALL(RR)                                                                           \
   k_pq<float, RR><<<nb, kRedThreads, 0, st>>>(w.p32, w.q32, N, rd);                        \
-  k_update<float, RR><<<nb, kRedThreads, 0, st>>>(w.x32, w.r32, w.p32, w.q32, di, N, rd);  \
+  k_update<float, RR><<<nb, kRedThreads, 0, st>>>(w.x32, w.r32, w.p32, w.q32, di, N, delta, rd); \
   k_pupdate<float, RR><<<nb, kRedThreads, 0, st>>>(w.p32, w.r32, di, N, w.scal, w.flags)
     DOGIP_R_SWITCH(w.R, CALL);
 #undef CALL
   }
   cuda_check(cudaGetLastError(), "cg step kernels");
   return 3;
+}
+
+int vec_rel_init(SolveWork& w, const float* dinv, double tol, cudaStream_t st) {
+  const int64_t N = w.n * w.R;
+  Red rd = red_of(w);
+#define CALL(RR)                                                                             \
+  k_narrow<RR><<<red_blocks(N), kRedThreads, 0, st>>>(w.r64, w.r32, w.x32, N);               \
+  k_init<float, RR><<<red_blocks(N), kRedThreads, 0, st>>>(w.r32, w.p32, w.x32, dinv, N, tol, \
+                                                            1, 0, rd)
+  DOGIP_R_SWITCH(w.R, CALL);
+#undef CALL
+  cuda_check(cudaGetLastError(), "reliable init kernels");
+  return 2;
+}
+
+int vec_fold(SolveWork& w, double* x64, cudaStream_t st) {
+  const int64_t N = w.n * w.R;
+#define CALL(RR) k_fold<RR><<<red_blocks(N), kRedThreads, 0, st>>>(x64, w.x32, N)
+  DOGIP_R_SWITCH(w.R, CALL);
+#undef CALL
+  cuda_check(cudaGetLastError(), "fold kernel");
+  return 1;
+}
+
+int vec_rel_restart(SolveWork& w, const float* dinv, cudaStream_t st) {
+  const int64_t N = w.n * w.R;
+  Red rd = red_of(w);
+#define CALL(RR)                                                                              \
+  k_rel_restart<RR><<<red_blocks(N), kRedThreads, 0, st>>>(w.r64, w.r32, dinv, N, rd);        \
+  k_pupdate<float, RR><<<red_blocks(N), kRedThreads, 0, st>>>(w.p32, w.r32, dinv, N, w.scal,  \
+                                                               w.flags)
+  DOGIP_R_SWITCH(w.R, CALL);
+#undef CALL
+  cuda_check(cudaGetLastError(), "reliable restart kernels");
+  return 2;
 }
 
 int vec_correct(SolveWork& w, double* x64, cudaStream_t st) {
