@@ -75,10 +75,10 @@ extern "C" {
 #define DOGIP_SCATTER_COLOUR 1 /* one pass per element colour, plain adds      */
 
 #define DOGIP_SOLVE_FP64 0  /* FP64 Jacobi-PCG                                 */
-#define DOGIP_SOLVE_MIXED 1 /* FP32 PCG with FP64 residual replacement (reliable
-                               updates): one Krylov sequence, FP64 solution     */
-#define DOGIP_SOLVE_MIXED_RESTART 2 /* FP64 iterative refinement around restarted
-                                       FP32 PCG solves of K d = r / ||r||       */
+#define DOGIP_SOLVE_MIXED 1 /* FP64 iterative refinement around restarted FP32
+                               PCG solves of K d = r / ||r||                   */
+#define DOGIP_SOLVE_MIXED_RELIABLE 2 /* one FP32 PCG recursion with FP64 residual
+                                        replacement (reliable updates)        */
 
 typedef struct dogip_ctx dogip_ctx;
 
@@ -210,8 +210,8 @@ typedef struct {
                          convergence checks (>= 1)                             */
   int use_x0;         /* 1: u holds the initial guess; 0: start from u = 0     */
   double timeout_ms;  /* host wall-clock limit, <= 0 for none                  */
-  double reliable_delta; /* MIXED: FP64 correction when the FP32 residual has
-                            dropped by this factor since the last one (0.1)   */
+  double reliable_delta; /* MIXED_RELIABLE: FP64 correction when the FP32
+                            residual has dropped by this factor (0.1)         */
 } dogip_solve_opts;
 
 typedef struct {
@@ -229,12 +229,12 @@ DOGIP_API int dogip_solve_opts_default(dogip_solve_opts* o);
  * A_T).  b, u: DEVICE double [n_dofs x nrhs]; nrhs in {1, 2, 4, 8, 16, 32}.
  * FP64 mode: PCG until the recursive residual reaches tol, then the true
  * residual is evaluated in FP64 (restarting from it if the recursion drifted).
- * MIXED: one PCG recursion in FP32 (A_T, vectors, applies); whenever its residual
- * has dropped by reliable_delta, the FP32 iterate is folded into the FP64
- * solution, r = b - K u is recomputed in FP64 and replaces the FP32 residual
- * (the search direction is kept); convergence is decided on that FP64 residual.
- * MIXED_RESTART: r = b - K u, norms and u += s d in FP64 around restarted FP32
- * PCG solves of K d = r / s.
+ * MIXED: r = b - K u, norms and u += s d in FP64 around restarted FP32 PCG
+ * solves of K d = r / s (inner_tol, inner_maxiter, max_outer).
+ * MIXED_RELIABLE: one PCG recursion in FP32; whenever its residual has dropped
+ * by reliable_delta, the FP32 iterate is folded into the FP64 solution and
+ * r = b - K u, recomputed in FP64, replaces the FP32 residual (the search
+ * direction is kept); convergence is decided on that FP64 residual.
  * rel_residual_per_rhs: host [nrhs] or NULL.  Returns ENOTCONV (u written)
  * when the limits are reached first.  Synchronises cuda_stream.
  */

@@ -21,11 +21,11 @@ PROJECTION, ELLIPTIC = 0, 1
 COEF_ELEM_SCALAR, COEF_ELEM_TENSOR = 0, 1
 FP64, FP32 = 0, 1
 SCATTER_ATOMIC, SCATTER_COLOUR = 0, 1
-SOLVE_FP64, SOLVE_MIXED, SOLVE_MIXED_RESTART = 0, 1, 2
+SOLVE_FP64, SOLVE_MIXED, SOLVE_MIXED_RELIABLE = 0, 1, 2
 FORMS = {"projection": PROJECTION, "elliptic": ELLIPTIC}
 PRECS = {"fp64": FP64, "fp32": FP32}
 SCATTERS = {"atomic": SCATTER_ATOMIC, "colour": SCATTER_COLOUR, None: -1}
-MODES = {"fp64": SOLVE_FP64, "mixed": SOLVE_MIXED, "mixed_restart": SOLVE_MIXED_RESTART}
+MODES = {"fp64": SOLVE_FP64, "mixed": SOLVE_MIXED, "mixed_reliable": SOLVE_MIXED_RELIABLE}
 
 
 class DogipError(RuntimeError):

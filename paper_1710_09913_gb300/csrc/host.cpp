@@ -514,10 +514,10 @@ int solve(Ctx& c, const double* b, double* u, int R, const dogip_solve_opts* opt
   if (opts) o = *opts;
   if (!b || !u) fail(DOGIP_EINVAL, "b and u are required");
   if (!r_ok(R)) fail(DOGIP_EINVAL, "nrhs must be 1, 2, 4, 8, 16 or 32 for solves");
-  if (o.mode != DOGIP_SOLVE_FP64 && o.mode != DOGIP_SOLVE_MIXED && o.mode != DOGIP_SOLVE_MIXED_RESTART)
+  if (o.mode != DOGIP_SOLVE_FP64 && o.mode != DOGIP_SOLVE_MIXED && o.mode != DOGIP_SOLVE_MIXED_RELIABLE)
     fail(DOGIP_EINVAL, "unknown mode");
   if (o.mode != DOGIP_SOLVE_FP64 && !c.keep32) fail(DOGIP_EINVAL, "mixed modes need keep_fp32");
-  if (o.mode == DOGIP_SOLVE_MIXED && !(o.reliable_delta > 0.0 && o.reliable_delta < 1.0))
+  if (o.mode == DOGIP_SOLVE_MIXED_RELIABLE && !(o.reliable_delta > 0.0 && o.reliable_delta < 1.0))
     fail(DOGIP_EINVAL, "reliable_delta must lie in (0, 1)");
   if (!(o.tol > 0.0)) fail(DOGIP_EINVAL, "tol must be positive");
   int scatter = o.scatter < 0 ? c.scatter : o.scatter;
@@ -575,7 +575,7 @@ int solve(Ctx& c, const double* b, double* u, int R, const dogip_solve_opts* opt
         break;
       }
     }
-  } else if (o.mode == DOGIP_SOLVE_MIXED) {
+  } else if (o.mode == DOGIP_SOLVE_MIXED_RELIABLE) {
     // Reliable-update PCG: FP32 recursion, FP64 residual replacement.
     if (o.use_x0) launch_apply(c, u, w.q64, R, DOGIP_FP64, scatter, s, nullptr);
     else cuda_check(cudaMemsetAsync(w.q64, 0, bytes, s), "zero q");
