@@ -274,6 +274,33 @@ DOGIP_API int dogip_grad_coef(dogip_ctx* ctx, const double* u, const double* lam
  */
 DOGIP_API int dogip_check(dogip_ctx* ctx, void* cuda_stream);
 
+/* ----------------------------------------------------- allocation-free norms */
+/*
+ * FP64 residual norms that allocate nothing.  The paper has no counterpart: this
+ * is a service of the library for callers that cannot allocate device memory --
+ * a framework whose allocator owns all device memory and forbids raw cudaMalloc,
+ * a latency-critical loop that cannot afford cudaMalloc/cudaFree (cudaFree
+ * synchronises the device), a process held to a fixed device-memory budget.
+ * It computes, with the same fused reduction as dogip_solve's residual check,
+ *     r = b - Ky,   rel[k] = ||r_k||_2 / ||b_k||_2   (0 where b_k = 0),
+ * for Ky = dogip_apply(u): rel is exactly the relative residual dogip_solve reports.
+ *   b, Ky : DEVICE double [n x nrhs] (dof-major); r: DEVICE [n x nrhs] or NULL;
+ *   rel   : DEVICE double [nrhs];  1 <= nrhs <= 32 (else DOGIP_EINVAL).
+ * No context is needed.  The reduction scratch is a fixed 128 KiB + 256 B array in
+ * the library's device memory, present on every GPU that loads the library until
+ * the process exits; no cudaMalloc, cudaFree or allocating library routine is
+ * called.  The first call on a device resolves the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call before
+ * any stream capture.  Every call shares the array and leaves it holding its last
+ * contents (the ticket counter is cleared at the start of each call), so calls
+ * whose work overlaps on the GPU -- on different streams, or from different host
+ * threads -- race with each other and must be serialised by the caller.
+ * Asynchronous on cuda_stream.
+ */
+DOGIP_API int dogip_residual_norms_noalloc(const double* b, const double* Ky, double* r,
+                                           int64_t n, int nrhs, double* rel,
+                                           void* cuda_stream);
+
 /* ------------------------------------------------------------------ errors */
 DOGIP_API const char* dogip_last_error(void); /* thread-local, never NULL */
 DOGIP_API int dogip_version(void);            /* major * 10000 + minor * 100 + patch */

@@ -101,6 +101,7 @@ _SIGS = {
                                    C.POINTER(SolveInfo), _vp, _vp]),
     "dogip_grad_coef": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "dogip_check": (C.c_int, [_vp, _vp]),
+    "dogip_residual_norms_noalloc": (C.c_int, [_vp, _vp, _vp, C.c_int64, C.c_int, _vp, _vp]),
     "dogip_last_error": (C.c_char_p, []),
     "dogip_version": (C.c_int, []),
 }
@@ -135,6 +136,20 @@ def _dptr(t, dtype=None):
 
 def _hptr(a, ctype):
     return a.ctypes.data_as(C.POINTER(ctype))
+
+
+def residual_norms_noalloc(b, Ky, r=None, rel=None, stream=None):
+    """||b - Ky|| / ||b|| per rhs on the device without any allocation by the
+    library (b, Ky: float64 CUDA [n] or [n, R]); returns rel (float64 CUDA [R])."""
+    import torch
+    R = 1 if b.dim() == 1 else b.shape[1]
+    if rel is None:
+        rel = torch.empty(R, dtype=torch.float64, device=b.device)
+    rp = _dptr(r, torch.float64) if r is not None else None
+    _check(lib.dogip_residual_norms_noalloc(_dptr(b, torch.float64), _dptr(Ky, torch.float64), rp,
+                                            b.shape[0], R, _dptr(rel, torch.float64),
+                                            _stream(stream)))
+    return rel
 
 
 def get_tables(dim, p, form):

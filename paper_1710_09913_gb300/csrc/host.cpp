@@ -19,6 +19,8 @@ thread_local std::string g_last_error;
 
 void fail(int code, const std::string& msg) { throw Failure{code, msg}; }
 
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
 void cuda_check(cudaError_t e, const char* what) {
   if (e != cudaSuccess) {
     cudaGetLastError();

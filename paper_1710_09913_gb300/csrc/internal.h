@@ -108,6 +108,7 @@ struct Failure {
 };
 
 [[noreturn]] void fail(int code, const std::string& msg);
+void set_last_error(const std::string& msg);  // message of dogip_last_error()
 void cuda_check(cudaError_t e, const char* what);
 
 // ---- kernel launchers (implemented in the .cu translation units) ----------
