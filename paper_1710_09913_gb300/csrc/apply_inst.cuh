@@ -51,7 +51,7 @@ const TmaLaunch& tma_launch() {
 
 template <int D, int P, int FORM, typename T>
 void run_apply_tma(const T* A, const Ctx& c, const void* u, void* y, int R, cudaStream_t s,
-                   const int* skip) {
+                   const int* skip, SolveWork* fuse) {
   using Cfg = TmaCfg<D, P, FORM, T>;
   auto kern = k_apply_tma<D, P, FORM, T>;
   const TmaLaunch& L = tma_launch<D, P, FORM, T>();
@@ -60,39 +60,49 @@ void run_apply_tma(const T* A, const Ctx& c, const void* u, void* y, int R, cuda
   const int64_t nchunks = (ntiles + Cfg::TPC - 1) / Cfg::TPC;
   if (nchunks == 0) return;
   const int64_t grid = std::min<int64_t>(nchunks, (int64_t)num_sms * blocks_per_sm);
-  TmaArgs<T> a{A, c.d_conn, (const T*)u, (T*)y, c.E, ntiles, nchunks, R, skip, c.d_kerr};
+  TmaArgs<T> a{A, c.d_conn, (const T*)u, (T*)y, c.E, ntiles, nchunks, R, skip, c.d_kerr,
+                c.d_bnd, c.dirichlet ? c.nbnd : 0,
+                fuse ? fuse->partial : nullptr, fuse ? fuse->counter : nullptr,
+                fuse ? fuse->scal : nullptr, fuse ? fuse->flags : nullptr};
   kern<<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
 }
 
+// Returns 2 when the staged kernel ran (it also wrote the Dirichlet rows and, with
+// `fuse`, the CG scalars), 1 for the one-thread-per-cell kernel.
 template <int D, int P, int FORM>
-void run_apply(const Ctx& c, const void* u, void* y, int R, int prec, bool atomic, int64_t e0,
-               int64_t e1, cudaStream_t s, const int* skip) {
+int run_apply(const Ctx& c, const void* u, void* y, int R, int prec, bool atomic, int64_t e0,
+              int64_t e1, cudaStream_t s, const int* skip, SolveWork* fuse) {
   constexpr bool ok64 = TmaCfg<D, P, FORM, double>::OK, ok32 = TmaCfg<D, P, FORM, float>::OK;
   if (u == nullptr) {  // preparation call from context set-up
     if constexpr (ok64) tma_launch<D, P, FORM, double>();
     if constexpr (ok32) tma_launch<D, P, FORM, float>();
-    return;
+    return 1;
   }
   const bool whole = atomic && e0 == 0 && e1 == c.E && c.apply_variant == 1;
   if (prec == DOGIP_FP64) {
     if constexpr (ok64) {
-      if (whole) return run_apply_tma<D, P, FORM, double>(c.d_A64, c, u, y, R, s, skip);
+      if (whole) {
+        run_apply_tma<D, P, FORM, double>(c.d_A64, c, u, y, R, s, skip, fuse);
+        return 2;
+      }
     }
     run_apply_t<D, P, FORM, double>(c.d_A64, c, u, y, R, atomic, e0, e1, s, skip);
   } else {
     if constexpr (ok32) {
-      if (whole) return run_apply_tma<D, P, FORM, float>(c.d_A32, c, u, y, R, s, skip);
+      if (whole) {
+        run_apply_tma<D, P, FORM, float>(c.d_A32, c, u, y, R, s, skip, fuse);
+        return 2;
+      }
     }
     run_apply_t<D, P, FORM, float>(c.d_A32, c, u, y, R, atomic, e0, e1, s, skip);
   }
+  return 1;
 }
 
 }  // namespace dogip
 
 #define DOGIP_APPLY_CASES(D, P)                                              \
   case P * 2 + 0:                                                            \
-    run_apply<D, P, 0>(c, u, y, R, prec, atomic, e0, e1, s, skip);          \
-    return true;                                                             \
+    return run_apply<D, P, 0>(c, u, y, R, prec, atomic, e0, e1, s, skip, fuse); \
   case P * 2 + 1:                                                            \
-    run_apply<D, P, 1>(c, u, y, R, prec, atomic, e0, e1, s, skip);          \
-    return true;
+    return run_apply<D, P, 1>(c, u, y, R, prec, atomic, e0, e1, s, skip, fuse);

@@ -451,11 +451,11 @@ void run_chunk(Ctx& c, int prec, int scatter, double* x64, int k, double delta) 
     try {
       for (int it = 0; it < k; ++it) {
         if (prec == DOGIP_FP64) {
-          launch_apply(c, w.p64, w.q64, w.R, DOGIP_FP64, scatter, s, w.flags);
-          c.launches += vec_cg_step(w, DOGIP_FP64, x64, c.d_dinv64, delta, s);
+          const bool fused = launch_apply_cg(c, w.p64, w.q64, w.R, DOGIP_FP64, scatter, s, w);
+          c.launches += vec_cg_step(w, DOGIP_FP64, x64, c.d_dinv64, delta, s, fused);
         } else {
-          launch_apply(c, w.p32, w.q32, w.R, DOGIP_FP32, scatter, s, w.flags);
-          c.launches += vec_cg_step(w, DOGIP_FP32, nullptr, c.d_dinv32, delta, s);
+          const bool fused = launch_apply_cg(c, w.p32, w.q32, w.R, DOGIP_FP32, scatter, s, w);
+          c.launches += vec_cg_step(w, DOGIP_FP32, nullptr, c.d_dinv32, delta, s, fused);
         }
       }
       cuda_check(cudaMemcpyAsync(w.h_flags, w.flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, s),

@@ -279,7 +279,70 @@ struct TmaArgs {
   int R;
   const int* skip;
   int* err;
+  const int32_t* bnd;  // Dirichlet dofs: y_b = u_b is written here (no extra kernel)
+  int64_t nbnd;
+  // Optional fused CG step (all null outside solves): p.q = u^T K u from the element
+  // energies sum_j g_j . h_j plus sum_b u_b^2, reduced over the grid; the last
+  // block sets alpha = rho / p.q per rhs.
+  double* partial;
+  unsigned int* counter;
+  CGScal* scal;
+  int* flags;
 };
+
+// Grid reduction of the per-block energies s_en[0..R) and, in the last block to
+// finish, alpha = rho / p.q per rhs (breakdown if p.q <= 0), then the stop flags.
+static __device__ __noinline__ void fused_alpha(double* partial, unsigned int* counter, CGScal* scal,
+                                         int* flags, int R, double* s_en) {
+  __shared__ bool last;
+  __shared__ double fin[256];
+  __syncthreads();
+  if (threadIdx.x < R) partial[(size_t)blockIdx.x * 64 + threadIdx.x] = s_en[threadIdx.x];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int G = blockDim.x / R;  // R is a power of two dividing the block
+  const int k = threadIdx.x % R, g = threadIdx.x / R;
+  double acc = 0.0;
+  if (g < G)
+    for (unsigned b = g; b < gridDim.x; b += G) acc += __ldcg(partial + (size_t)b * 64 + k);
+  fin[threadIdx.x] = acc;
+  __syncthreads();
+  for (int off = G / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off * R) fin[threadIdx.x] += fin[threadIdx.x + off * R];
+    __syncthreads();
+  }
+  if (threadIdx.x < R) {
+    CGScal& s = scal[threadIdx.x];
+    const double v = fin[threadIdx.x];
+    if (s.done) {
+      s.alpha = 0.0;
+    } else if (!(v > 0.0) || !isfinite(v)) {
+      s.brk = 1;
+      s.done = 1;
+      s.alpha = 0.0;
+    } else {
+      s.pq = v;
+      s.alpha = s.rho / v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int all = 1, brk = 0;
+    for (int r = 0; r < R; ++r) {
+      all &= scal[r].done;
+      brk |= scal[r].brk;
+    }
+    flags[0] = all;
+    flags[1] = brk;
+    flags[2] = all;
+    flags[3] = 0;
+    *counter = 0u;
+  }
+}
 
 template <int D, int P, int FORM, typename T>
 __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T>::THREADS)
@@ -295,6 +358,9 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T>::THREADS)
   if (a.skip != nullptr && *a.skip) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t G = gridDim.x;
+  const bool fused = a.partial != nullptr;
+  __shared__ double s_en[32];
+  if (tid < 32) s_en[tid] = 0.0;
   if (tid == 0) {
     for (int s = 0; s < C::S; ++s) mbar_init(&bars[s], 1);
     mbar_fence_init();
@@ -338,6 +404,7 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T>::THREADS)
       });
       for (int r = 0; r < a.R; ++r) {
         T ul[V], Y[V];
+        T en = T(0);
         static_for<V>([&](auto lc) {
           constexpr int l = decltype(lc)::value;
           ul[l] = (c[l] & kBndBit) ? T(0) : __ldg(a.u + (int64_t)(c[l] & kIdMask) * a.R + r);
@@ -352,12 +419,19 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T>::THREADS)
           });
           interp<TB, j>(ul, g);
           block_mul<D, FORM>(aj, g, h);
+          if (fused) {
+            static_for<NB>([&](auto rc) {
+              constexpr int rr = decltype(rc)::value;
+              en = fma(g[rr], h[rr], en);
+            });
+          }
           project<TB, j>(h, Y);
         });
         static_for<V>([&](auto lc) {
           constexpr int l = decltype(lc)::value;
           if (!(c[l] & kBndBit)) atomicAdd(a.y + (int64_t)(c[l] & kIdMask) * a.R + r, Y[l]);
         });
+        if (fused) atomicAdd(&s_en[r], (double)en);
       }
     }
     __syncthreads();  // every read of stage s is done
@@ -377,6 +451,16 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T>::THREADS)
     }
     __syncthreads();
   }
+  // Dirichlet rows: y_b = u_b (the scatter skipped them), and u_b^2 for p.q
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + tid; t < a.nbnd * a.R;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t % a.R);
+    const int64_t idx = (int64_t)a.bnd[t / a.R] * a.R + r;
+    const T ub = a.u[idx];
+    a.y[idx] = ub;
+    if (fused) atomicAdd(&s_en[r], (double)ub * (double)ub);
+  }
+  if (fused) fused_alpha(a.partial, a.counter, a.scal, a.flags, a.R, s_en);
 }
 
 // ------------------------------------------------------------------ setup

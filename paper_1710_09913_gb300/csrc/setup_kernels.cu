@@ -6,12 +6,24 @@
 
 namespace dogip {
 
-bool apply_d2(const Ctx&, const void*, void*, int, int, bool, int64_t, int64_t, cudaStream_t,
-              const int*);
-bool apply_d3a(const Ctx&, const void*, void*, int, int, bool, int64_t, int64_t, cudaStream_t,
-               const int*);
-bool apply_d3b(const Ctx&, const void*, void*, int, int, bool, int64_t, int64_t, cudaStream_t,
-               const int*);
+// Apply dispatchers (apply_d*.cu): 0 = not compiled, 1 = per-cell kernel, 2 = staged
+// kernel (which also wrote the Dirichlet rows and, with `fuse`, the CG scalars).
+int apply_d2(const Ctx&, const void*, void*, int, int, bool, int64_t, int64_t, cudaStream_t,
+             const int*, SolveWork*);
+int apply_d3a(const Ctx&, const void*, void*, int, int, bool, int64_t, int64_t, cudaStream_t,
+              const int*, SolveWork*);
+int apply_d3b(const Ctx&, const void*, void*, int, int, bool, int64_t, int64_t, cudaStream_t,
+              const int*, SolveWork*);
+
+namespace {
+int apply_dispatch(const Ctx& c, const void* u, void* y, int R, int prec, bool atomic, int64_t e0,
+                   int64_t e1, cudaStream_t s, const int* skip, SolveWork* fuse) {
+  if (c.d == 2) return apply_d2(c, u, y, R, prec, atomic, e0, e1, s, skip, fuse);
+  if (c.p <= 2) return apply_d3a(c, u, y, R, prec, atomic, e0, e1, s, skip, fuse);
+  if (c.p == 3) return apply_d3b(c, u, y, R, prec, atomic, e0, e1, s, skip, fuse);
+  return 0;
+}
+}  // namespace
 
 __global__ void k_export_ahat(const double* A, const int64_t* perm, double* out, int64_t E,
                               int nsw) {
@@ -176,24 +188,37 @@ void launch_dirichlet_copy(const Ctx& c, const void* u, void* y, int R, int prec
 }
 
 void prepare_apply(Ctx& c) {
-  bool ok;
-  if (c.d == 2) ok = apply_d2(c, nullptr, nullptr, 1, 0, true, 0, 0, nullptr, nullptr);
-  else if (c.p <= 2) ok = apply_d3a(c, nullptr, nullptr, 1, 0, true, 0, 0, nullptr, nullptr);
-  else ok = apply_d3b(c, nullptr, nullptr, 1, 0, true, 0, 0, nullptr, nullptr);
-  if (!ok) fail(DOGIP_EUNSUPPORTED, "no compiled apply instance for this (dim, p, form)");
+  if (!apply_dispatch(c, nullptr, nullptr, 1, 0, true, 0, 0, nullptr, nullptr, nullptr))
+    fail(DOGIP_EUNSUPPORTED, "no compiled apply instance for this (dim, p, form)");
+}
+
+bool launch_apply_cg(Ctx& c, const void* p, void* q, int R, int prec, int scatter, cudaStream_t s,
+                     SolveWork& w) {
+  if (scatter == DOGIP_SCATTER_ATOMIC) {
+    const int k = apply_dispatch(c, p, q, R, prec, true, 0, c.E, s, w.flags, &w);
+    if (!k) fail(DOGIP_EUNSUPPORTED, "no compiled apply instance for this (dim, p, form)");
+    cuda_check(cudaGetLastError(), "apply kernel launch");
+    c.launches += 1;
+    if (k == 2) return true;
+    if (c.dirichlet && c.nbnd > 0) {
+      launch_dirichlet_copy(c, p, q, R, prec, s, w.flags);
+      c.launches += 1;
+    }
+    return false;
+  }
+  launch_apply(c, p, q, R, prec, scatter, s, w.flags);  // colour passes (memset inside)
+  return false;
 }
 
 void launch_apply(Ctx& c, const void* u, void* y, int R, int prec, int scatter, cudaStream_t s,
                   const int* skip) {
   const size_t es = prec == DOGIP_FP64 ? sizeof(double) : sizeof(float);
   cuda_check(cudaMemsetAsync(y, 0, es * c.n * R, s), "memset y");
+  bool staged = false;
   auto run = [&](bool atomic, int64_t e0, int64_t e1) {
-    bool ok;
-    if (c.d == 2) ok = apply_d2(c, u, y, R, prec, atomic, e0, e1, s, skip);
-    else if (c.p <= 2) ok = apply_d3a(c, u, y, R, prec, atomic, e0, e1, s, skip);
-    else if (c.p == 3) ok = apply_d3b(c, u, y, R, prec, atomic, e0, e1, s, skip);
-    else ok = false;
-    if (!ok) fail(DOGIP_EUNSUPPORTED, "no compiled apply instance for this (dim, p, form)");
+    const int k = apply_dispatch(c, u, y, R, prec, atomic, e0, e1, s, skip, nullptr);
+    if (!k) fail(DOGIP_EUNSUPPORTED, "no compiled apply instance for this (dim, p, form)");
+    staged = staged || k == 2;
   };
   if (scatter == DOGIP_SCATTER_COLOUR) {
     for (int k = 0; k < c.ncolours; ++k) run(false, c.colour_start[k], c.colour_start[k + 1]);
@@ -202,7 +227,7 @@ void launch_apply(Ctx& c, const void* u, void* y, int R, int prec, int scatter, 
     run(true, 0, c.E);
     c.launches += 1;
   }
-  if (c.dirichlet && c.nbnd > 0) {
+  if (c.dirichlet && c.nbnd > 0 && !staged) {
     launch_dirichlet_copy(c, u, y, R, prec, s, skip);
     c.launches += 1;
   }

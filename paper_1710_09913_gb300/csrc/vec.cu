@@ -179,17 +179,20 @@ __global__ void __launch_bounds__(kRedThreads) k_update(T* __restrict__ x, T* __
   if (threadIdx.x == 0) set_all_done(rd, R);
 }
 
-// p = Dinv r + beta p
+// p = Dinv r + beta p; also clears q (when given) for the next scatter-add apply
 template <typename T, int R>
 __global__ void __launch_bounds__(kRedThreads) k_pupdate(T* __restrict__ p, const T* __restrict__ r,
                                                          const T* __restrict__ dinv, int64_t N,
-                                                         const CGScal* scal, const int* flags) {
+                                                         const CGScal* scal, const int* flags,
+                                                         T* __restrict__ qzero) {
   if (flags[0]) return;
   const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if (qzero != nullptr)
+    for (int64_t i = t0; i < N; i += stride) qzero[i] = T(0);
   const CGScal& s = scal[t0 % R];
   if (s.done) return;
   const T be = (T)s.beta;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = t0; i < N; i += stride) p[i] = dinv[i / R] * r[i] + be * p[i];
 }
 
@@ -198,13 +201,14 @@ template <typename T, int R>
 __global__ void __launch_bounds__(kRedThreads) k_init(const T* __restrict__ r, T* __restrict__ p,
                                                       T* __restrict__ x, const T* __restrict__ dinv,
                                                       int64_t N, double tol, int r0_from_bb,
-                                                      int zero_x, Red rd) {
+                                                      int zero_x, T* __restrict__ qzero, Red rd) {
   T a0 = T(0), a1 = T(0);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += stride) {
     const T ri = r[i];
     const T zi = dinv[i / R] * ri;
     p[i] = zi;
+    qzero[i] = T(0);
     if (zero_x) x[i] = T(0);
     a0 += ri * zi;
     a1 += ri * ri;
@@ -415,7 +419,7 @@ int vec_inner_init32(SolveWork& w, const float* dinv, double inner_tol, cudaStre
 #define CALL(RR)                                                                              \
   k_to32<RR><<<red_blocks(N), kRedThreads, 0, st>>>(w.r64, w.r32, w.x32, N, w.scal);          \
   k_init<float, RR><<<red_blocks(N), kRedThreads, 0, st>>>(w.r32, w.p32, w.x32, dinv, N,       \
-                                                            inner_tol, 0, 0, rd)
+                                                            inner_tol, 0, 0, w.q32, rd)
   DOGIP_R_SWITCH(w.R, CALL);
 #undef CALL
   cuda_check(cudaGetLastError(), "inner init kernels");
@@ -426,7 +430,8 @@ int vec_init64(SolveWork& w, const double* dinv, double tol, cudaStream_t st) {
   const int64_t N = w.n * w.R;
   Red rd = red_of(w);
 #define CALL(RR) \
-  k_init<double, RR><<<red_blocks(N), kRedThreads, 0, st>>>(w.r64, w.p64, w.x64, dinv, N, tol, 1, 0, rd)
+  k_init<double, RR><<<red_blocks(N), kRedThreads, 0, st>>>(w.r64, w.p64, w.x64, dinv, N, tol, 1, 0, \
+                                                             w.q64, rd)
   DOGIP_R_SWITCH(w.R, CALL);
 #undef CALL
   cuda_check(cudaGetLastError(), "init kernel");
@@ -434,29 +439,31 @@ int vec_init64(SolveWork& w, const double* dinv, double tol, cudaStream_t st) {
 }
 
 int vec_cg_step(SolveWork& w, int prec, double* x64, const void* dinv, double delta,
-                cudaStream_t st) {
+                cudaStream_t st, bool pq_fused) {
   const int64_t N = w.n * w.R;
   Red rd = red_of(w);
   const unsigned nb = red_blocks(N);
   if (prec == DOGIP_FP64) {
     const double* di = (const double*)dinv;
 #define CALL(RR)                                                                           \
-  k_pq<double, RR><<<nb, kRedThreads, 0, st>>>(w.p64, w.q64, N, rd);                       \
+  if (!pq_fused) k_pq<double, RR><<<nb, kRedThreads, 0, st>>>(w.p64, w.q64, N, rd);        \
   k_update<double, RR><<<nb, kRedThreads, 0, st>>>(x64, w.r64, w.p64, w.q64, di, N, delta, rd); \
-  k_pupdate<double, RR><<<nb, kRedThreads, 0, st>>>(w.p64, w.r64, di, N, w.scal, w.flags)
+  k_pupdate<double, RR><<<nb, kRedThreads, 0, st>>>(w.p64, w.r64, di, N, w.scal, w.flags,  \
+                                                     pq_fused ? w.q64 : nullptr)
     DOGIP_R_SWITCH(w.R, CALL);
 #undef CALL
   } else {
     const float* di = (const float*)dinv;
 #define CALL(RR)                                                                           \
-  k_pq<float, RR><<<nb, kRedThreads, 0, st>>>(w.p32, w.q32, N, rd);                        \
+  if (!pq_fused) k_pq<float, RR><<<nb, kRedThreads, 0, st>>>(w.p32, w.q32, N, rd);         \
   k_update<float, RR><<<nb, kRedThreads, 0, st>>>(w.x32, w.r32, w.p32, w.q32, di, N, delta, rd); \
-  k_pupdate<float, RR><<<nb, kRedThreads, 0, st>>>(w.p32, w.r32, di, N, w.scal, w.flags)
+  k_pupdate<float, RR><<<nb, kRedThreads, 0, st>>>(w.p32, w.r32, di, N, w.scal, w.flags,   \
+                                                    pq_fused ? w.q32 : nullptr)
     DOGIP_R_SWITCH(w.R, CALL);
 #undef CALL
   }
   cuda_check(cudaGetLastError(), "cg step kernels");
-  return 3;
+  return pq_fused ? 2 : 3;
 }
 
 int vec_rel_init(SolveWork& w, const float* dinv, double tol, cudaStream_t st) {
@@ -465,7 +472,7 @@ int vec_rel_init(SolveWork& w, const float* dinv, double tol, cudaStream_t st) {
 #define CALL(RR)                                                                             \
   k_narrow<RR><<<red_blocks(N), kRedThreads, 0, st>>>(w.r64, w.r32, w.x32, N);               \
   k_init<float, RR><<<red_blocks(N), kRedThreads, 0, st>>>(w.r32, w.p32, w.x32, dinv, N, tol, \
-                                                            1, 0, rd)
+                                                            1, 0, w.q32, rd)
   DOGIP_R_SWITCH(w.R, CALL);
 #undef CALL
   cuda_check(cudaGetLastError(), "reliable init kernels");
@@ -487,7 +494,7 @@ int vec_rel_restart(SolveWork& w, const float* dinv, cudaStream_t st) {
 #define CALL(RR)                                                                              \
   k_rel_restart<RR><<<red_blocks(N), kRedThreads, 0, st>>>(w.r64, w.r32, dinv, N, rd);        \
   k_pupdate<float, RR><<<red_blocks(N), kRedThreads, 0, st>>>(w.p32, w.r32, dinv, N, w.scal,  \
-                                                               w.flags)
+                                                               w.flags, w.q32)
   DOGIP_R_SWITCH(w.R, CALL);
 #undef CALL
   cuda_check(cudaGetLastError(), "reliable restart kernels");
