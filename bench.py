@@ -211,6 +211,76 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------- assembled CSR baseline
+
+
+def csr_operator(ctx, B):
+    """Assembled CSR matrix of the same operator on the GPU (comparison only): element
+    matrices K_T = B^T A_T B from the library's A_T and tables, summed into CSR by
+    torch (coalesce), Dirichlet rows/columns replaced by the identity."""
+    import torch
+    Bh, _ = B.get_tables(ctx.d, ctx.p, ctx.form)
+    Bt = torch.tensor(Bh, device="cuda")                       # [NB, W, V]
+    Ah = ctx.ahat()                                            # [E, W, n_sym]
+    d = ctx.d
+    if ctx.form == "projection":
+        Ke = torch.einsum("jk,ej,jl->ekl", Bt[0], Ah[:, :, 0], Bt[0])
+    else:
+        idx = [(r, s) for r in range(d) for s in range(r, d)]
+        Afull = torch.zeros(Ah.shape[0], Ah.shape[1], d, d, dtype=Ah.dtype, device="cuda")
+        for k, (r, s_) in enumerate(idx):
+            Afull[:, :, r, s_] = Ah[:, :, k]
+            Afull[:, :, s_, r] = Ah[:, :, k]
+        Ke = torch.einsum("rjk,ejrs,sjl->ekl", Bt, Afull, Bt)
+        del Afull
+    conn = torch.tensor(ctx.dofmap(), device="cuda", dtype=torch.int64)
+    V = conn.shape[1]
+    rows = conn[:, :, None].expand(-1, V, V).reshape(-1)
+    cols = conn[:, None, :].expand(-1, V, V).reshape(-1)
+    vals = Ke.reshape(-1)
+    del Ke
+    bnd = torch.tensor(ctx.boundary(), device="cuda")
+    if bnd.any():
+        keep = ~(bnd[rows] | bnd[cols])
+        rows, cols, vals = rows[keep], cols[keep], vals[keep]
+        bi = torch.nonzero(bnd).flatten()
+        rows = torch.cat([rows, bi])
+        cols = torch.cat([cols, bi])
+        vals = torch.cat([vals, torch.ones_like(bi, dtype=vals.dtype)])
+    K = torch.sparse_coo_tensor(torch.stack([rows, cols]), vals, (ctx.n, ctx.n)).coalesce()
+    return K.to_sparse_csr()
+
+
+def csr_pcg(K, b, tol, maxiter=200000, check=50):
+    """Jacobi-PCG with torch ops around cuSPARSE SpMV; returns (x, iterations)."""
+    import torch
+    crow, col, val = K.crow_indices(), K.col_indices(), K.values()
+    rid = torch.repeat_interleave(torch.arange(K.shape[0], device="cuda"), crow[1:] - crow[:-1])
+    dg = torch.zeros(K.shape[0], dtype=val.dtype, device="cuda").index_add_(
+        0, rid, torch.where(col == rid, val, torch.zeros_like(val)))
+    dinv = 1.0 / dg
+    x = torch.zeros_like(b)
+    r = b.clone()
+    z = dinv * r
+    p = z.clone()
+    rz = torch.dot(r, z)
+    nb = torch.linalg.vector_norm(b).item()
+    it = 0
+    while it < maxiter:
+        q = torch.mv(K, p)
+        a = rz / torch.dot(p, q)
+        x.add_(a * p)
+        r.sub_(a * q)
+        z = dinv * r
+        rz_new = torch.dot(r, z)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+        it += 1
+        if it % check == 0 and torch.linalg.vector_norm(r).item() <= tol * nb:
+            break
+    return x, it
+
+
 # ------------------------------------------------------------- GPU arm
 
 
@@ -240,6 +310,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solves")
     ap.add_argument("--check-every", type=int, default=32)
+    ap.add_argument("--no-csr", action="store_true", help="skip the assembled-CSR comparison")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven solve")
     ap.add_argument("--only-apply", type=int, default=0, metavar="P",
                     help="profiling mode: only run --reps applies of order P (no JSON line)")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
@@ -359,6 +431,86 @@ def main():
                                        "GBps": round(bytes_alg / ms / 1e6, 1),
                                        "TFLOPs": round(flops_alg / ms / 1e9, 3),
                                        "alg_bytes": int(bytes_alg), "alg_flops": int(flops_alg)}
+    # assembled CSR on the same GPU: SpMV bandwidth and FP64 PCG time-to-tolerance
+    csr = {}
+    if not args.no_csr:
+        for p in P_LIST:
+            c = ctxs[p]
+            K64 = csr_operator(c, B)
+            nnz = K64.values().numel()
+            out = {"nnz": int(nnz)}
+            for prec, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
+                K = K64 if dt == torch.float64 else torch.sparse_csr_tensor(
+                    K64.crow_indices().to(torch.int32), K64.col_indices().to(torch.int32),
+                    K64.values().to(torch.float32), K64.shape)
+                x = torch.randn(c.n, dtype=dt, device="cuda")
+                for _ in range(3):
+                    torch.mv(K, x)
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                ev0.record(stream)
+                for _ in range(10):
+                    torch.mv(K, x)
+                ev1.record(stream)
+                torch.cuda.synchronize()
+                ms = ev0.elapsed_time(ev1) / 10
+                ib = 8 if K.col_indices().dtype == torch.int64 else 4
+                byt = nnz * (dt.itemsize + ib) + (c.n + 1) * ib + 2 * c.n * dt.itemsize
+                out[f"spmv_{prec}_ms"] = round(ms, 4)
+                out[f"spmv_{prec}_GBps"] = round(byt / ms / 1e6, 1)
+                out[f"spmv_{prec}_gdofs"] = round(c.n / ms / 1e6, 3)
+                del K
+            if not args.no_fp64:
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                ev0.record(stream)
+                _, its = csr_pcg(K64, bs[p], TOL)
+                ev1.record(stream)
+                torch.cuda.synchronize()
+                out["pcg_fp64_ms"] = round(ev0.elapsed_time(ev1), 3)
+                out["pcg_fp64_iters"] = its
+            csr[f"P{p}"] = out
+            del K64
+            torch.cuda.empty_cache()
+
+    # batched uneven problems (256 independent 2D problems, one graph launch per phase)
+    batch = None
+    if not args.no_batch:
+        from paper_1710_09913_gb300 import inputs
+        specs = inputs.uneven_problems(256, seed=5)
+        bctx, bb, bu = [], [], []
+        for N, p, sd in specs:
+            bc, bcl = inputs.lattice_mesh(2, N)
+            m = inputs.coef_lognormal(len(bcl), 1.0, sd)
+            c = B.Context(bc, bcl, p, "elliptic", m)
+            bctx.append(c)
+            bb.append(c.load())
+            bu.append(torch.zeros(c.n, dtype=torch.float64, device="cuda"))
+        B.batch_solve(bctx, bb, bu, mode="mixed", tol=TOL)  # warm-up (graph capture)
+        l0 = sum(c.launches() for c in bctx)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        infos = B.batch_solve(bctx, bb, bu, mode="mixed", tol=TOL)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        dofs = sum(c.n for c in bctx)
+        work_b = sum(c.n * (i["iterations"] + i["outer"]) for c, i in zip(bctx, infos))
+        secs = np.array([i["seconds"] for i in infos]) * 1e3
+        batch = {"problems": len(bctx), "dofs": int(dofs), "ms": round(ms, 2),
+                 "apply_gdofs": round(work_b / ms / 1e6, 3),
+                 "solve_gdofs": round(dofs / ms / 1e6, 4),
+                 "p50_ms": round(float(np.percentile(secs, 50)), 2),
+                 "p99_ms": round(float(np.percentile(secs, 99)), 2),
+                 "max_rel_residual": max(i["rel_residual"] for i in infos),
+                 "all_converged": all(i["status"] == 0 for i in infos),
+                 "gpu_launches": int(sum(c.launches() for c in bctx) - l0)}
+        del bctx, bb, bu
+
     dom = applies["P4_fp32"]
     roofline = {"bound": "hbm", "achieved": dom["GBps"], "peak": hbm, "unit": "GB/s",
                 "frac": round(dom["GBps"] / hbm, 4), "traffic": None,
@@ -410,7 +562,8 @@ def main():
                            "parallelism": "replicas (independent problems per GPU)"},
                 "value_definition": "sum_p n_p x operator applies / step time (applies inside the "
                                     "mixed solves, FP32 inner and FP64 residual)",
-                "time_to_tol": t2t, "apply": applies, "roofline": roofline,
+                "time_to_tol": t2t, "apply": applies, "csr_baseline": csr, "batch_uneven": batch,
+                "roofline": roofline,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks}
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -251,6 +251,26 @@ DOGIP_API int dogip_solve_host(dogip_ctx* ctx, const double* b_host, double* u_h
                      dogip_solve_info* info, double* rel_residual_per_rhs,
                      void* cuda_stream);
 
+/* ---------------------------------------------------------- batched solves */
+/*
+ * Solve nprob independent problems K_i u_i = b_i together (one right-hand side
+ * each; the contexts may differ in mesh, p and form, and must share a device and
+ * be distinct).  Each phase of the solve -- FP64 residual, FP32 (or FP64) CG
+ * iteration chunk, correction -- is one CUDA graph launch for the whole batch, with
+ * one concurrent branch per problem; converged problems skip their work on the
+ * device.  Modes DOGIP_SOLVE_FP64 and DOGIP_SOLVE_MIXED (in which every round of
+ * inner iterations lasts until all inner solves are done); u_i start at 0.
+ *   ctxs : host array [nprob] of contexts;  b, u : host arrays [nprob] of DEVICE
+ *   double [n_i] vectors;  infos : host [nprob] or NULL -- per problem status,
+ *   iterations, refinement steps, final FP64 relative residual, and `seconds` =
+ *   host time from the start of the call until that problem met the tolerance.
+ * Returns DOGIP_OK when every problem converged, else the first failure code.
+ * Synchronises cuda_stream.  Not part of the paper (a batching service).
+ */
+DOGIP_API int dogip_batch_solve(dogip_ctx* const* ctxs, int nprob, const double* const* b,
+                                double* const* u, const dogip_solve_opts* o,
+                                dogip_solve_info* infos, void* cuda_stream);
+
 /* ---------------------------------------------------------------- gradient */
 /*
  * Gradient of the compliance-type functional J = lambda^T K(A) u with respect

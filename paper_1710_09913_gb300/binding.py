@@ -101,6 +101,8 @@ _SIGS = {
                                    C.POINTER(SolveInfo), _vp, _vp]),
     "dogip_grad_coef": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "dogip_check": (C.c_int, [_vp, _vp]),
+    "dogip_batch_solve": (C.c_int, [C.POINTER(_vp), C.c_int, C.POINTER(_vp), C.POINTER(_vp),
+                                    C.POINTER(SolveOpts), C.POINTER(SolveInfo), _vp]),
     "dogip_residual_norms_noalloc": (C.c_int, [_vp, _vp, _vp, C.c_int64, C.c_int, _vp, _vp]),
     "dogip_last_error": (C.c_char_p, []),
     "dogip_version": (C.c_int, []),
@@ -150,6 +152,24 @@ def residual_norms_noalloc(b, Ky, r=None, rel=None, stream=None):
                                             b.shape[0], R, _dptr(rel, torch.float64),
                                             _stream(stream)))
     return rel
+
+
+def batch_solve(ctxs, bs, us, *, mode="mixed", tol=1e-8, check_every=None, inner_tol=None,
+                max_outer=None, maxiter=None, stream=None):
+    """Solve independent problems together (dogip_batch_solve); returns per-problem
+    info dicts."""
+    import torch
+    n = len(ctxs)
+    hs = (_vp * n)(*[c._h.value for c in ctxs])
+    bp = (_vp * n)(*[_dptr(x, torch.float64).value for x in bs])
+    up = (_vp * n)(*[_dptr(x, torch.float64).value for x in us])
+    o = ctxs[0]._solve_opts(mode, tol, maxiter, inner_tol, None, max_outer, None, check_every,
+                            False, 0.0)
+    infos = (SolveInfo * n)()
+    code = lib.dogip_batch_solve(hs, n, bp, up, C.byref(o), infos, _stream(stream))
+    _check(code, allow=(ENOTCONV,))
+    return [dict(status=i.status, iterations=i.iterations, outer=i.outer,
+                 rel_residual=i.rel_residual, seconds=i.seconds) for i in infos]
 
 
 def get_tables(dim, p, form):

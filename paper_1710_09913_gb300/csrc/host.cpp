@@ -5,6 +5,7 @@
 #include <cstdlib>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -659,6 +660,234 @@ int solve(Ctx& c, const double* b, double* u, int R, const dogip_solve_opts* opt
   return status;
 }
 
+
+// ------------------------------------------------------------- batched solve
+//
+// Many independent problems (each with its own context, stream and workspace)
+// solved together.  Every phase of the solve is captured once as ONE CUDA graph
+// with a parallel branch per problem (fork/join over the contexts' streams), and a
+// round of the solve is one graph launch for the whole batch: the GPU schedules the
+// small kernels of all problems concurrently.  Problems that have converged skip
+// their work inside the kernels (device flags).  Mixed mode: every round of FP32
+// inner iterations ends when all inner solves are done; the FP64 residual and the
+// correction are batch phases too.
+
+struct BatchGraph {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<int64_t> kernels;  // kernel nodes per problem branch
+};
+
+BatchGraph capture_batch(std::vector<Ctx*>& cs, cudaStream_t main,
+                         const std::function<void(int, Ctx&, cudaStream_t)>& body) {
+  BatchGraph bg;
+  bg.kernels.assign(cs.size(), 0);
+  cudaEvent_t fork = nullptr;
+  cuda_check(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming), "event");
+  std::vector<int64_t> before(cs.size());
+  for (size_t i = 0; i < cs.size(); ++i) before[i] = cs[i]->launches;
+  cuda_check(cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal), "begin capture");
+  try {
+    cuda_check(cudaEventRecord(fork, main), "fork record");
+    for (size_t i = 0; i < cs.size(); ++i) {
+      cudaStream_t s = cs[i]->stream;
+      cuda_check(cudaStreamWaitEvent(s, fork, 0), "fork wait");
+      body((int)i, *cs[i], s);
+      cuda_check(cudaEventRecord(cs[i]->ev_out, s), "join record");
+      cuda_check(cudaStreamWaitEvent(main, cs[i]->ev_out, 0), "join wait");
+    }
+  } catch (...) {
+    cudaGraph_t g = nullptr;
+    cudaStreamEndCapture(main, &g);
+    if (g) cudaGraphDestroy(g);
+    cudaEventDestroy(fork);
+    for (size_t i = 0; i < cs.size(); ++i) cs[i]->launches = before[i];
+    throw;
+  }
+  cudaGraph_t g = nullptr;
+  cuda_check(cudaStreamEndCapture(main, &g), "end capture");
+  cudaEventDestroy(fork);
+  for (size_t i = 0; i < cs.size(); ++i) {
+    bg.kernels[i] = cs[i]->launches - before[i];  // counted during capture, run on replay
+    cs[i]->launches = before[i];
+  }
+  cudaError_t e = cudaGraphInstantiate(&bg.exec, g, 0);
+  cudaGraphDestroy(g);
+  cuda_check(e, "batch graph instantiate");
+  return bg;
+}
+
+void replay(BatchGraph& bg, std::vector<Ctx*>& cs, cudaStream_t main) {
+  cuda_check(cudaGraphLaunch(bg.exec, main), "batch graph launch");
+  for (size_t i = 0; i < cs.size(); ++i) cs[i]->launches += bg.kernels[i];
+  cuda_check(cudaStreamSynchronize(main), "batch round");
+}
+
+int batch_solve(Ctx* const* ctxs, int np, const double* const* b, double* const* u,
+                const dogip_solve_opts* opts, dogip_solve_info* infos, double* seconds_out,
+                cudaStream_t user) {
+  const auto t0 = std::chrono::steady_clock::now();
+  dogip_solve_opts o;
+  dogip_solve_opts_default(&o);
+  if (opts) o = *opts;
+  if (np < 1 || !ctxs || !b || !u) fail(DOGIP_EINVAL, "ctxs, b and u arrays are required");
+  if (o.mode != DOGIP_SOLVE_FP64 && o.mode != DOGIP_SOLVE_MIXED)
+    fail(DOGIP_EINVAL, "batched solves support the FP64 and MIXED modes");
+  if (o.use_x0) fail(DOGIP_EINVAL, "batched solves start from u = 0");
+  std::vector<Ctx*> cs(ctxs, ctxs + np);
+  const int dev = cs[0]->device;
+  for (int i = 0; i < np; ++i) {
+    if (!cs[i] || !b[i] || !u[i]) fail(DOGIP_EINVAL, "null context or vector in the batch");
+    if (cs[i]->device != dev) fail(DOGIP_EINVAL, "all contexts of a batch share one device");
+    if (o.mode == DOGIP_SOLVE_MIXED && !cs[i]->keep32) fail(DOGIP_EINVAL, "mixed mode needs keep_fp32");
+    for (int j = 0; j < i; ++j)
+      if (cs[j] == cs[i]) fail(DOGIP_EINVAL, "a context appears twice in the batch");
+  }
+  DeviceGuard guard(dev);
+  for (Ctx* c : cs) vec_alloc(c->work, c->n, 1);
+  cudaStream_t main = nullptr;
+  cuda_check(cudaStreamCreateWithFlags(&main, cudaStreamNonBlocking), "batch stream");
+  cudaEvent_t ev = nullptr;
+  cuda_check(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+  std::vector<BatchGraph> graphs;
+  auto cleanup = [&]() {
+    for (auto& g : graphs)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+    cudaEventDestroy(ev);
+    cudaStreamDestroy(main);
+  };
+  std::vector<double> t_done(np, -1.0);
+  std::vector<int> iters(np, 0), outers(np, 0);
+  int status = DOGIP_OK;
+  auto elapsed = [&]() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  };
+  try {
+    cuda_check(cudaEventRecord(ev, user), "event record");
+    cuda_check(cudaStreamWaitEvent(main, ev, 0), "stream wait");
+    const int chunk = std::max(1, o.check_every);
+    const int scat = DOGIP_SCATTER_ATOMIC;
+    auto scal_copy = [&](Ctx& c, cudaStream_t s) {
+      cuda_check(cudaMemcpyAsync(c.work.h_scal, c.work.scal, sizeof(CGScal), cudaMemcpyDeviceToHost, s),
+                 "scal copy");
+      cuda_check(cudaMemcpyAsync(c.work.h_flags, c.work.flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, s),
+                 "flags copy");
+    };
+    const bool mixed = o.mode == DOGIP_SOLVE_MIXED;
+    // phase 0: r = b (u = 0), norms; FP64 mode also starts PCG here
+    graphs.push_back(capture_batch(cs, main, [&](int i, Ctx& c, cudaStream_t s) {
+      cuda_check(cudaMemsetAsync(u[i], 0, sizeof(double) * c.n, s), "zero u");
+      cuda_check(cudaMemsetAsync(c.work.q64, 0, sizeof(double) * c.n, s), "zero q");
+      c.launches += vec_residual64(c.work, b[i], c.work.q64, true, o.tol, s);
+      if (!mixed) c.launches += vec_init64(c.work, c.d_dinv64, o.tol, s);
+      scal_copy(c, s);
+    }));
+    // phase 1: a chunk of CG iterations (FP32 inner or FP64)
+    graphs.push_back(capture_batch(cs, main, [&](int i, Ctx& c, cudaStream_t s) {
+      SolveWork& w = c.work;
+      for (int it = 0; it < chunk; ++it) {
+        if (mixed) {
+          const bool f = launch_apply_cg(c, w.p32, w.q32, 1, DOGIP_FP32, scat, s, w);
+          c.launches += vec_cg_step(w, DOGIP_FP32, nullptr, c.d_dinv32, 0.0, s, f);
+        } else {
+          const bool f = launch_apply_cg(c, w.p64, w.q64, 1, DOGIP_FP64, scat, s, w);
+          c.launches += vec_cg_step(w, DOGIP_FP64, u[i], c.d_dinv64, 0.0, s, f);
+        }
+      }
+      scal_copy(c, s);
+    }));
+    // phase 2: FP64 correction and true residual (mixed: then a new inner start)
+    graphs.push_back(capture_batch(cs, main, [&](int i, Ctx& c, cudaStream_t s) {
+      if (mixed) c.launches += vec_correct(c.work, u[i], s);
+      launch_apply(c, u[i], c.work.q64, 1, DOGIP_FP64, scat, s, nullptr);
+      c.launches += vec_residual64(c.work, b[i], c.work.q64, false, o.tol, s);
+      scal_copy(c, s);
+    }));
+    // phase 3 (mixed): inner start r32 = r64 / ||r64||
+    if (mixed)
+      graphs.push_back(capture_batch(cs, main, [&](int i, Ctx& c, cudaStream_t s) {
+        c.launches += vec_inner_init32(c.work, c.d_dinv32, o.inner_tol, s);
+        scal_copy(c, s);
+      }));
+    auto note_done = [&]() {
+      bool all = true;
+      for (int i = 0; i < np; ++i) {
+        if (cs[i]->work.h_scal[0].odone) {
+          if (t_done[i] < 0) t_done[i] = elapsed();
+        } else {
+          all = false;
+        }
+      }
+      return all;
+    };
+    replay(graphs[0], cs, main);
+    bool all = note_done();
+    if (mixed) {
+      for (int outer = 0; !all; ++outer) {
+        if (outer >= o.max_outer) { status = DOGIP_ENOTCONV; break; }
+        if (o.timeout_ms > 0 && elapsed() * 1e3 > o.timeout_ms) { status = DOGIP_ETIMEOUT; break; }
+        replay(graphs[3], cs, main);
+        for (int i = 0; i < np; ++i)
+          if (!cs[i]->work.h_scal[0].odone) outers[i] = outer + 1;
+        int inner = 0;
+        while (inner < o.inner_maxiter) {
+          bool all_in = true;
+          for (Ctx* c : cs) all_in = all_in && c->work.h_flags[2];
+          if (all_in) break;
+          replay(graphs[1], cs, main);
+          inner += chunk;
+          bool brk = false;
+          for (Ctx* c : cs) brk = brk || c->work.h_flags[1];
+          if (brk) break;
+        }
+        for (int i = 0; i < np; ++i) iters[i] += cs[i]->work.h_scal[0].iters;
+        replay(graphs[2], cs, main);
+        all = note_done();
+      }
+    } else {
+      int total = 0;
+      while (!all) {
+        if (total >= o.maxiter) { status = DOGIP_ENOTCONV; break; }
+        if (o.timeout_ms > 0 && elapsed() * 1e3 > o.timeout_ms) { status = DOGIP_ETIMEOUT; break; }
+        replay(graphs[1], cs, main);
+        total += chunk;
+        bool all_in = true;
+        for (int i = 0; i < np; ++i) {
+          const bool di = cs[i]->work.h_flags[2];
+          if (di && t_done[i] < 0) t_done[i] = elapsed();
+          all_in = all_in && di;
+        }
+        if (all_in) break;
+      }
+      for (int i = 0; i < np; ++i) iters[i] = cs[i]->work.h_scal[0].iters;
+      replay(graphs[2], cs, main);  // true residual of the final iterates
+      note_done();
+    }
+    cuda_check(cudaEventRecord(ev, main), "event record");
+    cuda_check(cudaStreamWaitEvent(user, ev, 0), "stream wait");
+  } catch (...) {
+    cudaStreamSynchronize(main);
+    cleanup();
+    throw;
+  }
+  cudaStreamSynchronize(main);
+  cleanup();
+  for (int i = 0; i < np; ++i) {
+    const CGScal& sc = cs[i]->work.h_scal[0];
+    int st = sc.rel <= o.tol ? DOGIP_OK : (status == DOGIP_OK ? DOGIP_ENOTCONV : status);
+    if (cs[i]->work.h_flags[1]) st = DOGIP_EBREAKDOWN;
+    if (st != DOGIP_OK && status == DOGIP_OK) status = st;
+    if (infos) {
+      infos[i].status = st;
+      infos[i].iterations = iters[i];
+      infos[i].outer = outers[i];
+      infos[i].rel_residual = sc.rel;
+      infos[i].seconds = t_done[i] >= 0 ? t_done[i] : elapsed();
+    }
+    if (seconds_out) seconds_out[i] = t_done[i];
+  }
+  return status;
+}
+
 template <typename F>
 int guarded(F&& f) {
   try {
@@ -906,6 +1135,13 @@ int dogip_solve_host(dogip_ctx* c, const double* bh, double* uh, int nrhs,
     dogip::cuda_check(cudaFreeAsync(du, s), "staging free");
     dogip::cuda_check(cudaStreamSynchronize(s), "solve_host sync");
     return st;
+  });
+}
+
+int dogip_batch_solve(dogip_ctx* const* ctxs, int nprob, const double* const* b, double* const* u,
+                      const dogip_solve_opts* o, dogip_solve_info* infos, void* stream) {
+  return guarded([&] {
+    return dogip::batch_solve(ctxs, nprob, b, u, o, infos, nullptr, (cudaStream_t)stream);
   });
 }
 

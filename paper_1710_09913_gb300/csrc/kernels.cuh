@@ -392,19 +392,20 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T>::THREADS)
     if (failed) break;
     const int64_t tile = k * C::TPC + warp;
     const int64_t e = tile * kTile + lane;
-    if (tile < a.ntiles && e < a.E) {
-      const T* sA = (const T*)(base + (size_t)s * C::CHUNK + warp * C::A_TILE) + lane;
-      const uint32_t* sC =
-          (const uint32_t*)(base + (size_t)s * C::CHUNK + C::TPC * C::A_TILE + warp * C::C_TILE) +
-          lane;
-      uint32_t c[V];
-      static_for<V>([&](auto lc) {
-        constexpr int l = decltype(lc)::value;
-        c[l] = sC[l * kTile];
-      });
-      for (int r = 0; r < a.R; ++r) {
+    const bool active = tile < a.ntiles && e < a.E;
+    const T* sA = (const T*)(base + (size_t)s * C::CHUNK + warp * C::A_TILE) + lane;
+    const uint32_t* sC =
+        (const uint32_t*)(base + (size_t)s * C::CHUNK + C::TPC * C::A_TILE + warp * C::C_TILE) +
+        lane;
+    uint32_t c[V];
+    static_for<V>([&](auto lc) {
+      constexpr int l = decltype(lc)::value;
+      c[l] = active ? sC[l * kTile] : kBndBit;
+    });
+    for (int r = 0; r < a.R; ++r) {  // uniform over the warp (the shuffles below)
+      T en = T(0);
+      if (active) {
         T ul[V], Y[V];
-        T en = T(0);
         static_for<V>([&](auto lc) {
           constexpr int l = decltype(lc)::value;
           ul[l] = (c[l] & kBndBit) ? T(0) : __ldg(a.u + (int64_t)(c[l] & kIdMask) * a.R + r);
@@ -431,7 +432,12 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T>::THREADS)
           constexpr int l = decltype(lc)::value;
           if (!(c[l] & kBndBit)) atomicAdd(a.y + (int64_t)(c[l] & kIdMask) * a.R + r, Y[l]);
         });
-        if (fused) atomicAdd(&s_en[r], (double)en);
+      }
+      if (fused) {  // warp sum, then one shared-memory add per warp
+        double v = (double)en;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) atomicAdd(&s_en[r], v);
       }
     }
     __syncthreads();  // every read of stage s is done
@@ -452,13 +458,22 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T>::THREADS)
     __syncthreads();
   }
   // Dirichlet rows: y_b = u_b (the scatter skipped them), and u_b^2 for p.q
+  double bsum = 0.0;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + tid; t < a.nbnd * a.R;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int r = (int)(t % a.R);
     const int64_t idx = (int64_t)a.bnd[t / a.R] * a.R + r;
     const T ub = a.u[idx];
     a.y[idx] = ub;
-    if (fused) atomicAdd(&s_en[r], (double)ub * (double)ub);
+    if (fused) {
+      if (a.R == 1) bsum += (double)ub * (double)ub;
+      else atomicAdd(&s_en[r], (double)ub * (double)ub);
+    }
+  }
+  if (fused && a.R == 1) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) bsum += __shfl_xor_sync(0xffffffffu, bsum, off);
+    if (lane == 0 && bsum != 0.0) atomicAdd(&s_en[0], bsum);
   }
   if (fused) fused_alpha(a.partial, a.counter, a.scal, a.flags, a.R, s_en);
 }

@@ -1,0 +1,66 @@
+"""Batched solves (dogip_batch_solve) of independent uneven problems, against the
+oracle's FP64 apply (true relative residual of every problem) and against the
+single-problem solver."""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import dogip as odogip  # noqa: E402
+from paper_1710_09913_gb300 import inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_1710_09913_gb300 import build
+    build.build()
+    from paper_1710_09913_gb300 import binding
+    return binding
+
+
+def _problems(B, specs):
+    out = []
+    for N, p, seed in specs:
+        coords, cells = inputs.lattice_mesh(2, N)
+        m = inputs.coef_lognormal(len(cells), 1.0, seed)
+        ctx = B.Context(coords, cells, p, "elliptic", m)
+        out.append((ctx, odogip.Problem("elliptic", p, coords, cells, m)))
+    return out
+
+
+@pytest.mark.parametrize("mode", ["mixed", "fp64"])
+def test_batch_small_uneven(B, mode):
+    specs = [(4, 1, 1), (9, 3, 2), (16, 2, 3), (5, 2, 4), (12, 1, 5), (7, 3, 6), (3, 1, 7)]
+    probs = _problems(B, specs)
+    bs = [c.load() for c, _ in probs]
+    us = [torch.zeros_like(b) for b in bs]
+    infos = B.batch_solve([c for c, _ in probs], bs, us, mode=mode, tol=1e-10, check_every=8)
+    for (c, P), b, u, inf in zip(probs, bs, us, infos):
+        assert inf["status"] == 0 and inf["rel_residual"] <= 1e-10
+        bb, uu = b.cpu().numpy(), u.cpu().numpy()
+        r = bb - P.apply(uu)
+        assert np.linalg.norm(r) <= 1.01e-10 * np.linalg.norm(bb)
+        u1, _ = c.solve(b, mode=mode, tol=1e-10)
+        assert np.linalg.norm(u1.cpu().numpy() - uu) <= 1e-8 * np.linalg.norm(uu)
+
+
+def test_batch_config_uneven_256(B):
+    """Config: 256 problems, N ~ U{16..128}, p ~ U{1,2,3}, lognormal(0,1) scalar,
+    f = 1, mixed precision to 1e-8: every problem's true residual (oracle) meets it."""
+    specs = inputs.uneven_problems(256, seed=5)
+    probs = _problems(B, specs)
+    bs = [c.load() for c, _ in probs]
+    us = [torch.zeros_like(b) for b in bs]
+    infos = B.batch_solve([c for c, _ in probs], bs, us, mode="mixed", tol=1e-8)
+    worst = 0.0
+    for (c, P), b, u, inf in zip(probs, bs, us, infos):
+        assert inf["status"] == 0
+        bb = b.cpu().numpy()
+        r = bb - P.apply(u.cpu().numpy())
+        worst = max(worst, np.linalg.norm(r) / np.linalg.norm(bb))
+    assert worst <= 1.01e-8
+    times = sorted(i["seconds"] for i in infos)
+    assert times[0] > 0 and times[-1] >= times[len(times) // 2]

@@ -320,3 +320,26 @@ def test_full_size_mixed_solve_residual(B):
     bb = b.cpu().numpy()
     r = bb - P.apply(x.cpu().numpy())
     assert np.linalg.norm(r) <= 1.01e-8 * np.linalg.norm(bb)
+
+
+@pytest.mark.parametrize("form", ["elliptic", "projection"])
+def test_config_small_fp64_pcg(B, form):
+    """Config: 32 x 32 squares x 2 triangles (2,048 cells), no jitter, P2 (4,225 dofs),
+    per-cell A ~ U[1, 10]; elliptic with f = 1 and zero Dirichlet data, projection with
+    f = sin(pi x) sin(pi y) (load by the oracle's quadrature); FP64 Jacobi-PCG to
+    1e-10 against the oracle's direct solve of the assembled system."""
+    coords, cells = inputs.lattice_mesh(2, 32)
+    A = inputs.coef_uniform(len(cells), 1.0, 10.0, seed=1)
+    ctx = B.Context(coords, cells, 2, form, A)
+    P = odogip.Problem(form, 2, coords, cells, A)
+    assert ctx.n == 4225 == P.n
+    if form == "elliptic":
+        b = odogip.load_const(2, 2, coords, cells, P.conn, P.n, np.ones(len(cells)))
+        b[P.bmask] = 0.0
+    else:
+        f = lambda X: np.sin(np.pi * X[..., 0]) * np.sin(np.pi * X[..., 1])
+        b = assembly.load(2, 2, coords, cells, P.conn, P.n, f)
+    x, info = ctx.solve(torch.tensor(b, device="cuda"), mode="fp64", tol=1e-10)
+    assert info["status"] == 0 and info["rel_residual"] <= 1e-10
+    ref = _direct(P, b)
+    assert np.linalg.norm(x.cpu().numpy() - ref) <= 1e-8 * np.linalg.norm(ref)
