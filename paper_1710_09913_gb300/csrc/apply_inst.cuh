@@ -25,7 +25,7 @@ void run_apply_t(const T* A, const Ctx& c, const void* u, void* y, int R, bool a
 
 // Persistent bulk-async variant over the whole cell range (atomic scatter).
 struct TmaLaunch {
-  int blocks_per_sm = 1, num_sms = 1;
+  int blocks_per_sm = 1, num_sms = 1;  // the fused and plain instances share the residency
 };
 
 // Kernel attributes and residency of one instance, set once (thread-safe static);
@@ -34,9 +34,12 @@ template <int D, int P, int FORM, typename T>
 const TmaLaunch& tma_launch() {
   static const TmaLaunch info = [] {
     using Cfg = TmaCfg<D, P, FORM, T>;
-    auto kern = k_apply_tma<D, P, FORM, T>;
+    auto kern = k_apply_tma<D, P, FORM, T, false>;
+    auto kern_f = k_apply_tma<D, P, FORM, T, true>;
     TmaLaunch t;
     cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM),
+               "apply smem attribute");
+    cuda_check(cudaFuncSetAttribute(kern_f, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM),
                "apply smem attribute");
     int dev = 0, nb = 0;
     cuda_check(cudaGetDevice(&dev), "get device");
@@ -53,7 +56,6 @@ template <int D, int P, int FORM, typename T>
 void run_apply_tma(const T* A, const Ctx& c, const void* u, void* y, int R, cudaStream_t s,
                    const int* skip, SolveWork* fuse) {
   using Cfg = TmaCfg<D, P, FORM, T>;
-  auto kern = k_apply_tma<D, P, FORM, T>;
   const TmaLaunch& L = tma_launch<D, P, FORM, T>();
   const int blocks_per_sm = L.blocks_per_sm, num_sms = L.num_sms;
   const int64_t ntiles = (c.E + kTile - 1) / kTile;
@@ -64,7 +66,8 @@ void run_apply_tma(const T* A, const Ctx& c, const void* u, void* y, int R, cuda
                 c.d_bnd, c.dirichlet ? c.nbnd : 0,
                 fuse ? fuse->partial : nullptr, fuse ? fuse->counter : nullptr,
                 fuse ? fuse->scal : nullptr, fuse ? fuse->flags : nullptr};
-  kern<<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
+  if (fuse) k_apply_tma<D, P, FORM, T, true><<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
+  else k_apply_tma<D, P, FORM, T, false><<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
 }
 
 // Returns 2 when the staged kernel ran (it also wrote the Dirichlet rows and, with

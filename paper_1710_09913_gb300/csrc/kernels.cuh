@@ -344,7 +344,7 @@ static __device__ __noinline__ void fused_alpha(double* partial, unsigned int* c
   }
 }
 
-template <int D, int P, int FORM, typename T>
+template <int D, int P, int FORM, typename T, bool FUSED>
 __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T>::THREADS)
     k_apply_tma(TmaArgs<T> a) {
   using C = TmaCfg<D, P, FORM, T>;
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T>::THREADS)
   if (a.skip != nullptr && *a.skip) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t G = gridDim.x;
-  const bool fused = a.partial != nullptr;
+  constexpr bool fused = FUSED;  // a.partial etc. are set exactly when FUSED
   __shared__ double s_en[32];
   if (tid < 32) s_en[tid] = 0.0;
   if (tid == 0) {
@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T>::THREADS)
           });
           interp<TB, j>(ul, g);
           block_mul<D, FORM>(aj, g, h);
-          if (fused) {
+          if constexpr (FUSED) {
             static_for<NB>([&](auto rc) {
               constexpr int rr = decltype(rc)::value;
               en = fma(g[rr], h[rr], en);
@@ -433,7 +433,7 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T>::THREADS)
           if (!(c[l] & kBndBit)) atomicAdd(a.y + (int64_t)(c[l] & kIdMask) * a.R + r, Y[l]);
         });
       }
-      if (fused) {  // warp sum, then one shared-memory add per warp
+      if constexpr (FUSED) {  // warp sum, then one shared-memory add per warp
         double v = (double)en;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -475,7 +475,7 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T>::THREADS)
     for (int off = 16; off > 0; off >>= 1) bsum += __shfl_xor_sync(0xffffffffu, bsum, off);
     if (lane == 0 && bsum != 0.0) atomicAdd(&s_en[0], bsum);
   }
-  if (fused) fused_alpha(a.partial, a.counter, a.scal, a.flags, a.R, s_en);
+  if constexpr (FUSED) fused_alpha(a.partial, a.counter, a.scal, a.flags, a.R, s_en);
 }
 
 // ------------------------------------------------------------------ setup
