@@ -284,6 +284,20 @@ def csr_pcg(K, b, tol, maxiter=200000, check=50):
 # ------------------------------------------------------------- GPU arm
 
 
+def only_solve(args):
+    """Profiling mode: build the workload at order P and run one mixed solve."""
+    import torch
+    from paper_1710_09913_gb300 import build
+    build.build()
+    from paper_1710_09913_gb300 import binding as B
+    coords, cells, A = mesh_and_coef()
+    c = B.Context(coords, cells, args.only_solve, "elliptic", A)
+    b = c.load()
+    c.solve(b, mode="mixed", tol=TOL, check_every=args.check_every)
+    torch.cuda.synchronize()
+    return 0
+
+
 def only_apply(args):
     """Profiling mode: build the workload at order P and run the apply alone."""
     import torch
@@ -314,6 +328,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven solve")
     ap.add_argument("--only-apply", type=int, default=0, metavar="P",
                     help="profiling mode: only run --reps applies of order P (no JSON line)")
+    ap.add_argument("--only-solve", type=int, default=0, metavar="P",
+                    help="profiling mode: one mixed solve of order P (no JSON line)")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
@@ -321,6 +337,8 @@ def main():
         return run_reference(args)
     if args.only_apply:
         return only_apply(args)
+    if args.only_solve:
+        return only_solve(args)
 
     import torch
 

@@ -63,7 +63,7 @@ void run_apply_tma(const T* A, const Ctx& c, const void* u, void* y, int R, cuda
   if (nchunks == 0) return;
   const int64_t grid = std::min<int64_t>(nchunks, (int64_t)num_sms * blocks_per_sm);
   TmaArgs<T> a{A, c.d_conn, (const T*)u, (T*)y, c.E, ntiles, nchunks, R, skip, c.d_kerr,
-                c.d_bnd, c.dirichlet ? c.nbnd : 0,
+                c.d_bnd, c.dirichlet ? c.nbnd : 0, c.wait_budget, c.test_skip_chunk,
                 fuse ? fuse->partial : nullptr, fuse ? fuse->counter : nullptr,
                 fuse ? fuse->scal : nullptr, fuse ? fuse->flags : nullptr};
   if (fuse) k_apply_tma<D, P, FORM, T, true><<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);

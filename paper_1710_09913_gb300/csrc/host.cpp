@@ -388,6 +388,11 @@ Ctx* setup(const dogip_mesh* m, int p, int form, int coef_kind, const double* co
     c->d_err = dev_alloc<int>(1);
     c->d_kerr = dev_alloc<int>(1);
     if (const char* v = std::getenv("DOGIP_APPLY_VARIANT")) c->apply_variant = std::atoi(v);
+    // Test hooks for the device-side failure path: a shorter wait budget, and one
+    // chunk of the staged apply whose copy is never issued, so that its bounded
+    // wait expires (nothing faults or hangs; the kernel reports and returns).
+    if (const char* v = std::getenv("DOGIP_TEST_WAIT_CYCLES")) c->wait_budget = std::atoll(v);
+    if (const char* v = std::getenv("DOGIP_TEST_SKIP_CHUNK")) c->test_skip_chunk = std::atoll(v);
     cudaStream_t s = c->stream;
     cuda_check(cudaMemcpyAsync(c->d_coords, m->coords, sizeof(double) * c->nv * d,
                                cudaMemcpyHostToDevice, s), "upload coords");

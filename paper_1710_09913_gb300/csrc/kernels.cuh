@@ -281,6 +281,8 @@ struct TmaArgs {
   int* err;
   const int32_t* bnd;  // Dirichlet dofs: y_b = u_b is written here (no extra kernel)
   int64_t nbnd;
+  long long wait_budget;  // clock cycles per bounded mbarrier wait
+  int64_t test_skip_chunk;  // test hook: this chunk's copy is never issued (-1: none)
   // Optional fused CG step (all null outside solves): p.q = u^T K u from the element
   // energies sum_j g_j . h_j plus sum_b u_b^2, reduced over the grid; the last
   // block sets alpha = rho / p.q per rhs.
@@ -368,7 +370,7 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T>::THREADS)
   __syncthreads();
   auto issue = [&](int64_t i) {
     const int64_t k = blockIdx.x + i * G;
-    if (k >= a.nchunks) return;
+    if (k >= a.nchunks || k == a.test_skip_chunk) return;
     const int s = (int)(i % C::S);
     const int64_t t0 = k * C::TPC;
     const int nt = (int)min((int64_t)C::TPC, a.ntiles - t0);
@@ -388,7 +390,7 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T>::THREADS)
     if (k >= a.nchunks) break;
     const int s = (int)(i % C::S);
     const uint32_t parity = (uint32_t)((i / C::S) & 1);
-    failed = __syncthreads_or(mbar_wait_bounded(&bars[s], parity, kWaitBudget) ? 0 : 1);
+    failed = __syncthreads_or(mbar_wait_bounded(&bars[s], parity, a.wait_budget) ? 0 : 1);
     if (failed) break;
     const int64_t tile = k * C::TPC + warp;
     const int64_t e = tile * kTile + lane;
@@ -451,7 +453,7 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T>::THREADS)
     if (tid == 0) {
       for (int64_t q = i; q < i + C::S; ++q) {
         if (blockIdx.x + q * G >= a.nchunks) break;
-        mbar_wait_bounded(&bars[q % C::S], (uint32_t)((q / C::S) & 1), kWaitBudget);
+        mbar_wait_bounded(&bars[q % C::S], (uint32_t)((q / C::S) & 1), a.wait_budget);
       }
       atomicOr(a.err, 1);
     }

@@ -1,0 +1,48 @@
+"""Device-side failure detection without a GPU fault: the staged apply's bounded
+mbarrier wait runs out on a copy that is never issued (a test hook, the analogue of
+a flag that nothing sets); the kernel drains its other copies, raises its error word
+and returns; dogip_check reports DOGIP_ETIMEOUT and the CUDA context stays usable."""
+
+import os
+import subprocess
+import sys
+
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+CHILD = r"""
+import os, sys
+sys.path.insert(0, os.environ["DOGIP_ROOT"])
+import numpy as np, torch
+from paper_1710_09913_gb300 import binding as B, inputs
+coords, cells = inputs.lattice_mesh(2, 64, 0.2, seed=3)
+A = inputs.coef_tensor_lognormal(len(cells), 2, 1.0, seed=3)
+ctx = B.Context(coords, cells, 2, "elliptic", A)
+u = torch.randn(ctx.n, dtype=torch.float32, device="cuda")
+ctx.apply(u, prec="fp32")
+try:
+    ctx.check()
+    print("NO-TIMEOUT")
+except B.DogipError as e:
+    print("TIMEOUT", e.code)
+# the context and the device remain usable: a second context without the hook
+os.environ.pop("DOGIP_TEST_SKIP_CHUNK")
+ok = B.Context(coords, cells, 2, "elliptic", A)
+y = ok.apply(u.double()).cpu().numpy()
+ok.check()
+print("USABLE", np.isfinite(y).all())
+"""
+
+
+def test_apply_wait_timeout_is_reported():
+    from paper_1710_09913_gb300 import build
+    build.build()
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, DOGIP_ROOT=root, DOGIP_TEST_SKIP_CHUNK="0",
+               DOGIP_TEST_WAIT_CYCLES="2000000")  # ~1 ms per bounded wait
+    out = subprocess.run([sys.executable, "-c", CHILD], env=env, capture_output=True, text=True,
+                         timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    assert "TIMEOUT 6" in out.stdout, out.stdout
+    assert "USABLE True" in out.stdout, out.stdout
