@@ -458,10 +458,12 @@ void run_chunk(Ctx& c, int prec, int scatter, double* x64, int k, double delta) 
       for (int it = 0; it < k; ++it) {
         if (prec == DOGIP_FP64) {
           const bool fused = launch_apply_cg(c, w.p64, w.q64, w.R, DOGIP_FP64, scatter, s, w);
-          c.launches += vec_cg_step(w, DOGIP_FP64, x64, c.d_dinv64, delta, s, fused);
+          c.launches += vec_cg_step(w, DOGIP_FP64, x64, c.d_dinv64, delta, s, fused,
+                                    scatter == DOGIP_SCATTER_ATOMIC);
         } else {
           const bool fused = launch_apply_cg(c, w.p32, w.q32, w.R, DOGIP_FP32, scatter, s, w);
-          c.launches += vec_cg_step(w, DOGIP_FP32, nullptr, c.d_dinv32, delta, s, fused);
+          c.launches += vec_cg_step(w, DOGIP_FP32, nullptr, c.d_dinv32, delta, s, fused,
+                                    scatter == DOGIP_SCATTER_ATOMIC);
         }
       }
       cuda_check(cudaMemcpyAsync(w.h_flags, w.flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, s),
@@ -792,10 +794,10 @@ int batch_solve(Ctx* const* ctxs, int np, const double* const* b, double* const*
       for (int it = 0; it < chunk; ++it) {
         if (mixed) {
           const bool f = launch_apply_cg(c, w.p32, w.q32, 1, DOGIP_FP32, scat, s, w);
-          c.launches += vec_cg_step(w, DOGIP_FP32, nullptr, c.d_dinv32, 0.0, s, f);
+          c.launches += vec_cg_step(w, DOGIP_FP32, nullptr, c.d_dinv32, 0.0, s, f, true);
         } else {
           const bool f = launch_apply_cg(c, w.p64, w.q64, 1, DOGIP_FP64, scat, s, w);
-          c.launches += vec_cg_step(w, DOGIP_FP64, u[i], c.d_dinv64, 0.0, s, f);
+          c.launches += vec_cg_step(w, DOGIP_FP64, u[i], c.d_dinv64, 0.0, s, f, true);
         }
       }
       scal_copy(c, s);

@@ -118,8 +118,9 @@ void cuda_check(cudaError_t e, const char* what);
 void launch_ahat(Ctx& c, const double* coef, int coef_kind, cudaStream_t s);
 void launch_apply(Ctx& c, const void* u, void* y, int R, int prec, int scatter,
                   cudaStream_t s, const int* skip);
-// The apply inside a CG iteration, q = K p with q already zero.  Returns true when
-// the staged kernel also produced p.q and alpha (then no separate p.q kernel).
+// The apply inside a CG iteration, q = K p.  With atomic scatter q must already be
+// zero (the previous p update clears it); colour scatter clears it itself.  Returns
+// true when the staged kernel also produced p.q and alpha (no separate p.q kernel).
 bool launch_apply_cg(Ctx& c, const void* p, void* q, int R, int prec, int scatter,
                      cudaStream_t s, SolveWork& w);
 void launch_load(Ctx& c, const double* f, double* b, cudaStream_t s);
@@ -151,8 +152,10 @@ int vec_inner_init32(SolveWork& w, const float* dinv, double inner_tol, cudaStre
 int vec_init64(SolveWork& w, const double* dinv, double tol, cudaStream_t st);
 // The CG iteration after q = K p: alpha = rho / p.q, x += alpha p, r -= alpha q,
 // rho' = r.Dinv r, beta, p = Dinv r + beta p; per-rhs convergence test.
+// zero_q: clear q for the next scatter-add apply (every atomic-scatter iteration;
+// colour passes clear it themselves).
 int vec_cg_step(SolveWork& w, int prec, double* x64, const void* dinv, double delta,
-                cudaStream_t st, bool pq_fused);
+                cudaStream_t st, bool pq_fused, bool zero_q);
 // Reliable-update mixed CG (FP32 recursion, FP64 corrections):
 // start: r32 = r64, x32 = 0, p = Dinv r32, rho, r0 = ||b||, rmax = ||r64||.
 int vec_rel_init(SolveWork& w, const float* dinv, double tol, cudaStream_t st);

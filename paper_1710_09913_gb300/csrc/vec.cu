@@ -439,7 +439,7 @@ int vec_init64(SolveWork& w, const double* dinv, double tol, cudaStream_t st) {
 }
 
 int vec_cg_step(SolveWork& w, int prec, double* x64, const void* dinv, double delta,
-                cudaStream_t st, bool pq_fused) {
+                cudaStream_t st, bool pq_fused, bool zero_q) {
   const int64_t N = w.n * w.R;
   Red rd = red_of(w);
   const unsigned nb = red_blocks(N);
@@ -449,7 +449,7 @@ int vec_cg_step(SolveWork& w, int prec, double* x64, const void* dinv, double de
   if (!pq_fused) k_pq<double, RR><<<nb, kRedThreads, 0, st>>>(w.p64, w.q64, N, rd);        \
   k_update<double, RR><<<nb, kRedThreads, 0, st>>>(x64, w.r64, w.p64, w.q64, di, N, delta, rd); \
   k_pupdate<double, RR><<<nb, kRedThreads, 0, st>>>(w.p64, w.r64, di, N, w.scal, w.flags,  \
-                                                     pq_fused ? w.q64 : nullptr)
+                                                     zero_q ? w.q64 : nullptr)
     DOGIP_R_SWITCH(w.R, CALL);
 #undef CALL
   } else {
@@ -458,7 +458,7 @@ int vec_cg_step(SolveWork& w, int prec, double* x64, const void* dinv, double de
   if (!pq_fused) k_pq<float, RR><<<nb, kRedThreads, 0, st>>>(w.p32, w.q32, N, rd);         \
   k_update<float, RR><<<nb, kRedThreads, 0, st>>>(w.x32, w.r32, w.p32, w.q32, di, N, delta, rd); \
   k_pupdate<float, RR><<<nb, kRedThreads, 0, st>>>(w.p32, w.r32, di, N, w.scal, w.flags,   \
-                                                    pq_fused ? w.q32 : nullptr)
+                                                    zero_q ? w.q32 : nullptr)
     DOGIP_R_SWITCH(w.R, CALL);
 #undef CALL
   }

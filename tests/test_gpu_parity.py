@@ -138,7 +138,8 @@ def _direct(P, b):
 
 @pytest.mark.parametrize("mode", ["fp64", "mixed"])
 @pytest.mark.parametrize("d,p,form", [(2, 2, "elliptic"), (2, 4, "elliptic"), (2, 2, "projection"),
-                                      (3, 2, "elliptic"), (3, 1, "projection")])
+                                      (3, 2, "elliptic"), (3, 1, "projection"),
+                                      (3, 3, "elliptic")])  # 3D P3 FP64: per-cell kernel path
 def test_solve(B, d, p, form, mode):
     ctx, P = make(B, d, p, form, NSMALL[d])
     b = ctx.load()
