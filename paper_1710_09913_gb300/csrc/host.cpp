@@ -388,6 +388,7 @@ Ctx* setup(const dogip_mesh* m, int p, int form, int coef_kind, const double* co
     c->d_err = dev_alloc<int>(1);
     c->d_kerr = dev_alloc<int>(1);
     if (const char* v = std::getenv("DOGIP_APPLY_VARIANT")) c->apply_variant = std::atoi(v);
+    if (const char* v = std::getenv("DOGIP_FUSE_PQ")) c->fuse_pq = std::atoi(v) != 0;
     // Test hooks for the device-side failure path: a shorter wait budget, and one
     // chunk of the staged apply whose copy is never issued, so that its bounded
     // wait expires (nothing faults or hangs; the kernel reports and returns).

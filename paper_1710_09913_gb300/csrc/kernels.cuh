@@ -294,7 +294,7 @@ struct TmaArgs {
 
 // Grid reduction of the per-block energies s_en[0..R) and, in the last block to
 // finish, alpha = rho / p.q per rhs (breakdown if p.q <= 0), then the stop flags.
-static __device__ __noinline__ void fused_alpha(double* partial, unsigned int* counter, CGScal* scal,
+static __device__ __forceinline__ void fused_alpha(double* partial, unsigned int* counter, CGScal* scal,
                                          int* flags, int R, double* s_en) {
   __shared__ bool last;
   __shared__ double fin[256];

@@ -195,11 +195,11 @@ void prepare_apply(Ctx& c) {
 bool launch_apply_cg(Ctx& c, const void* p, void* q, int R, int prec, int scatter, cudaStream_t s,
                      SolveWork& w) {
   if (scatter == DOGIP_SCATTER_ATOMIC) {
-    const int k = apply_dispatch(c, p, q, R, prec, true, 0, c.E, s, w.flags, &w);
+    const int k = apply_dispatch(c, p, q, R, prec, true, 0, c.E, s, w.flags, c.fuse_pq ? &w : nullptr);
     if (!k) fail(DOGIP_EUNSUPPORTED, "no compiled apply instance for this (dim, p, form)");
     cuda_check(cudaGetLastError(), "apply kernel launch");
     c.launches += 1;
-    if (k == 2) return true;
+    if (k == 2) return c.fuse_pq;  // the staged kernel also wrote the Dirichlet rows
     if (c.dirichlet && c.nbnd > 0) {
       launch_dirichlet_copy(c, p, q, R, prec, s, w.flags);
       c.launches += 1;
