@@ -284,8 +284,8 @@ struct TmaArgs {
   long long wait_budget;  // clock cycles per bounded mbarrier wait
   int64_t test_skip_chunk;  // test hook: this chunk's copy is never issued (-1: none)
   // Optional fused CG step (all null outside solves): p.q = u^T K u from the element
-  // energies sum_j g_j . h_j plus sum_b u_b^2, reduced over the grid; the last
-  // block sets alpha = rho / p.q per rhs.
+  // energies u_T . Y_T (= sum_j g_j . h_j) plus sum_b u_b^2, reduced over the grid;
+  // the last block sets alpha = rho / p.q per rhs.
   double* partial;
   unsigned int* counter;
   CGScal* scal;
@@ -422,14 +422,15 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T>::THREADS)
           });
           interp<TB, j>(ul, g);
           block_mul<D, FORM>(aj, g, h);
-          if constexpr (FUSED) {
-            static_for<NB>([&](auto rc) {
-              constexpr int rr = decltype(rc)::value;
-              en = fma(g[rr], h[rr], en);
-            });
-          }
           project<TB, j>(h, Y);
         });
+        if constexpr (FUSED) {
+          // element energy u_T^T K_T u_T = sum_j g_j . h_j = u_T . (B^T h) = u_T . Y_T
+          static_for<V>([&](auto lc) {
+            constexpr int l = decltype(lc)::value;
+            en = fma(ul[l], Y[l], en);
+          });
+        }
         static_for<V>([&](auto lc) {
           constexpr int l = decltype(lc)::value;
           if (!(c[l] & kBndBit)) atomicAdd(a.y + (int64_t)(c[l] & kIdMask) * a.R + r, Y[l]);
