@@ -25,7 +25,7 @@ void run_apply_t(const T* A, const Ctx& c, const void* u, void* y, int R, bool a
 
 // Persistent bulk-async variant over the whole cell range (atomic scatter).
 struct TmaLaunch {
-  int blocks_per_sm = 1, num_sms = 1;  // the fused and plain instances share the residency
+  int blocks_per_sm = 1, num_sms = 1;
 };
 
 // Kernel attributes and residency of one instance, set once (thread-safe static);
@@ -34,12 +34,9 @@ template <int D, int P, int FORM, typename T>
 const TmaLaunch& tma_launch() {
   static const TmaLaunch info = [] {
     using Cfg = TmaCfg<D, P, FORM, T>;
-    auto kern = k_apply_tma<D, P, FORM, T, false>;
-    auto kern_f = k_apply_tma<D, P, FORM, T, true>;
+    auto kern = k_apply_tma<D, P, FORM, T>;
     TmaLaunch t;
     cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM),
-               "apply smem attribute");
-    cuda_check(cudaFuncSetAttribute(kern_f, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM),
                "apply smem attribute");
     int dev = 0, nb = 0;
     cuda_check(cudaGetDevice(&dev), "get device");
@@ -54,7 +51,7 @@ const TmaLaunch& tma_launch() {
 
 template <int D, int P, int FORM, typename T>
 void run_apply_tma(const T* A, const Ctx& c, const void* u, void* y, int R, cudaStream_t s,
-                   const int* skip, SolveWork* fuse) {
+                   const int* skip) {
   using Cfg = TmaCfg<D, P, FORM, T>;
   const TmaLaunch& L = tma_launch<D, P, FORM, T>();
   const int blocks_per_sm = L.blocks_per_sm, num_sms = L.num_sms;
@@ -63,18 +60,15 @@ void run_apply_tma(const T* A, const Ctx& c, const void* u, void* y, int R, cuda
   if (nchunks == 0) return;
   const int64_t grid = std::min<int64_t>(nchunks, (int64_t)num_sms * blocks_per_sm);
   TmaArgs<T> a{A, c.d_conn, (const T*)u, (T*)y, c.E, ntiles, nchunks, R, skip, c.d_kerr,
-                c.d_bnd, c.dirichlet ? c.nbnd : 0, c.wait_budget, c.test_skip_chunk,
-                fuse ? fuse->partial : nullptr, fuse ? fuse->counter : nullptr,
-                fuse ? fuse->scal : nullptr, fuse ? fuse->flags : nullptr};
-  if (fuse) k_apply_tma<D, P, FORM, T, true><<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
-  else k_apply_tma<D, P, FORM, T, false><<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
+                c.d_bnd, c.dirichlet ? c.nbnd : 0, c.wait_budget, c.test_skip_chunk};
+  k_apply_tma<D, P, FORM, T><<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
 }
 
-// Returns 2 when the staged kernel ran (it also wrote the Dirichlet rows and, with
-// `fuse`, the CG scalars), 1 for the one-thread-per-cell kernel.
+// Returns 2 when the staged kernel ran (it also wrote the Dirichlet rows), 1 for the
+// one-thread-per-cell kernel.
 template <int D, int P, int FORM>
 int run_apply(const Ctx& c, const void* u, void* y, int R, int prec, bool atomic, int64_t e0,
-              int64_t e1, cudaStream_t s, const int* skip, SolveWork* fuse) {
+              int64_t e1, cudaStream_t s, const int* skip) {
   constexpr bool ok64 = TmaCfg<D, P, FORM, double>::OK, ok32 = TmaCfg<D, P, FORM, float>::OK;
   if (u == nullptr) {  // preparation call from context set-up
     if constexpr (ok64) tma_launch<D, P, FORM, double>();
@@ -85,7 +79,7 @@ int run_apply(const Ctx& c, const void* u, void* y, int R, int prec, bool atomic
   if (prec == DOGIP_FP64) {
     if constexpr (ok64) {
       if (whole) {
-        run_apply_tma<D, P, FORM, double>(c.d_A64, c, u, y, R, s, skip, fuse);
+        run_apply_tma<D, P, FORM, double>(c.d_A64, c, u, y, R, s, skip);
         return 2;
       }
     }
@@ -93,7 +87,7 @@ int run_apply(const Ctx& c, const void* u, void* y, int R, int prec, bool atomic
   } else {
     if constexpr (ok32) {
       if (whole) {
-        run_apply_tma<D, P, FORM, float>(c.d_A32, c, u, y, R, s, skip, fuse);
+        run_apply_tma<D, P, FORM, float>(c.d_A32, c, u, y, R, s, skip);
         return 2;
       }
     }
@@ -106,6 +100,6 @@ int run_apply(const Ctx& c, const void* u, void* y, int R, int prec, bool atomic
 
 #define DOGIP_APPLY_CASES(D, P)                                              \
   case P * 2 + 0:                                                            \
-    return run_apply<D, P, 0>(c, u, y, R, prec, atomic, e0, e1, s, skip, fuse); \
+    return run_apply<D, P, 0>(c, u, y, R, prec, atomic, e0, e1, s, skip);     \
   case P * 2 + 1:                                                            \
-    return run_apply<D, P, 1>(c, u, y, R, prec, atomic, e0, e1, s, skip, fuse);
+    return run_apply<D, P, 1>(c, u, y, R, prec, atomic, e0, e1, s, skip);

@@ -388,7 +388,6 @@ Ctx* setup(const dogip_mesh* m, int p, int form, int coef_kind, const double* co
     c->d_err = dev_alloc<int>(1);
     c->d_kerr = dev_alloc<int>(1);
     if (const char* v = std::getenv("DOGIP_APPLY_VARIANT")) c->apply_variant = std::atoi(v);
-    if (const char* v = std::getenv("DOGIP_FUSE_PQ")) c->fuse_pq = std::atoi(v) != 0;
     // Test hooks for the device-side failure path: a shorter wait budget, and one
     // chunk of the staged apply whose copy is never issued, so that its bounded
     // wait expires (nothing faults or hangs; the kernel reports and returns).
@@ -458,12 +457,12 @@ void run_chunk(Ctx& c, int prec, int scatter, double* x64, int k, double delta) 
     try {
       for (int it = 0; it < k; ++it) {
         if (prec == DOGIP_FP64) {
-          const bool fused = launch_apply_cg(c, w.p64, w.q64, w.R, DOGIP_FP64, scatter, s, w);
-          c.launches += vec_cg_step(w, DOGIP_FP64, x64, c.d_dinv64, delta, s, fused,
+          launch_apply_cg(c, w.p64, w.q64, w.R, DOGIP_FP64, scatter, s, w);
+          c.launches += vec_cg_step(w, DOGIP_FP64, x64, c.d_dinv64, delta, s,
                                     scatter == DOGIP_SCATTER_ATOMIC);
         } else {
-          const bool fused = launch_apply_cg(c, w.p32, w.q32, w.R, DOGIP_FP32, scatter, s, w);
-          c.launches += vec_cg_step(w, DOGIP_FP32, nullptr, c.d_dinv32, delta, s, fused,
+          launch_apply_cg(c, w.p32, w.q32, w.R, DOGIP_FP32, scatter, s, w);
+          c.launches += vec_cg_step(w, DOGIP_FP32, nullptr, c.d_dinv32, delta, s,
                                     scatter == DOGIP_SCATTER_ATOMIC);
         }
       }
@@ -794,11 +793,11 @@ int batch_solve(Ctx* const* ctxs, int np, const double* const* b, double* const*
       SolveWork& w = c.work;
       for (int it = 0; it < chunk; ++it) {
         if (mixed) {
-          const bool f = launch_apply_cg(c, w.p32, w.q32, 1, DOGIP_FP32, scat, s, w);
-          c.launches += vec_cg_step(w, DOGIP_FP32, nullptr, c.d_dinv32, 0.0, s, f, true);
+          launch_apply_cg(c, w.p32, w.q32, 1, DOGIP_FP32, scat, s, w);
+          c.launches += vec_cg_step(w, DOGIP_FP32, nullptr, c.d_dinv32, 0.0, s, true);
         } else {
-          const bool f = launch_apply_cg(c, w.p64, w.q64, 1, DOGIP_FP64, scat, s, w);
-          c.launches += vec_cg_step(w, DOGIP_FP64, u[i], c.d_dinv64, 0.0, s, f, true);
+          launch_apply_cg(c, w.p64, w.q64, 1, DOGIP_FP64, scat, s, w);
+          c.launches += vec_cg_step(w, DOGIP_FP64, u[i], c.d_dinv64, 0.0, s, true);
         }
       }
       scal_copy(c, s);

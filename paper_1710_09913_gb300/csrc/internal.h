@@ -91,7 +91,6 @@ struct dogip_ctx {
   int* d_err = nullptr;        // validation flags
   int* d_kerr = nullptr;       // kernel wait timeouts (bounded mbarrier waits)
   int apply_variant = 1;       // 1: bulk-async staged apply; 0: one thread per cell
-  bool fuse_pq = true;         // staged apply reduces p.K.p inside CG iterations
   long long wait_budget = 4000000000LL;  // clock cycles per bounded wait in kernels
   int64_t test_skip_chunk = -1;  // test hook (see DOGIP_TEST_SKIP_CHUNK)
   dogip::SolveWork work;
@@ -120,9 +119,8 @@ void launch_ahat(Ctx& c, const double* coef, int coef_kind, cudaStream_t s);
 void launch_apply(Ctx& c, const void* u, void* y, int R, int prec, int scatter,
                   cudaStream_t s, const int* skip);
 // The apply inside a CG iteration, q = K p.  With atomic scatter q must already be
-// zero (the previous p update clears it); colour scatter clears it itself.  Returns
-// true when the staged kernel also produced p.q and alpha (no separate p.q kernel).
-bool launch_apply_cg(Ctx& c, const void* p, void* q, int R, int prec, int scatter,
+// zero (the previous p update clears it); colour scatter clears it itself.
+void launch_apply_cg(Ctx& c, const void* p, void* q, int R, int prec, int scatter,
                      cudaStream_t s, SolveWork& w);
 void launch_load(Ctx& c, const double* f, double* b, cudaStream_t s);
 void launch_grad(Ctx& c, const double* u, const double* lam, double* dA,
@@ -156,7 +154,7 @@ int vec_init64(SolveWork& w, const double* dinv, double tol, cudaStream_t st);
 // zero_q: clear q for the next scatter-add apply (every atomic-scatter iteration;
 // colour passes clear it themselves).
 int vec_cg_step(SolveWork& w, int prec, double* x64, const void* dinv, double delta,
-                cudaStream_t st, bool pq_fused, bool zero_q);
+                cudaStream_t st, bool zero_q);
 // Reliable-update mixed CG (FP32 recursion, FP64 corrections):
 // start: r32 = r64, x32 = 0, p = Dinv r32, rho, r0 = ||b||, rmax = ||r64||.
 int vec_rel_init(SolveWork& w, const float* dinv, double tol, cudaStream_t st);

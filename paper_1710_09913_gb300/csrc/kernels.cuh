@@ -201,8 +201,9 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> a) {
 // S-stage ring tracked by mbarriers, while the warps of the CTA compute on the
 // previous stage.  One warp owns one tile (one thread per cell) and loops over the
 // right-hand sides, reusing A_T from shared memory.  The u gathers and the atomic
-// scatter go to L2.  Every wait is bounded by a clock budget; on expiry the kernel
-// raises an error flag, drains its copies in flight (bounded again) and returns.
+// scatter go to L2; the Dirichlet rows y_b = u_b are written at the end.  Every wait
+// is bounded by a clock budget; on expiry the kernel raises an error flag, drains its
+// copies in flight (bounded again) and returns.
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -283,70 +284,9 @@ struct TmaArgs {
   int64_t nbnd;
   long long wait_budget;  // clock cycles per bounded mbarrier wait
   int64_t test_skip_chunk;  // test hook: this chunk's copy is never issued (-1: none)
-  // Optional fused CG step (all null outside solves): p.q = u^T K u from the element
-  // energies u_T . Y_T (= sum_j g_j . h_j) plus sum_b u_b^2, reduced over the grid;
-  // the last block sets alpha = rho / p.q per rhs.
-  double* partial;
-  unsigned int* counter;
-  CGScal* scal;
-  int* flags;
 };
 
-// Grid reduction of the per-block energies s_en[0..R) and, in the last block to
-// finish, alpha = rho / p.q per rhs (breakdown if p.q <= 0), then the stop flags.
-static __device__ __forceinline__ void fused_alpha(double* partial, unsigned int* counter, CGScal* scal,
-                                         int* flags, int R, double* s_en) {
-  __shared__ bool last;
-  __shared__ double fin[256];
-  __syncthreads();
-  if (threadIdx.x < R) partial[(size_t)blockIdx.x * 64 + threadIdx.x] = s_en[threadIdx.x];
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  const int G = blockDim.x / R;  // R is a power of two dividing the block
-  const int k = threadIdx.x % R, g = threadIdx.x / R;
-  double acc = 0.0;
-  if (g < G)
-    for (unsigned b = g; b < gridDim.x; b += G) acc += __ldcg(partial + (size_t)b * 64 + k);
-  fin[threadIdx.x] = acc;
-  __syncthreads();
-  for (int off = G / 2; off > 0; off >>= 1) {
-    if (threadIdx.x < off * R) fin[threadIdx.x] += fin[threadIdx.x + off * R];
-    __syncthreads();
-  }
-  if (threadIdx.x < R) {
-    CGScal& s = scal[threadIdx.x];
-    const double v = fin[threadIdx.x];
-    if (s.done) {
-      s.alpha = 0.0;
-    } else if (!(v > 0.0) || !isfinite(v)) {
-      s.brk = 1;
-      s.done = 1;
-      s.alpha = 0.0;
-    } else {
-      s.pq = v;
-      s.alpha = s.rho / v;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int all = 1, brk = 0;
-    for (int r = 0; r < R; ++r) {
-      all &= scal[r].done;
-      brk |= scal[r].brk;
-    }
-    flags[0] = all;
-    flags[1] = brk;
-    flags[2] = all;
-    flags[3] = 0;
-    *counter = 0u;
-  }
-}
-
-template <int D, int P, int FORM, typename T, bool FUSED>
+template <int D, int P, int FORM, typename T>
 __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T>::THREADS)
     k_apply_tma(TmaArgs<T> a) {
   using C = TmaCfg<D, P, FORM, T>;
@@ -360,9 +300,6 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T>::THREADS)
   if (a.skip != nullptr && *a.skip) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t G = gridDim.x;
-  constexpr bool fused = FUSED;  // a.partial etc. are set exactly when FUSED
-  __shared__ double s_en[32];
-  if (tid < 32) s_en[tid] = 0.0;
   if (tid == 0) {
     for (int s = 0; s < C::S; ++s) mbar_init(&bars[s], 1);
     mbar_fence_init();
@@ -404,8 +341,7 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T>::THREADS)
       constexpr int l = decltype(lc)::value;
       c[l] = active ? sC[l * kTile] : kBndBit;
     });
-    for (int r = 0; r < a.R; ++r) {  // uniform over the warp (the shuffles below)
-      T en = T(0);
+    for (int r = 0; r < a.R; ++r) {
       if (active) {
         T ul[V], Y[V];
         static_for<V>([&](auto lc) {
@@ -424,23 +360,10 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T>::THREADS)
           block_mul<D, FORM>(aj, g, h);
           project<TB, j>(h, Y);
         });
-        if constexpr (FUSED) {
-          // element energy u_T^T K_T u_T = sum_j g_j . h_j = u_T . (B^T h) = u_T . Y_T
-          static_for<V>([&](auto lc) {
-            constexpr int l = decltype(lc)::value;
-            en = fma(ul[l], Y[l], en);
-          });
-        }
         static_for<V>([&](auto lc) {
           constexpr int l = decltype(lc)::value;
           if (!(c[l] & kBndBit)) atomicAdd(a.y + (int64_t)(c[l] & kIdMask) * a.R + r, Y[l]);
         });
-      }
-      if constexpr (FUSED) {  // warp sum, then one shared-memory add per warp
-        double v = (double)en;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if (lane == 0) atomicAdd(&s_en[r], v);
       }
     }
     __syncthreads();  // every read of stage s is done
@@ -460,25 +383,12 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T>::THREADS)
     }
     __syncthreads();
   }
-  // Dirichlet rows: y_b = u_b (the scatter skipped them), and u_b^2 for p.q
-  double bsum = 0.0;
+  // Dirichlet rows: y_b = u_b (the scatter skipped them)
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + tid; t < a.nbnd * a.R;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(t % a.R);
-    const int64_t idx = (int64_t)a.bnd[t / a.R] * a.R + r;
-    const T ub = a.u[idx];
-    a.y[idx] = ub;
-    if (fused) {
-      if (a.R == 1) bsum += (double)ub * (double)ub;
-      else atomicAdd(&s_en[r], (double)ub * (double)ub);
-    }
+    const int64_t idx = (int64_t)a.bnd[t / a.R] * a.R + (t % a.R);
+    a.y[idx] = a.u[idx];
   }
-  if (fused && a.R == 1) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) bsum += __shfl_xor_sync(0xffffffffu, bsum, off);
-    if (lane == 0 && bsum != 0.0) atomicAdd(&s_en[0], bsum);
-  }
-  if constexpr (FUSED) fused_alpha(a.partial, a.counter, a.scal, a.flags, a.R, s_en);
 }
 
 // ------------------------------------------------------------------ setup

@@ -7,20 +7,20 @@
 namespace dogip {
 
 // Apply dispatchers (apply_d*.cu): 0 = not compiled, 1 = per-cell kernel, 2 = staged
-// kernel (which also wrote the Dirichlet rows and, with `fuse`, the CG scalars).
+// kernel (which also wrote the Dirichlet rows).
 int apply_d2(const Ctx&, const void*, void*, int, int, bool, int64_t, int64_t, cudaStream_t,
-             const int*, SolveWork*);
+             const int*);
 int apply_d3a(const Ctx&, const void*, void*, int, int, bool, int64_t, int64_t, cudaStream_t,
-              const int*, SolveWork*);
+              const int*);
 int apply_d3b(const Ctx&, const void*, void*, int, int, bool, int64_t, int64_t, cudaStream_t,
-              const int*, SolveWork*);
+              const int*);
 
 namespace {
 int apply_dispatch(const Ctx& c, const void* u, void* y, int R, int prec, bool atomic, int64_t e0,
-                   int64_t e1, cudaStream_t s, const int* skip, SolveWork* fuse) {
-  if (c.d == 2) return apply_d2(c, u, y, R, prec, atomic, e0, e1, s, skip, fuse);
-  if (c.p <= 2) return apply_d3a(c, u, y, R, prec, atomic, e0, e1, s, skip, fuse);
-  if (c.p == 3) return apply_d3b(c, u, y, R, prec, atomic, e0, e1, s, skip, fuse);
+                   int64_t e1, cudaStream_t s, const int* skip) {
+  if (c.d == 2) return apply_d2(c, u, y, R, prec, atomic, e0, e1, s, skip);
+  if (c.p <= 2) return apply_d3a(c, u, y, R, prec, atomic, e0, e1, s, skip);
+  if (c.p == 3) return apply_d3b(c, u, y, R, prec, atomic, e0, e1, s, skip);
   return 0;
 }
 }  // namespace
@@ -188,26 +188,24 @@ void launch_dirichlet_copy(const Ctx& c, const void* u, void* y, int R, int prec
 }
 
 void prepare_apply(Ctx& c) {
-  if (!apply_dispatch(c, nullptr, nullptr, 1, 0, true, 0, 0, nullptr, nullptr, nullptr))
+  if (!apply_dispatch(c, nullptr, nullptr, 1, 0, true, 0, 0, nullptr, nullptr))
     fail(DOGIP_EUNSUPPORTED, "no compiled apply instance for this (dim, p, form)");
 }
 
-bool launch_apply_cg(Ctx& c, const void* p, void* q, int R, int prec, int scatter, cudaStream_t s,
+void launch_apply_cg(Ctx& c, const void* p, void* q, int R, int prec, int scatter, cudaStream_t s,
                      SolveWork& w) {
   if (scatter == DOGIP_SCATTER_ATOMIC) {
-    const int k = apply_dispatch(c, p, q, R, prec, true, 0, c.E, s, w.flags, c.fuse_pq ? &w : nullptr);
+    const int k = apply_dispatch(c, p, q, R, prec, true, 0, c.E, s, w.flags);
     if (!k) fail(DOGIP_EUNSUPPORTED, "no compiled apply instance for this (dim, p, form)");
     cuda_check(cudaGetLastError(), "apply kernel launch");
     c.launches += 1;
-    if (k == 2) return c.fuse_pq;  // the staged kernel also wrote the Dirichlet rows
-    if (c.dirichlet && c.nbnd > 0) {
+    if (k == 1 && c.dirichlet && c.nbnd > 0) {  // the staged kernel writes these itself
       launch_dirichlet_copy(c, p, q, R, prec, s, w.flags);
       c.launches += 1;
     }
-    return false;
+    return;
   }
   launch_apply(c, p, q, R, prec, scatter, s, w.flags);  // colour passes (memset inside)
-  return false;
 }
 
 void launch_apply(Ctx& c, const void* u, void* y, int R, int prec, int scatter, cudaStream_t s,
@@ -216,7 +214,7 @@ void launch_apply(Ctx& c, const void* u, void* y, int R, int prec, int scatter, 
   cuda_check(cudaMemsetAsync(y, 0, es * c.n * R, s), "memset y");
   bool staged = false;
   auto run = [&](bool atomic, int64_t e0, int64_t e1) {
-    const int k = apply_dispatch(c, u, y, R, prec, atomic, e0, e1, s, skip, nullptr);
+    const int k = apply_dispatch(c, u, y, R, prec, atomic, e0, e1, s, skip);
     if (!k) fail(DOGIP_EUNSUPPORTED, "no compiled apply instance for this (dim, p, form)");
     staged = staged || k == 2;
   };

@@ -439,14 +439,14 @@ int vec_init64(SolveWork& w, const double* dinv, double tol, cudaStream_t st) {
 }
 
 int vec_cg_step(SolveWork& w, int prec, double* x64, const void* dinv, double delta,
-                cudaStream_t st, bool pq_fused, bool zero_q) {
+                cudaStream_t st, bool zero_q) {
   const int64_t N = w.n * w.R;
   Red rd = red_of(w);
   const unsigned nb = red_blocks(N);
   if (prec == DOGIP_FP64) {
     const double* di = (const double*)dinv;
 #define CALL(RR)                                                                           \
-  if (!pq_fused) k_pq<double, RR><<<nb, kRedThreads, 0, st>>>(w.p64, w.q64, N, rd);        \
+  k_pq<double, RR><<<nb, kRedThreads, 0, st>>>(w.p64, w.q64, N, rd);                       \
   k_update<double, RR><<<nb, kRedThreads, 0, st>>>(x64, w.r64, w.p64, w.q64, di, N, delta, rd); \
   k_pupdate<double, RR><<<nb, kRedThreads, 0, st>>>(w.p64, w.r64, di, N, w.scal, w.flags,  \
                                                      zero_q ? w.q64 : nullptr)
@@ -455,7 +455,7 @@ int vec_cg_step(SolveWork& w, int prec, double* x64, const void* dinv, double de
   } else {
     const float* di = (const float*)dinv;
 #define CALL(RR)                                                                           \
-  if (!pq_fused) k_pq<float, RR><<<nb, kRedThreads, 0, st>>>(w.p32, w.q32, N, rd);         \
+  k_pq<float, RR><<<nb, kRedThreads, 0, st>>>(w.p32, w.q32, N, rd);                        \
   k_update<float, RR><<<nb, kRedThreads, 0, st>>>(w.x32, w.r32, w.p32, w.q32, di, N, delta, rd); \
   k_pupdate<float, RR><<<nb, kRedThreads, 0, st>>>(w.p32, w.r32, di, N, w.scal, w.flags,   \
                                                     zero_q ? w.q32 : nullptr)
@@ -463,7 +463,7 @@ int vec_cg_step(SolveWork& w, int prec, double* x64, const void* dinv, double de
 #undef CALL
   }
   cuda_check(cudaGetLastError(), "cg step kernels");
-  return pq_fused ? 2 : 3;
+  return 3;
 }
 
 int vec_rel_init(SolveWork& w, const float* dinv, double tol, cudaStream_t st) {
