@@ -326,6 +326,7 @@ def main():
     ap.add_argument("--check-every", type=int, default=32)
     ap.add_argument("--no-csr", action="store_true", help="skip the assembled-CSR comparison")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven solve")
+    ap.add_argument("--no-3d", action="store_true", help="skip the 3D 16-right-hand-side case")
     ap.add_argument("--only-apply", type=int, default=0, metavar="P",
                     help="profiling mode: only run --reps applies of order P (no JSON line)")
     ap.add_argument("--only-solve", type=int, default=0, metavar="P",
@@ -352,8 +353,10 @@ def main():
     E = len(cells)
     A_dev = torch.tensor(A, device="cuda")
     ctxs, bs, us = {}, {}, {}
+    tuned = {}
     for p in P_LIST:
         ctxs[p] = B.Context(coords, cells, p, "elliptic", A)
+        tuned[f"P{p}"] = ctxs[p].autotune()  # apply kernel per precision (timed on this data)
         bs[p] = torch.empty(ctxs[p].n, dtype=torch.float64, device="cuda")
         us[p] = torch.zeros(ctxs[p].n, dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -503,6 +506,7 @@ def main():
             bc, bcl = inputs.lattice_mesh(2, N)
             m = inputs.coef_lognormal(len(bcl), 1.0, sd)
             c = B.Context(bc, bcl, p, "elliptic", m)
+            c.autotune()  # cached per (p, size bucket) after the first of each kind
             bctx.append(c)
             bb.append(c.load())
             bu.append(torch.zeros(c.n, dtype=torch.float64, device="cuda"))
@@ -528,6 +532,58 @@ def main():
                  "all_converged": all(i["status"] == 0 for i in infos),
                  "gpu_launches": int(sum(c.launches() for c in bctx) - l0)}
         del bctx, bb, bu
+
+    # 3D, 64^3 cube x 6 tetrahedra, P2, inclusions, 16 right-hand sides in one launch
+    multi = None
+    if not args.no_3d:
+        from paper_1710_09913_gb300 import inputs
+        c3, t3 = inputs.lattice_mesh(3, 64)
+        m3 = inputs.coef_inclusions(inputs.centroids(c3, t3), 200, 0.03, 0.08, seed=3)
+        multi = {}
+        R = 16
+        for form in ("elliptic", "projection"):
+            c = B.Context(c3, t3, 2, form, m3)
+            c.autotune()
+            b3 = torch.tensor(inputs.rhs_normal(c.n, R, seed=3), device="cuda")
+            if form == "elliptic":
+                b3[torch.tensor(c.boundary(), device="cuda")] = 0.0
+            out = {"dofs": c.n, "rhs": R}
+            for prec, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
+                x = b3.to(dt).contiguous()
+                y = torch.empty_like(x)
+                for _ in range(2):
+                    c.apply(x, y, prec=prec)
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                ev0.record(stream)
+                reps = 5
+                for _ in range(reps):
+                    c.apply(x, y, prec=prec)
+                ev1.record(stream)
+                torch.cuda.synchronize()
+                ms = ev0.elapsed_time(ev1) / reps
+                inf = c.info
+                byt = (c.E * inf.w_loc * inf.n_sym * dt.itemsize + c.E * inf.v_loc * 4
+                       + 2 * c.n * R * dt.itemsize)
+                out[f"apply_{prec}_ms"] = round(ms, 4)
+                out[f"apply_{prec}_gdofs"] = round(c.n * R / ms / 1e6, 3)
+                out[f"apply_{prec}_GBps"] = round(byt / ms / 1e6, 1)
+            u3 = torch.zeros_like(b3)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            _, info = c.solve(b3, u3, mode="mixed", tol=TOL, check_every=args.check_every,
+                              allow_notconv=True)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            out.update(mixed_ms=round(ev0.elapsed_time(ev1), 2), mixed_iters=info["iterations"],
+                       mixed_outer=info["outer"], max_rel_residual=float(info["rel_per_rhs"].max()),
+                       status=info["status"])
+            multi[form] = out
+            del c, b3, u3
+            torch.cuda.empty_cache()
 
     dom = applies["P4_fp32"]
     roofline = {"bound": "hbm", "achieved": dom["GBps"], "peak": hbm, "unit": "GB/s",
@@ -577,10 +633,12 @@ def main():
                 "config": {"workload": WORKLOAD, "cells": E, "p": list(P_LIST),
                            "dofs": {f"P{p}": ctxs[p].n for p in P_LIST}, "tol": TOL,
                            "l2": "flushed between steps (512 MiB write)",
+                           "apply_kernel": tuned,
                            "parallelism": "replicas (independent problems per GPU)"},
                 "value_definition": "sum_p n_p x operator applies / step time (applies inside the "
                                     "mixed solves, FP32 inner and FP64 residual)",
                 "time_to_tol": t2t, "apply": applies, "csr_baseline": csr, "batch_uneven": batch,
+                "cube_p2_16rhs": multi,
                 "roofline": roofline,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks}
         print(json.dumps(line), flush=True)

@@ -251,6 +251,26 @@ DOGIP_API int dogip_solve_host(dogip_ctx* ctx, const double* b_host, double* u_h
                      dogip_solve_info* info, double* rel_residual_per_rhs,
                      void* cuda_stream);
 
+/* --------------------------------------------------------------- autotuner */
+typedef struct {
+  int variant[2]; /* per precision (index DOGIP_FP64 / DOGIP_FP32): 1 staged kernel,
+                     0 one thread per cell                                    */
+  int block[2];   /* cells per CTA of the one-thread-per-cell kernel          */
+} dogip_tune_info;
+
+/*
+ * Choose the apply kernel of this context per precision by timing the candidates
+ * on its own data: the bulk-async staged kernel, and the one-thread-per-cell kernel
+ * with 64, 128 or 256 cells per CTA (median of 5 CUDA-event timings after 2 warm-up
+ * applies, atomic scatter, one right-hand side).  Choices are cached for the process
+ * per (dim, p, form, precision, log2 cells) and reused without timing unless
+ * force != 0; the environment variable DOGIP_TUNE_CACHE names a text file the cache
+ * is read from and appended to.  Allocates two temporary vectors (stream-ordered)
+ * and synchronises cuda_stream.  info: host or NULL.  Not part of the paper.
+ */
+DOGIP_API int dogip_autotune(dogip_ctx* ctx, int force, dogip_tune_info* info,
+                             void* cuda_stream);
+
 /* ---------------------------------------------------------- batched solves */
 /*
  * Solve nprob independent problems K_i u_i = b_i together (one right-hand side

@@ -65,6 +65,10 @@ class Info(C.Structure):
                 ("kernel_launches", C.c_int64)]
 
 
+class TuneInfo(C.Structure):
+    _fields_ = [("variant", C.c_int * 2), ("block", C.c_int * 2)]
+
+
 class SolveOpts(C.Structure):
     _fields_ = [("mode", C.c_int), ("tol", C.c_double), ("maxiter", C.c_int),
                 ("inner_tol", C.c_double), ("inner_maxiter", C.c_int), ("max_outer", C.c_int),
@@ -101,6 +105,7 @@ _SIGS = {
                                    C.POINTER(SolveInfo), _vp, _vp]),
     "dogip_grad_coef": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "dogip_check": (C.c_int, [_vp, _vp]),
+    "dogip_autotune": (C.c_int, [_vp, C.c_int, C.POINTER(TuneInfo), _vp]),
     "dogip_batch_solve": (C.c_int, [C.POINTER(_vp), C.c_int, C.POINTER(_vp), C.POINTER(_vp),
                                     C.POINTER(SolveOpts), C.POINTER(SolveInfo), _vp]),
     "dogip_residual_norms_noalloc": (C.c_int, [_vp, _vp, _vp, C.c_int64, C.c_int, _vp, _vp]),
@@ -344,6 +349,13 @@ class Context:
                                     rel.ctypes.data_as(_vp), _stream(stream)))
         return dict(status=inf.status, iterations=inf.iterations, outer=inf.outer,
                     rel_residual=inf.rel_residual, seconds=inf.seconds)
+
+    def autotune(self, force=False, stream=None):
+        """Pick the apply kernel per precision by timing (dogip_autotune); returns
+        {precision: (variant, cells per CTA)}."""
+        t = TuneInfo()
+        _check(lib.dogip_autotune(self._h, int(force), C.byref(t), _stream(stream)))
+        return {"fp64": (t.variant[FP64], t.block[FP64]), "fp32": (t.variant[FP32], t.block[FP32])}
 
     def check(self, stream=None):
         """Synchronise and raise if a kernel-side bounded wait expired."""

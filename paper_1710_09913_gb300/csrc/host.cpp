@@ -6,6 +6,9 @@
 #include <cmath>
 #include <cstring>
 #include <functional>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -895,6 +898,130 @@ int batch_solve(Ctx* const* ctxs, int np, const double* const* b, double* const*
   return status;
 }
 
+
+// --------------------------------------------------------------- autotuner
+//
+// Picks, per precision, the apply kernel (bulk-async staged, or one thread per
+// cell with 64 / 128 / 256 cells per CTA) by timing each on the context's own data
+// (CUDA events, median of 5 after 2 warm-up applies).  Choices are cached process-
+// wide per (dim, p, form, precision, log2 of the cell count); with DOGIP_TUNE_CACHE
+// set they are also read from and appended to that text file.
+
+struct TuneKey {
+  int d, p, form, prec, logE;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(d, p, form, prec, logE) < std::tie(o.d, o.p, o.form, o.prec, o.logE);
+  }
+};
+struct TuneChoice {
+  int variant, block;
+  float ms;
+};
+std::mutex g_tune_mutex;
+std::map<TuneKey, TuneChoice> g_tune;
+bool g_tune_loaded = false;
+
+void tune_load_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = std::getenv("DOGIP_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  TuneKey k;
+  TuneChoice ch;
+  while (std::fscanf(f, "%d %d %d %d %d %d %d %f", &k.d, &k.p, &k.form, &k.prec, &k.logE,
+                     &ch.variant, &ch.block, &ch.ms) == 8)
+    g_tune[k] = ch;
+  std::fclose(f);
+}
+
+void tune_store_locked(const TuneKey& k, const TuneChoice& ch) {
+  g_tune[k] = ch;
+  const char* path = std::getenv("DOGIP_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%d %d %d %d %d %d %d %.6f\n", k.d, k.p, k.form, k.prec, k.logE, ch.variant,
+               ch.block, ch.ms);
+  std::fclose(f);
+}
+
+int autotune(Ctx& c, int force, cudaStream_t s) {
+  DeviceGuard guard(c.device);
+  int logE = 0;
+  while ((int64_t(1) << logE) < c.E) ++logE;
+  int tuned = 0;
+  for (int prec : {DOGIP_FP32, DOGIP_FP64}) {
+    if (prec == DOGIP_FP32 && !c.keep32) continue;
+    const TuneKey key{c.d, c.p, c.form, prec, logE};
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mutex);
+      tune_load_locked();
+      auto it = g_tune.find(key);
+      if (it != g_tune.end() && !force) {
+        c.apply_variant_prec[prec] = it->second.variant;
+        c.apply_block[prec] = it->second.block;
+        continue;
+      }
+    }
+    const size_t es = prec == DOGIP_FP64 ? 8 : 4;
+    void *u = nullptr, *y = nullptr;
+    cuda_check(cudaMallocAsync(&u, es * c.n, s), "tuning buffers");
+    if (cudaMallocAsync(&y, es * c.n, s) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFreeAsync(u, s);
+      fail(DOGIP_ENOMEM, "tuning buffers");
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    TuneChoice best{1, 256, 1e30f};
+    try {
+      cuda_check(cudaMemsetAsync(u, 0, es * c.n, s), "tuning input");
+      cuda_check(cudaEventCreate(&e0), "event");
+      cuda_check(cudaEventCreate(&e1), "event");
+      // staged, staged with two warps per tile (falls back to staged where not
+      // compiled), one thread per cell with 64 / 128 / 256 cells per CTA
+      const std::pair<int, int> cands[] = {{1, 256}, {2, 256}, {0, 64}, {0, 128}, {0, 256}};
+      for (auto [var, blk] : cands) {
+        c.apply_variant_prec[prec] = var;
+        c.apply_block[prec] = blk;
+        for (int w = 0; w < 2; ++w) launch_apply(c, u, y, 1, prec, DOGIP_SCATTER_ATOMIC, s, nullptr);
+        std::vector<float> t(5);
+        for (float& ti : t) {
+          cuda_check(cudaEventRecord(e0, s), "event record");
+          launch_apply(c, u, y, 1, prec, DOGIP_SCATTER_ATOMIC, s, nullptr);
+          cuda_check(cudaEventRecord(e1, s), "event record");
+          cuda_check(cudaEventSynchronize(e1), "tuning sync");
+          cuda_check(cudaEventElapsedTime(&ti, e0, e1), "elapsed");
+        }
+        std::sort(t.begin(), t.end());
+        if (t[2] < best.ms) best = TuneChoice{var, blk, t[2]};
+      }
+    } catch (...) {
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+      cudaFreeAsync(u, s);
+      cudaFreeAsync(y, s);
+      throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cuda_check(cudaFreeAsync(u, s), "tuning buffers");
+    cuda_check(cudaFreeAsync(y, s), "tuning buffers");
+    c.apply_variant_prec[prec] = best.variant;
+    c.apply_block[prec] = best.block;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    tune_store_locked(key, best);
+    ++tuned;
+  }
+  // captured solver graphs hold the old launch shapes
+  if (c.work.graph) {
+    cudaGraphExecDestroy(c.work.graph);
+    c.work.graph = nullptr;
+  }
+  return tuned;
+}
+
 template <typename F>
 int guarded(F&& f) {
   try {
@@ -1142,6 +1269,20 @@ int dogip_solve_host(dogip_ctx* c, const double* bh, double* uh, int nrhs,
     dogip::cuda_check(cudaFreeAsync(du, s), "staging free");
     dogip::cuda_check(cudaStreamSynchronize(s), "solve_host sync");
     return st;
+  });
+}
+
+int dogip_autotune(dogip_ctx* c, int force, dogip_tune_info* info, void* stream) {
+  return guarded([&] {
+    if (!c) fail(DOGIP_EINVAL, "ctx is required");
+    dogip::autotune(*c, force, (cudaStream_t)stream);
+    if (info) {
+      for (int pr = 0; pr < 2; ++pr) {
+        info->variant[pr] = c->apply_variant_prec[pr] >= 0 ? c->apply_variant_prec[pr] : c->apply_variant;
+        info->block[pr] = c->apply_block[pr];
+      }
+    }
+    return DOGIP_OK;
   });
 }
 

@@ -344,3 +344,22 @@ def test_config_small_fp64_pcg(B, form):
     assert info["status"] == 0 and info["rel_residual"] <= 1e-10
     ref = _direct(P, b)
     assert np.linalg.norm(x.cpu().numpy() - ref) <= 1e-8 * np.linalg.norm(ref)
+
+
+def test_autotune_keeps_parity(B):
+    """dogip_autotune picks a kernel per precision from the candidates; the tuned
+    apply still matches the oracle, and a second context of the same kind reuses
+    the cached choice."""
+    ctx, P = make(B, 2, 3, "elliptic", 40)
+    choice = ctx.autotune()
+    for prec in ("fp64", "fp32"):
+        var, blk = choice[prec]
+        assert (var, blk) in {(1, 256), (0, 64), (0, 128), (0, 256)}
+    u = inputs.rhs_normal(P.n, 1, seed=8)[:, 0]
+    y = ctx.apply(torch.tensor(u, device="cuda")).cpu().numpy()
+    assert np.all(np.abs(y - P.apply(u)) <= TOL64 * P.apply_abs(u))
+    u32 = u.astype(np.float32)
+    y32 = ctx.apply(torch.tensor(u32, device="cuda"), prec="fp32").cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(y32 - P.apply(u32.astype(np.float64))) <= TOL32 * P.apply_abs(u32.astype(np.float64)))
+    ctx2, _ = make(B, 2, 3, "elliptic", 40, seed=2)
+    assert ctx2.autotune() == choice
