@@ -18,6 +18,17 @@ namespace {
 
 constexpr int kNV = 2;  // values reduced per rhs
 
+// 16-byte vector of T (4 floats or 2 doubles) for the one-rhs streaming loops.
+template <typename T>
+struct alignas(16) Vec16 {
+  static constexpr int L = 16 / sizeof(T);
+  T v[L];
+};
+template <typename T>
+__device__ __forceinline__ bool aligned16(const T* p) {
+  return ((uintptr_t)p & 15u) == 0;
+}
+
 struct Red {
   double* partial;
   unsigned int* counter;
@@ -100,9 +111,10 @@ __device__ __forceinline__ void set_all_done(const Red& rd, int R) {
   *rd.counter = 0u;
 }
 
+// Two CTAs of 256 threads per SM (152 SMs), at least 8 elements per thread.
 unsigned red_blocks(int64_t N) {
-  int64_t b = (N + 4 * kRedThreads - 1) / (4 * kRedThreads);  // >= 4 elements per thread
-  if (b > kMaxRedBlocks) b = kMaxRedBlocks;
+  int64_t b = (N + 8 * kRedThreads - 1) / (8 * kRedThreads);
+  if (b > 2 * 152) b = 2 * 152;
   if (b < 1) b = 1;
   return (unsigned)b;
 }
@@ -114,9 +126,25 @@ __global__ void __launch_bounds__(kRedThreads) k_pq(const T* __restrict__ p, con
   if (rd.flags[0]) return;
   double acc[1] = {0.0};
   T a = T(0);
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += stride)
-    a += p[i] * q[i];
+  int64_t head = 0;
+  if constexpr (R == 1) {
+    if (aligned16(p) && aligned16(q)) {
+      using V = Vec16<T>;
+      const int64_t nv = N / V::L;
+      const V* p4 = (const V*)p;
+      const V* q4 = (const V*)q;
+#pragma unroll 2
+      for (int64_t k = t0; k < nv; k += stride) {
+        const V pv = p4[k], qv = q4[k];
+#pragma unroll
+        for (int e = 0; e < V::L; ++e) a += pv.v[e] * qv.v[e];
+      }
+      head = nv * V::L;
+    }
+  }
+  for (int64_t i = head + t0; i < N; i += stride) a += p[i] * q[i];
   acc[0] = (double)a;
   __shared__ double tot[R];
   if (!grid_reduce<R, 1>(rd, acc, tot)) return;
@@ -150,7 +178,34 @@ __global__ void __launch_bounds__(kRedThreads) k_update(T* __restrict__ x, T* __
   const T al = (T)rd.scal[t0 % R].alpha;
   T a0 = T(0), a1 = T(0);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = t0; i < N; i += stride) {
+  int64_t head = 0;
+  if constexpr (R == 1) {
+    if (aligned16(x) && aligned16(r) && aligned16(p) && aligned16(q) && aligned16(dinv)) {
+      using V = Vec16<T>;
+      const int64_t nv = N / V::L;
+      V* x4 = (V*)x;
+      V* r4 = (V*)r;
+      const V* p4 = (const V*)p;
+      const V* q4 = (const V*)q;
+      const V* d4 = (const V*)dinv;
+#pragma unroll 2
+      for (int64_t k = t0; k < nv; k += stride) {
+        V xv = x4[k], rv = r4[k];
+        const V pv = p4[k], qv = q4[k], dv = d4[k];
+#pragma unroll
+        for (int e = 0; e < V::L; ++e) {
+          xv.v[e] += al * pv.v[e];
+          rv.v[e] -= al * qv.v[e];
+          a0 += rv.v[e] * (dv.v[e] * rv.v[e]);
+          a1 += rv.v[e] * rv.v[e];
+        }
+        x4[k] = xv;
+        r4[k] = rv;
+      }
+      head = nv * V::L;
+    }
+  }
+  for (int64_t i = head + t0; i < N; i += stride) {
     x[i] += al * p[i];
     const T ri = r[i] - al * q[i];
     r[i] = ri;
@@ -188,12 +243,39 @@ __global__ void __launch_bounds__(kRedThreads) k_pupdate(T* __restrict__ p, cons
   if (flags[0]) return;
   const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  if (qzero != nullptr)
-    for (int64_t i = t0; i < N; i += stride) qzero[i] = T(0);
   const CGScal& s = scal[t0 % R];
-  if (s.done) return;
+  const bool upd = !s.done;
   const T be = (T)s.beta;
-  for (int64_t i = t0; i < N; i += stride) p[i] = dinv[i / R] * r[i] + be * p[i];
+  int64_t head = 0;
+  if constexpr (R == 1) {
+    if (aligned16(p) && aligned16(r) && aligned16(dinv) && (qzero == nullptr || aligned16(qzero))) {
+      using V = Vec16<T>;
+      const int64_t nv = N / V::L;
+      V* p4 = (V*)p;
+      const V* r4 = (const V*)r;
+      const V* d4 = (const V*)dinv;
+      V* q4 = (V*)qzero;
+      V zero;
+#pragma unroll
+      for (int e = 0; e < V::L; ++e) zero.v[e] = T(0);
+#pragma unroll 2
+      for (int64_t k = t0; k < nv; k += stride) {
+        if (q4 != nullptr) q4[k] = zero;
+        if (upd) {
+          V pv = p4[k];
+          const V rv = r4[k], dv = d4[k];
+#pragma unroll
+          for (int e = 0; e < V::L; ++e) pv.v[e] = dv.v[e] * rv.v[e] + be * pv.v[e];
+          p4[k] = pv;
+        }
+      }
+      head = nv * V::L;
+    }
+  }
+  for (int64_t i = head + t0; i < N; i += stride) {
+    if (qzero != nullptr) qzero[i] = T(0);
+    if (upd) p[i] = dinv[i / R] * r[i] + be * p[i];
+  }
 }
 
 // Start of a PCG run from the residual r: p = Dinv r, rho = r.p, r0.
