@@ -28,17 +28,13 @@ struct TmaLaunch {
   int blocks_per_sm = 1, num_sms = 1;
 };
 
-// Split (two warps per tile) instances exist where the W-node loop is long enough.
-template <int D, int P, int FORM>
-constexpr bool kHasSplit = dogip_tab::Tab<D, P, FORM>::W >= 6;
-
 // Kernel attributes and residency of one instance, set once (thread-safe static);
 // first called from context set-up, outside any stream capture.
-template <int D, int P, int FORM, typename T, int SPLIT>
+template <int D, int P, int FORM, typename T>
 const TmaLaunch& tma_launch() {
   static const TmaLaunch info = [] {
-    using Cfg = TmaCfg<D, P, FORM, T, SPLIT>;
-    auto kern = k_apply_tma<D, P, FORM, T, SPLIT>;
+    using Cfg = TmaCfg<D, P, FORM, T>;
+    auto kern = k_apply_tma<D, P, FORM, T>;
     TmaLaunch t;
     cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM),
                "apply smem attribute");
@@ -53,11 +49,11 @@ const TmaLaunch& tma_launch() {
   return info;
 }
 
-template <int D, int P, int FORM, typename T, int SPLIT>
+template <int D, int P, int FORM, typename T>
 void run_apply_tma(const T* A, const Ctx& c, const void* u, void* y, int R, cudaStream_t s,
                    const int* skip) {
-  using Cfg = TmaCfg<D, P, FORM, T, SPLIT>;
-  const TmaLaunch& L = tma_launch<D, P, FORM, T, SPLIT>();
+  using Cfg = TmaCfg<D, P, FORM, T>;
+  const TmaLaunch& L = tma_launch<D, P, FORM, T>();
   const int blocks_per_sm = L.blocks_per_sm, num_sms = L.num_sms;
   const int64_t ntiles = (c.E + kTile - 1) / kTile;
   const int64_t nchunks = (ntiles + Cfg::TPC - 1) / Cfg::TPC;
@@ -65,7 +61,7 @@ void run_apply_tma(const T* A, const Ctx& c, const void* u, void* y, int R, cuda
   const int64_t grid = std::min<int64_t>(nchunks, (int64_t)num_sms * blocks_per_sm);
   TmaArgs<T> a{A, c.d_conn, (const T*)u, (T*)y, c.E, ntiles, nchunks, R, skip, c.d_kerr,
                 c.d_bnd, c.dirichlet ? c.nbnd : 0, c.wait_budget, c.test_skip_chunk};
-  k_apply_tma<D, P, FORM, T, SPLIT><<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
+  k_apply_tma<D, P, FORM, T><<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
 }
 
 // Returns 2 when the staged kernel ran (it also wrote the Dirichlet rows), 1 for the
@@ -74,27 +70,18 @@ template <int D, int P, int FORM>
 int run_apply(const Ctx& c, const void* u, void* y, int R, int prec, bool atomic, int64_t e0,
               int64_t e1, cudaStream_t s, const int* skip) {
   constexpr bool ok64 = TmaCfg<D, P, FORM, double>::OK, ok32 = TmaCfg<D, P, FORM, float>::OK;
-  constexpr bool split = kHasSplit<D, P, FORM>;
   if (u == nullptr) {  // preparation call from context set-up
-    if constexpr (ok64) tma_launch<D, P, FORM, double, 1>();
-    if constexpr (ok32) tma_launch<D, P, FORM, float, 1>();
-    if constexpr (ok64 && split) tma_launch<D, P, FORM, double, 2>();
-    if constexpr (ok32 && split) tma_launch<D, P, FORM, float, 2>();
+    if constexpr (ok64) tma_launch<D, P, FORM, double>();
+    if constexpr (ok32) tma_launch<D, P, FORM, float>();
     return 1;
   }
-  // variant: 1 staged, 2 staged with two warps per tile, 0 one thread per cell
+  // variant: 1 staged, 0 one thread per cell
   const int var = c.apply_variant_prec[prec] >= 0 ? c.apply_variant_prec[prec] : c.apply_variant;
-  const bool whole = atomic && e0 == 0 && e1 == c.E && var >= 1;
+  const bool whole = atomic && e0 == 0 && e1 == c.E && var == 1;
   if (prec == DOGIP_FP64) {
     if constexpr (ok64) {
       if (whole) {
-        if constexpr (split) {
-          if (var == 2) {
-            run_apply_tma<D, P, FORM, double, 2>(c.d_A64, c, u, y, R, s, skip);
-            return 2;
-          }
-        }
-        run_apply_tma<D, P, FORM, double, 1>(c.d_A64, c, u, y, R, s, skip);
+        run_apply_tma<D, P, FORM, double>(c.d_A64, c, u, y, R, s, skip);
         return 2;
       }
     }
@@ -102,13 +89,7 @@ int run_apply(const Ctx& c, const void* u, void* y, int R, int prec, bool atomic
   } else {
     if constexpr (ok32) {
       if (whole) {
-        if constexpr (split) {
-          if (var == 2) {
-            run_apply_tma<D, P, FORM, float, 2>(c.d_A32, c, u, y, R, s, skip);
-            return 2;
-          }
-        }
-        run_apply_tma<D, P, FORM, float, 1>(c.d_A32, c, u, y, R, s, skip);
+        run_apply_tma<D, P, FORM, float>(c.d_A32, c, u, y, R, s, skip);
         return 2;
       }
     }

@@ -979,9 +979,8 @@ int autotune(Ctx& c, int force, cudaStream_t s) {
       cuda_check(cudaMemsetAsync(u, 0, es * c.n, s), "tuning input");
       cuda_check(cudaEventCreate(&e0), "event");
       cuda_check(cudaEventCreate(&e1), "event");
-      // staged, staged with two warps per tile (falls back to staged where not
-      // compiled), one thread per cell with 64 / 128 / 256 cells per CTA
-      const std::pair<int, int> cands[] = {{1, 256}, {2, 256}, {0, 64}, {0, 128}, {0, 256}};
+      // staged, one thread per cell with 64 / 128 / 256 cells per CTA
+      const std::pair<int, int> cands[] = {{1, 256}, {0, 64}, {0, 128}, {0, 256}};
       for (auto [var, blk] : cands) {
         c.apply_variant_prec[prec] = var;
         c.apply_block[prec] = blk;

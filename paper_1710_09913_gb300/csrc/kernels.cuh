@@ -108,21 +108,6 @@ __device__ __forceinline__ void project(const T (&h)[TB::NB], T (&Y)[TB::V]) {
   });
 }
 
-// Y_l += sum_r B[r][J][l] h_r, accumulating only (Y initialised by the caller).
-template <class TB, int J, typename T>
-__device__ __forceinline__ void project_acc(const T (&h)[TB::NB], T (&Y)[TB::V]) {
-  static_for<TB::NB>([&](auto rc) {
-    constexpr int r = decltype(rc)::value;
-    static_for<TB::V>([&](auto lc) {
-      constexpr int l = decltype(lc)::value;
-      constexpr double b = TB::B[r][J][l];
-      if constexpr (b == 1.0) Y[l] += h[r];
-      else if constexpr (b == -1.0) Y[l] -= h[r];
-      else if constexpr (b != 0.0) Y[l] = fma(T(b), h[r], Y[l]);
-    });
-  });
-}
-
 // h = A_j g with A_j the packed symmetric block (elliptic) or the scalar (projection).
 template <int D, int FORM, typename T>
 __device__ __forceinline__ void block_mul(const T* a, const T* g, T* h) {
@@ -267,7 +252,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 
 constexpr long long kWaitBudget = 4000000000LL;  // ~2 s of SM clock per wait
 
-template <int D, int P, int FORM, typename T, int SPLIT = 1>
+template <int D, int P, int FORM, typename T>
 struct TmaCfg {
   using TB = dogip_tab::Tab<D, P, FORM>;
   static constexpr int V = TB::V, W = TB::W, NS = NSym<D, FORM>::value;
@@ -279,8 +264,7 @@ struct TmaCfg {
   static constexpr int S0 = (int)(kBudget / CHUNK);
   static constexpr int S = S0 > 4 ? 4 : (S0 < 2 ? 2 : S0);  // pipeline stages
   static constexpr uint32_t SMEM = S * CHUNK + S * 8 + 128;
-  static constexpr int THREADS = TPC * 32 * SPLIT;  // SPLIT warps share one tile
-  static constexpr int W0 = SPLIT == 1 ? W : W / 2;  // W nodes of the first warp
+  static constexpr int THREADS = TPC * 32;
   // Instances whose double-buffered 4-warp ring does not fit (3D P3 FP64) use the
   // one-thread-per-cell kernel instead.
   static constexpr bool OK = 2 * CHUNK <= kBudget;
@@ -302,10 +286,10 @@ struct TmaArgs {
   int64_t test_skip_chunk;  // test hook: this chunk's copy is never issued (-1: none)
 };
 
-template <int D, int P, int FORM, typename T, int SPLIT>
-__global__ void __launch_bounds__(TmaCfg<D, P, FORM, T, SPLIT>::THREADS)
+template <int D, int P, int FORM, typename T>
+__global__ void __launch_bounds__(TmaCfg<D, P, FORM, T>::THREADS)
     k_apply_tma(TmaArgs<T> a) {
-  using C = TmaCfg<D, P, FORM, T, SPLIT>;
+  using C = TmaCfg<D, P, FORM, T>;
   static_assert(C::OK, "stage does not fit in shared memory");
   using TB = typename C::TB;
   constexpr int V = C::V, W = C::W, NB = TB::NB, NS = C::NS;
@@ -314,9 +298,7 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T, SPLIT>::THREADS)
       (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
   uint64_t* bars = (uint64_t*)(base + C::S * C::CHUNK);
   if (a.skip != nullptr && *a.skip) return;
-  const int tid = threadIdx.x, lane = tid & 31;
-  const int warp = (tid >> 5) % C::TPC;  // tile slot within the chunk
-  const int half = (tid >> 5) / C::TPC;  // which part of the W nodes (SPLIT = 2)
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t G = gridDim.x;
   if (tid == 0) {
     for (int s = 0; s < C::S; ++s) mbar_init(&bars[s], 1);
@@ -367,7 +349,7 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T, SPLIT>::THREADS)
           ul[l] = (c[l] & kBndBit) ? T(0) : __ldg(a.u + (int64_t)(c[l] & kIdMask) * a.R + r);
           if constexpr (SPLIT > 1 || col_empty<TB>(l)) Y[l] = T(0);
         });
-        auto node = [&](auto jc) {
+        static_for<W>([&](auto jc) {
           constexpr int j = decltype(jc)::value;
           T g[NB], h[NB], aj[NS];
           static_for<NS>([&](auto kc) {
@@ -376,18 +358,8 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T, SPLIT>::THREADS)
           });
           interp<TB, j>(ul, g);
           block_mul<D, FORM>(aj, g, h);
-          if constexpr (SPLIT == 1) project<TB, j>(h, Y);
-          else project_acc<TB, j>(h, Y);
-        };
-        if constexpr (SPLIT == 1) {
-          static_for<W>(node);
-        } else if (half == 0) {  // warp-uniform: each warp takes half of the W nodes
-          static_for<C::W0>(node);
-        } else {
-          static_for<W - C::W0>([&](auto jc) {
-            node(std::integral_constant<int, C::W0 + decltype(jc)::value>{});
-          });
-        }
+          project<TB, j>(h, Y);
+        });
         static_for<V>([&](auto lc) {
           constexpr int l = decltype(lc)::value;
           if (!(c[l] & kBndBit)) atomicAdd(a.y + (int64_t)(c[l] & kIdMask) * a.R + r, Y[l]);
