@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T>::THREADS)
         static_for<V>([&](auto lc) {
           constexpr int l = decltype(lc)::value;
           ul[l] = (c[l] & kBndBit) ? T(0) : __ldg(a.u + (int64_t)(c[l] & kIdMask) * a.R + r);
-          if constexpr (SPLIT > 1 || col_empty<TB>(l)) Y[l] = T(0);
+          if constexpr (col_empty<TB>(l)) Y[l] = T(0);
         });
         static_for<W>([&](auto jc) {
           constexpr int j = decltype(jc)::value;
