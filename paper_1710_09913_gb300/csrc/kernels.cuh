@@ -198,9 +198,10 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> a) {
 // Persistent variant of Algorithm 1 for the whole cell range: the A_T and conn
 // streams are contiguous per 32-cell tile in the AoSoA layout, so chunks of TPC
 // tiles are moved HBM -> shared memory by cp.async.bulk (the TMA engine) into an
-// S-stage ring tracked by mbarriers, while the warps of the CTA compute on the
-// previous stage.  One warp owns one tile (one thread per cell) and loops over the
-// right-hand sides, reusing A_T from shared memory.  The u gathers and the atomic
+// S-stage ring.  A producer warp refills a stage as soon as every consumer warp has
+// released it (per-stage full/empty mbarriers), so the TPC consumer warps run
+// decoupled, one warp per tile (one thread per cell), looping over the right-hand
+// sides and reusing A_T from shared memory.  The u gathers and the atomic
 // scatter go to L2; the Dirichlet rows y_b = u_b are written at the end.  Every wait
 // is bounded by a clock budget; on expiry the kernel raises an error flag, drains its
 // copies in flight (bounded again) and returns.
@@ -238,6 +239,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -263,8 +267,8 @@ struct TmaCfg {
   static constexpr uint32_t CHUNK = TPC * (A_TILE + C_TILE);
   static constexpr int S0 = (int)(kBudget / CHUNK);
   static constexpr int S = S0 > 4 ? 4 : (S0 < 2 ? 2 : S0);  // pipeline stages
-  static constexpr uint32_t SMEM = S * CHUNK + S * 8 + 128;
-  static constexpr int THREADS = TPC * 32;
+  static constexpr uint32_t SMEM = S * CHUNK + 2 * S * 8 + 128;  // ring + full/empty bars
+  static constexpr int THREADS = (TPC + 1) * 32;  // TPC consumer warps + 1 producer warp
   // Instances whose double-buffered 4-warp ring does not fit (3D P3 FP64) use the
   // one-thread-per-cell kernel instead.
   static constexpr bool OK = 2 * CHUNK <= kBudget;
@@ -296,93 +300,107 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T>::THREADS)
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base =
       (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
-  uint64_t* bars = (uint64_t*)(base + C::S * C::CHUNK);
+  uint64_t* full = (uint64_t*)(base + C::S * C::CHUNK);  // chunk landed (tx count)
+  uint64_t* empty = full + C::S;                          // all consumer warps done with it
   if (a.skip != nullptr && *a.skip) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t G = gridDim.x;
   if (tid == 0) {
-    for (int s = 0; s < C::S; ++s) mbar_init(&bars[s], 1);
+    for (int s = 0; s < C::S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], C::TPC);
+    }
     mbar_fence_init();
   }
   __syncthreads();
-  auto issue = [&](int64_t i) {
-    const int64_t k = blockIdx.x + i * G;
-    if (k >= a.nchunks || k == a.test_skip_chunk) return;
-    const int s = (int)(i % C::S);
-    const int64_t t0 = k * C::TPC;
-    const int nt = (int)min((int64_t)C::TPC, a.ntiles - t0);
-    unsigned char* sa = base + (size_t)s * C::CHUNK;
-    unsigned char* sc = sa + C::TPC * C::A_TILE;
-    mbar_expect_tx(&bars[s], (uint32_t)nt * (C::A_TILE + C::C_TILE));
-    bulk_copy_g2s(sa, (const unsigned char*)a.A + t0 * C::A_TILE, (uint32_t)nt * C::A_TILE, &bars[s]);
-    bulk_copy_g2s(sc, (const unsigned char*)a.conn + t0 * C::C_TILE, (uint32_t)nt * C::C_TILE,
-                  &bars[s]);
-  };
-  if (tid == 0)
-    for (int i = 0; i < C::S; ++i) issue(i);
-  int failed = 0;
-  int64_t i = 0;
-  for (;; ++i) {
-    const int64_t k = blockIdx.x + i * G;
-    if (k >= a.nchunks) break;
-    const int s = (int)(i % C::S);
-    const uint32_t parity = (uint32_t)((i / C::S) & 1);
-    failed = __syncthreads_or(mbar_wait_bounded(&bars[s], parity, a.wait_budget) ? 0 : 1);
-    if (failed) break;
-    const int64_t tile = k * C::TPC + warp;
-    const int64_t e = tile * kTile + lane;
-    const bool active = tile < a.ntiles && e < a.E;
-    const T* sA = (const T*)(base + (size_t)s * C::CHUNK + warp * C::A_TILE) + lane;
-    const uint32_t* sC =
-        (const uint32_t*)(base + (size_t)s * C::CHUNK + C::TPC * C::A_TILE + warp * C::C_TILE) +
-        lane;
-    uint32_t c[V];
-    static_for<V>([&](auto lc) {
-      constexpr int l = decltype(lc)::value;
-      c[l] = active ? sC[l * kTile] : kBndBit;
-    });
-    for (int r = 0; r < a.R; ++r) {
-      if (active) {
-        T ul[V], Y[V];
-        static_for<V>([&](auto lc) {
-          constexpr int l = decltype(lc)::value;
-          ul[l] = (c[l] & kBndBit) ? T(0) : __ldg(a.u + (int64_t)(c[l] & kIdMask) * a.R + r);
-          if constexpr (col_empty<TB>(l)) Y[l] = T(0);
-        });
-        static_for<W>([&](auto jc) {
-          constexpr int j = decltype(jc)::value;
-          T g[NB], h[NB], aj[NS];
-          static_for<NS>([&](auto kc) {
-            constexpr int kk = decltype(kc)::value;
-            aj[kk] = sA[(j * NS + kk) * kTile];
+  if (warp == C::TPC) {
+    // ---- producer warp: keep the ring full
+    if (lane == 0) {
+      int failed = 0;
+      int64_t issued = 0;  // chunks whose copies were issued
+      for (int64_t i = 0;; ++i) {
+        const int64_t k = blockIdx.x + i * G;
+        if (k >= a.nchunks) break;
+        const int s = (int)(i % C::S);
+        if (i >= C::S &&
+            !mbar_wait_bounded(&empty[s], (uint32_t)(((i / C::S) - 1) & 1), a.wait_budget)) {
+          failed = 1;
+          break;
+        }
+        fence_proxy_async_smem();
+        issued = i + 1;
+        if (k == a.test_skip_chunk) continue;  // test hook: this chunk never lands
+        const int64_t t0 = k * C::TPC;
+        const int nt = (int)min((int64_t)C::TPC, a.ntiles - t0);
+        unsigned char* sa = base + (size_t)s * C::CHUNK;
+        unsigned char* sc = sa + C::TPC * C::A_TILE;
+        mbar_expect_tx(&full[s], (uint32_t)nt * (C::A_TILE + C::C_TILE));
+        bulk_copy_g2s(sa, (const unsigned char*)a.A + t0 * C::A_TILE, (uint32_t)nt * C::A_TILE,
+                      &full[s]);
+        bulk_copy_g2s(sc, (const unsigned char*)a.conn + t0 * C::C_TILE,
+                      (uint32_t)nt * C::C_TILE, &full[s]);
+      }
+      // drain: wait (bounded) until the last copies issued have landed
+      for (int64_t q = issued - C::S; q < issued; ++q) {
+        if (q < 0) continue;
+        if (blockIdx.x + q * G == a.test_skip_chunk) continue;
+        mbar_wait_bounded(&full[q % C::S], (uint32_t)((q / C::S) & 1), a.wait_budget);
+      }
+      if (failed) atomicOr(a.err, 1);
+    }
+  } else {
+    // ---- consumer warps: warp w computes tile w of every chunk
+    int failed = 0;
+    for (int64_t i = 0;; ++i) {
+      const int64_t k = blockIdx.x + i * G;
+      if (k >= a.nchunks) break;
+      const int s = (int)(i % C::S);
+      const uint32_t parity = (uint32_t)((i / C::S) & 1);
+      failed = __any_sync(0xffffffffu, mbar_wait_bounded(&full[s], parity, a.wait_budget) ? 0 : 1);
+      if (failed) break;
+      const int64_t tile = k * C::TPC + warp;
+      const int64_t e = tile * kTile + lane;
+      const bool active = tile < a.ntiles && e < a.E;
+      const T* sA = (const T*)(base + (size_t)s * C::CHUNK + warp * C::A_TILE) + lane;
+      const uint32_t* sC =
+          (const uint32_t*)(base + (size_t)s * C::CHUNK + C::TPC * C::A_TILE + warp * C::C_TILE) +
+          lane;
+      uint32_t c[V];
+      static_for<V>([&](auto lc) {
+        constexpr int l = decltype(lc)::value;
+        c[l] = active ? sC[l * kTile] : kBndBit;
+      });
+      for (int r = 0; r < a.R; ++r) {
+        if (active) {
+          T ul[V], Y[V];
+          static_for<V>([&](auto lc) {
+            constexpr int l = decltype(lc)::value;
+            ul[l] = (c[l] & kBndBit) ? T(0) : __ldg(a.u + (int64_t)(c[l] & kIdMask) * a.R + r);
+            if constexpr (col_empty<TB>(l)) Y[l] = T(0);
           });
-          interp<TB, j>(ul, g);
-          block_mul<D, FORM>(aj, g, h);
-          project<TB, j>(h, Y);
-        });
-        static_for<V>([&](auto lc) {
-          constexpr int l = decltype(lc)::value;
-          if (!(c[l] & kBndBit)) atomicAdd(a.y + (int64_t)(c[l] & kIdMask) * a.R + r, Y[l]);
-        });
+          static_for<W>([&](auto jc) {
+            constexpr int j = decltype(jc)::value;
+            T g[NB], h[NB], aj[NS];
+            static_for<NS>([&](auto kc) {
+              constexpr int kk = decltype(kc)::value;
+              aj[kk] = sA[(j * NS + kk) * kTile];
+            });
+            interp<TB, j>(ul, g);
+            block_mul<D, FORM>(aj, g, h);
+            project<TB, j>(h, Y);
+          });
+          static_for<V>([&](auto lc) {
+            constexpr int l = decltype(lc)::value;
+            if (!(c[l] & kBndBit)) atomicAdd(a.y + (int64_t)(c[l] & kIdMask) * a.R + r, Y[l]);
+          });
+        }
       }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);  // this warp no longer reads stage s
     }
-    __syncthreads();  // every read of stage s is done
-    if (tid == 0) {
-      fence_proxy_async_smem();
-      issue(i + C::S);
-    }
+    if (failed && lane == 0) atomicOr(a.err, 1);
   }
-  if (failed) {
-    // drain the copies this CTA still has in flight, then report
-    if (tid == 0) {
-      for (int64_t q = i; q < i + C::S; ++q) {
-        if (blockIdx.x + q * G >= a.nchunks) break;
-        mbar_wait_bounded(&bars[q % C::S], (uint32_t)((q / C::S) & 1), a.wait_budget);
-      }
-      atomicOr(a.err, 1);
-    }
-    __syncthreads();
-  }
+  __syncthreads();
   // Dirichlet rows: y_b = u_b (the scatter skipped them)
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + tid; t < a.nbnd * a.R;
        t += (int64_t)gridDim.x * blockDim.x) {
