@@ -585,6 +585,42 @@ def main():
             del c, b3, u3
             torch.cuda.empty_cache()
 
+    # factorised element factors (A_T,j = w_j K_T, K_T per cell): a different memory
+    # trade-off, reported beside the per-node storage of the headline
+    fact = {}
+    for p in P_LIST:
+        cf = B.Context(coords, cells, p, "elliptic", A, factorized=True)
+        out = {"bytes_per_cell_fp32": int(cf.info.bytes_ahat_fp32 // cf.E + cf.info.v_loc * 4)}
+        for prec, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
+            u = torch.randn(cf.n, dtype=dt, device="cuda")
+            y = torch.empty_like(u)
+            for _ in range(3):
+                cf.apply(u, y, prec=prec)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(20):
+                cf.apply(u, y, prec=prec)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1) / 20
+            out[f"apply_{prec}_ms"] = round(ms, 4)
+            out[f"apply_{prec}_gdofs"] = round(cf.n / ms / 1e6, 3)
+        b = cf.load()
+        ux = torch.zeros_like(b)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        _, info = cf.solve(b, ux, mode="mixed", tol=TOL, check_every=args.check_every)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        out["mixed_ms"] = round(ev0.elapsed_time(ev1), 2)
+        out["mixed_iters"] = info["iterations"]
+        fact[f"P{p}"] = out
+        del cf
+
     dom = applies["P4_fp32"]
     roofline = {"bound": "hbm", "achieved": dom["GBps"], "peak": hbm, "unit": "GB/s",
                 "frac": round(dom["GBps"] / hbm, 4), "traffic": None,
@@ -638,7 +674,7 @@ def main():
                 "value_definition": "sum_p n_p x operator applies / step time (applies inside the "
                                     "mixed solves, FP32 inner and FP64 residual)",
                 "time_to_tol": t2t, "apply": applies, "csr_baseline": csr, "batch_uneven": batch,
-                "cube_p2_16rhs": multi,
+                "cube_p2_16rhs": multi, "factorized": fact,
                 "roofline": roofline,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks}
         print(json.dumps(line), flush=True)

@@ -99,6 +99,13 @@ typedef struct {
                       cells by colour) and the default scatter of solves      */
   int keep_fp32;   /* 1 (default): also keep an FP32 copy of A_T              */
   int device;      /* CUDA device ordinal, -1 = current device                */
+  int factorized;  /* 0 (default): store A_T per W node (eqs. wp_dogip_mul,
+                      ep_dogip_mul).  1: the coefficients are constant per cell
+                      (they are, for every coefficient kind of this ABI), so
+                      A_T,j = w_j K_T with K_T = |det R_T| R_T^-1 M_T R_T^-T (or
+                      m_T |det R_T|): only K_T is stored (d(d+1)/2 or 1 values
+                      per cell) and w_j is applied inside the kernel.  Needs
+                      scatter = ATOMIC.                                         */
 } dogip_opts;
 
 /* Fill *o with the defaults above.  Never fails for o != NULL. */

@@ -52,7 +52,7 @@ class Mesh(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("dirichlet", C.c_int), ("scatter", C.c_int), ("keep_fp32", C.c_int),
-                ("device", C.c_int)]
+                ("device", C.c_int), ("factorized", C.c_int)]
 
 
 class Info(C.Structure):
@@ -193,7 +193,7 @@ class Context:
     """A DoGIP operator on one mesh (wraps ``dogip_ctx``)."""
 
     def __init__(self, coords, cells, p, form, coef, *, dirichlet=None, scatter="atomic",
-                 keep_fp32=True, device=None):
+                 keep_fp32=True, device=None, factorized=False):
         coords = np.ascontiguousarray(coords, dtype=np.float64)
         cells = np.ascontiguousarray(cells, dtype=np.int32)
         coef = np.ascontiguousarray(coef, dtype=np.float64)
@@ -209,6 +209,7 @@ class Context:
         o.keep_fp32 = int(keep_fp32)
         if device is not None:
             o.device = int(device)
+        o.factorized = int(bool(factorized))
         kind = COEF_ELEM_TENSOR if coef.ndim == 3 else COEF_ELEM_SCALAR
         h = C.c_void_p()
         _check(lib.dogip_setup(C.byref(mesh), int(p), FORMS.get(form, form), kind,

@@ -30,11 +30,11 @@ struct TmaLaunch {
 
 // Kernel attributes and residency of one instance, set once (thread-safe static);
 // first called from context set-up, outside any stream capture.
-template <int D, int P, int FORM, typename T>
+template <int D, int P, int FORM, typename T, bool FACT>
 const TmaLaunch& tma_launch() {
   static const TmaLaunch info = [] {
-    using Cfg = TmaCfg<D, P, FORM, T>;
-    auto kern = k_apply_tma<D, P, FORM, T>;
+    using Cfg = TmaCfg<D, P, FORM, T, FACT>;
+    auto kern = k_apply_tma<D, P, FORM, T, FACT>;
     TmaLaunch t;
     cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM),
                "apply smem attribute");
@@ -49,11 +49,11 @@ const TmaLaunch& tma_launch() {
   return info;
 }
 
-template <int D, int P, int FORM, typename T>
+template <int D, int P, int FORM, typename T, bool FACT>
 void run_apply_tma(const T* A, const Ctx& c, const void* u, void* y, int R, cudaStream_t s,
                    const int* skip) {
-  using Cfg = TmaCfg<D, P, FORM, T>;
-  const TmaLaunch& L = tma_launch<D, P, FORM, T>();
+  using Cfg = TmaCfg<D, P, FORM, T, FACT>;
+  const TmaLaunch& L = tma_launch<D, P, FORM, T, FACT>();
   const int blocks_per_sm = L.blocks_per_sm, num_sms = L.num_sms;
   const int64_t ntiles = (c.E + kTile - 1) / kTile;
   const int64_t nchunks = (ntiles + Cfg::TPC - 1) / Cfg::TPC;
@@ -61,7 +61,7 @@ void run_apply_tma(const T* A, const Ctx& c, const void* u, void* y, int R, cuda
   const int64_t grid = std::min<int64_t>(nchunks, (int64_t)num_sms * blocks_per_sm);
   TmaArgs<T> a{A, c.d_conn, (const T*)u, (T*)y, c.E, ntiles, nchunks, R, skip, c.d_kerr,
                 c.d_bnd, c.dirichlet ? c.nbnd : 0, c.wait_budget, c.test_skip_chunk};
-  k_apply_tma<D, P, FORM, T><<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
+  k_apply_tma<D, P, FORM, T, FACT><<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
 }
 
 // Returns 2 when the staged kernel ran (it also wrote the Dirichlet rows), 1 for the
@@ -71,9 +71,19 @@ int run_apply(const Ctx& c, const void* u, void* y, int R, int prec, bool atomic
               int64_t e1, cudaStream_t s, const int* skip) {
   constexpr bool ok64 = TmaCfg<D, P, FORM, double>::OK, ok32 = TmaCfg<D, P, FORM, float>::OK;
   if (u == nullptr) {  // preparation call from context set-up
-    if constexpr (ok64) tma_launch<D, P, FORM, double>();
-    if constexpr (ok32) tma_launch<D, P, FORM, float>();
+    if (c.factorized) {
+      tma_launch<D, P, FORM, double, true>();
+      tma_launch<D, P, FORM, float, true>();
+    } else {
+      if constexpr (ok64) tma_launch<D, P, FORM, double, false>();
+      if constexpr (ok32) tma_launch<D, P, FORM, float, false>();
+    }
     return 1;
+  }
+  if (c.factorized) {  // staged kernel over the whole range, atomic scatter only
+    if (prec == DOGIP_FP64) run_apply_tma<D, P, FORM, double, true>(c.d_A64, c, u, y, R, s, skip);
+    else run_apply_tma<D, P, FORM, float, true>(c.d_A32, c, u, y, R, s, skip);
+    return 2;
   }
   // variant: 1 staged, 0 one thread per cell
   const int var = c.apply_variant_prec[prec] >= 0 ? c.apply_variant_prec[prec] : c.apply_variant;
@@ -81,7 +91,7 @@ int run_apply(const Ctx& c, const void* u, void* y, int R, int prec, bool atomic
   if (prec == DOGIP_FP64) {
     if constexpr (ok64) {
       if (whole) {
-        run_apply_tma<D, P, FORM, double>(c.d_A64, c, u, y, R, s, skip);
+        run_apply_tma<D, P, FORM, double, false>(c.d_A64, c, u, y, R, s, skip);
         return 2;
       }
     }
@@ -89,7 +99,7 @@ int run_apply(const Ctx& c, const void* u, void* y, int R, int prec, bool atomic
   } else {
     if constexpr (ok32) {
       if (whole) {
-        run_apply_tma<D, P, FORM, float>(c.d_A32, c, u, y, R, s, skip);
+        run_apply_tma<D, P, FORM, float, false>(c.d_A32, c, u, y, R, s, skip);
         return 2;
       }
     }

@@ -334,6 +334,9 @@ Ctx* setup(const dogip_mesh* m, int p, int form, int coef_kind, const double* co
     c->dirichlet = o.dirichlet < 0 ? form == DOGIP_ELLIPTIC : o.dirichlet != 0;
     c->scatter = o.scatter == DOGIP_SCATTER_COLOUR ? DOGIP_SCATTER_COLOUR : DOGIP_SCATTER_ATOMIC;
     c->keep32 = o.keep_fp32 != 0;
+    c->factorized = o.factorized != 0;
+    if (c->factorized && c->scatter == DOGIP_SCATTER_COLOUR)
+      fail(DOGIP_EINVAL, "factorized storage needs atomic scatter");
     c->E = m->n_cells;
     c->Epad = (c->E + kTile - 1) / kTile * kTile;
     c->nv = m->n_vertices;
@@ -380,8 +383,9 @@ Ctx* setup(const dogip_mesh* m, int p, int form, int coef_kind, const double* co
     c->d_cells = dev_alloc<int32_t>(pcells.size());
     c->d_perm = dev_alloc<int64_t>(c->E);
     c->d_conn = dev_alloc<uint32_t>(conn.size());
-    c->d_A64 = dev_alloc<double>((size_t)c->Epad * W * c->NS);
-    if (c->keep32) c->d_A32 = dev_alloc<float>((size_t)c->Epad * W * c->NS);
+    const size_t nA = (size_t)c->Epad * (c->factorized ? 1 : W) * c->NS;
+    c->d_A64 = dev_alloc<double>(nA);
+    if (c->keep32) c->d_A32 = dev_alloc<float>(nA);
     c->d_geo = dev_alloc<double>((size_t)c->E * (d * d + 1));
     c->d_diag = dev_alloc<double>(c->n);
     c->d_dinv64 = dev_alloc<double>(c->n);
@@ -411,9 +415,8 @@ Ctx* setup(const dogip_mesh* m, int p, int form, int coef_kind, const double* co
     cuda_check(cudaMemcpyAsync(c->d_coef, coef, sizeof(double) * ncoef, cudaMemcpyHostToDevice, s),
                "upload coefficients");
     // padding of A_T stays zero
-    cuda_check(cudaMemsetAsync(c->d_A64, 0, sizeof(double) * c->Epad * W * c->NS, s), "memset A");
-    if (c->keep32)
-      cuda_check(cudaMemsetAsync(c->d_A32, 0, sizeof(float) * c->Epad * W * c->NS, s), "memset A32");
+    cuda_check(cudaMemsetAsync(c->d_A64, 0, sizeof(double) * nA, s), "memset A");
+    if (c->keep32) cuda_check(cudaMemsetAsync(c->d_A32, 0, sizeof(float) * nA, s), "memset A32");
     cuda_check(cudaMemsetAsync(c->d_err, 0, sizeof(int), s), "memset err");
     cuda_check(cudaMemsetAsync(c->d_kerr, 0, sizeof(int), s), "memset kernel err");
     launch_ahat(*c, c->d_coef, coef_kind, s);
@@ -949,6 +952,7 @@ void tune_store_locked(const TuneKey& k, const TuneChoice& ch) {
 
 int autotune(Ctx& c, int force, cudaStream_t s) {
   DeviceGuard guard(c.device);
+  if (c.factorized) return 0;  // one kernel only
   int logE = 0;
   while ((int64_t(1) << logE) < c.E) ++logE;
   int tuned = 0;
@@ -1056,6 +1060,7 @@ int dogip_opts_default(dogip_opts* o) {
   o->scatter = DOGIP_SCATTER_ATOMIC;
   o->keep_fp32 = 1;
   o->device = -1;
+  o->factorized = 0;
   return DOGIP_OK;
 }
 
@@ -1113,8 +1118,9 @@ int dogip_get_info(const dogip_ctx* c, dogip_info* i) {
     i->n_colours = c->ncolours;
     i->nnz_b = c->nnzb;
     i->nnz_pm1_b = c->nnzb1;
-    i->bytes_ahat_fp64 = (int64_t)c->E * c->WT * c->NS * 8;
-    i->bytes_ahat_fp32 = (int64_t)c->E * c->WT * c->NS * 4;
+    const int64_t per = (int64_t)(c->factorized ? 1 : c->WT) * c->NS;
+    i->bytes_ahat_fp64 = (int64_t)c->E * per * 8;
+    i->bytes_ahat_fp32 = (int64_t)c->E * per * 4;
     i->bytes_conn = (int64_t)c->E * c->VT * 4;
     i->kernel_launches = c->launches;
     return DOGIP_OK;

@@ -256,11 +256,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 
 constexpr long long kWaitBudget = 4000000000LL;  // ~2 s of SM clock per wait
 
-template <int D, int P, int FORM, typename T>
+// FACT: factorised element factors (element-wise constant coefficients): the
+// stream holds K_T (n_sym values per cell) and A_T,j = w_j K_T is formed in
+// registers, w_j a compile-time constant.
+template <int D, int P, int FORM, typename T, bool FACT = false>
 struct TmaCfg {
   using TB = dogip_tab::Tab<D, P, FORM>;
   static constexpr int V = TB::V, W = TB::W, NS = NSym<D, FORM>::value;
-  static constexpr uint32_t A_TILE = W * NS * kTile * sizeof(T);
+  static constexpr uint32_t A_TILE = (FACT ? 1 : W) * NS * kTile * sizeof(T);
   static constexpr uint32_t C_TILE = V * kTile * 4;
   static constexpr uint32_t kBudget = 200 * 1024;  // shared memory for the ring
   static constexpr int TPC = (2 * 8 * (A_TILE + C_TILE) <= kBudget) ? 8 : 4;  // warps per CTA
@@ -290,10 +293,10 @@ struct TmaArgs {
   int64_t test_skip_chunk;  // test hook: this chunk's copy is never issued (-1: none)
 };
 
-template <int D, int P, int FORM, typename T>
-__global__ void __launch_bounds__(TmaCfg<D, P, FORM, T>::THREADS)
+template <int D, int P, int FORM, typename T, bool FACT>
+__global__ void __launch_bounds__(TmaCfg<D, P, FORM, T, FACT>::THREADS)
     k_apply_tma(TmaArgs<T> a) {
-  using C = TmaCfg<D, P, FORM, T>;
+  using C = TmaCfg<D, P, FORM, T, FACT>;
   static_assert(C::OK, "stage does not fit in shared memory");
   using TB = typename C::TB;
   constexpr int V = C::V, W = C::W, NB = TB::NB, NS = C::NS;
@@ -370,6 +373,13 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T>::THREADS)
         constexpr int l = decltype(lc)::value;
         c[l] = active ? sC[l * kTile] : kBndBit;
       });
+      T kf[NS];  // factorised K_T (FACT only)
+      if constexpr (FACT) {
+        static_for<NS>([&](auto kc) {
+          constexpr int kk = decltype(kc)::value;
+          kf[kk] = active ? sA[kk * kTile] : T(0);
+        });
+      }
       for (int r = 0; r < a.R; ++r) {
         if (active) {
           T ul[V], Y[V];
@@ -383,7 +393,12 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T>::THREADS)
             T g[NB], h[NB], aj[NS];
             static_for<NS>([&](auto kc) {
               constexpr int kk = decltype(kc)::value;
-              aj[kk] = sA[(j * NS + kk) * kTile];
+              if constexpr (FACT) {
+                constexpr double wj = TB::w[j];
+                aj[kk] = T(wj) * kf[kk];
+              } else {
+                aj[kk] = sA[(j * NS + kk) * kTile];
+              }
             });
             interp<TB, j>(ul, g);
             block_mul<D, FORM>(aj, g, h);
@@ -413,6 +428,7 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T>::THREADS)
 
 struct AhatArgs {
   const double* coords;   // [nv x D]
+  int fact;               // 1: write K_T (n_sym per cell) instead of A_T per W node
   const int32_t* cells;   // [E x (D+1)] processing order
   const int64_t* perm;    // processing position -> caller cell
   const double* coef;     // caller order
@@ -557,18 +573,28 @@ __global__ void __launch_bounds__(128) k_ahat(AhatArgs a) {
   if (err) atomicOr(a.err, err);
   const int64_t tile = pos >> 5;
   const int lane = (int)(pos & 31);
-  double* At = a.A64 + tile * ((int64_t)W * NS * kTile) + lane;
-  float* At32 = a.A32 ? a.A32 + tile * ((int64_t)W * NS * kTile) + lane : nullptr;
-  static_for<W>([&](auto jc) {
-    constexpr int j = decltype(jc)::value;
+  if (a.fact) {
+    double* Kt = a.A64 + tile * ((int64_t)NS * kTile) + lane;
+    float* Kt32 = a.A32 ? a.A32 + tile * ((int64_t)NS * kTile) + lane : nullptr;
     static_for<NS>([&](auto kc) {
       constexpr int k = decltype(kc)::value;
-      constexpr double wj = TB::w[j];
-      const double v = wj * K[k];
-      At[(j * NS + k) * kTile] = v;
-      if (At32) At32[(j * NS + k) * kTile] = (float)v;
+      Kt[k * kTile] = K[k];
+      if (Kt32) Kt32[k * kTile] = (float)K[k];
     });
-  });
+  } else {
+    double* At = a.A64 + tile * ((int64_t)W * NS * kTile) + lane;
+    float* At32 = a.A32 ? a.A32 + tile * ((int64_t)W * NS * kTile) + lane : nullptr;
+    static_for<W>([&](auto jc) {
+      constexpr int j = decltype(jc)::value;
+      static_for<NS>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        constexpr double wj = TB::w[j];
+        const double v = wj * K[k];
+        At[(j * NS + k) * kTile] = v;
+        if (At32) At32[(j * NS + k) * kTile] = (float)v;
+      });
+    });
+  }
   double* g = a.geo + pos * (D * D + 1);
   static_for<D>([&](auto ic) {
     constexpr int i = decltype(ic)::value;
@@ -713,6 +739,25 @@ __global__ void __launch_bounds__(128) k_grad(GradArgs a) {
     static_for<NB>([&](auto pc) { tr += G[decltype(pc)::value][decltype(pc)::value]; });
     a.dA[user] = -tr;
   }
+}
+
+// Factorised K_T (AoSoA [Epad/32][NS][32]) -> A_T,j = w_j K_T as [E][W][NS], caller order.
+template <int D, int P, int FORM>
+__global__ void k_export_fact(const double* K, const int64_t* perm, double* out, int64_t E) {
+  using TB = dogip_tab::Tab<D, P, FORM>;
+  constexpr int W = TB::W, NS = NSym<D, FORM>::value;
+  const int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (pos >= E) return;
+  const double* Kt = K + (pos >> 5) * ((int64_t)NS * kTile) + (pos & 31);
+  double* o = out + perm[pos] * (int64_t)W * NS;
+  static_for<W>([&](auto jc) {
+    constexpr int j = decltype(jc)::value;
+    constexpr double wj = TB::w[j];
+    static_for<NS>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      o[j * NS + k] = wj * Kt[k * kTile];
+    });
+  });
 }
 
 // A_T (AoSoA, processing order) -> [E][W][NS] caller order; nsw = W * NS.

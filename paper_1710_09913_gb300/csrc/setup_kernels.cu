@@ -62,7 +62,7 @@ namespace {
 
 template <int D, int P, int FORM>
 void ahat_one(Ctx& c, const double* coef, int coef_kind, cudaStream_t s) {
-  AhatArgs a{c.d_coords, c.d_cells, c.d_perm, coef, coef_kind, c.d_conn, c.d_A64,
+  AhatArgs a{c.d_coords, c.factorized ? 1 : 0, c.d_cells, c.d_perm, coef, coef_kind, c.d_conn, c.d_A64,
              c.keep32 ? c.d_A32 : nullptr, c.d_geo, c.d_diag, c.d_err, c.E};
   const unsigned nb = (unsigned)((c.E + 127) / 128);
   k_ahat<D, P, FORM><<<nb, 128, 0, s>>>(a);
@@ -167,6 +167,16 @@ void launch_grad(Ctx& c, const double* u, const double* lam, double* dA, cudaStr
 }
 
 void launch_export_ahat(const Ctx& c, double* out, cudaStream_t s) {
+  if (c.factorized) {
+    bool ok_ = true;
+    const unsigned nb = (unsigned)((c.E + 127) / 128);
+#define CALL(D, P, F) k_export_fact<D, P, F><<<nb, 128, 0, s>>>(c.d_A64, c.d_perm, out, c.E)
+    DOGIP_DISPATCH(c.d, c.p, c.form, CALL);
+#undef CALL
+    if (!ok_) fail(DOGIP_EUNSUPPORTED, "no compiled instance for this (dim, p, form)");
+    cuda_check(cudaGetLastError(), "export kernel launch");
+    return;
+  }
   const int nsw = c.WT * c.NS;
   const int64_t tot = c.E * nsw;
   if (tot == 0) return;

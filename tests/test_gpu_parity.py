@@ -363,3 +363,43 @@ def test_autotune_keeps_parity(B):
     assert np.all(np.abs(y32 - P.apply(u32.astype(np.float64))) <= TOL32 * P.apply_abs(u32.astype(np.float64)))
     ctx2, _ = make(B, 2, 3, "elliptic", 40, seed=2)
     assert ctx2.autotune() == choice
+
+
+@pytest.mark.parametrize("R", [1, 4])
+@pytest.mark.parametrize("d,p,form", SMALL, ids=IDS)
+def test_factorized_storage(B, d, p, form, R):
+    """Factorised element factors (A_T,j = w_j K_T, only K_T stored): the exported
+    A_T and the FP64 / FP32 applies match the oracle like the per-node storage."""
+    jitter = 0.2 if d == 2 else 0.1
+    coords, cells = inputs.lattice_mesh(d, NSMALL[d], jitter, 1)
+    E = len(cells)
+    coef = inputs.coef_tensor_lognormal(E, d, 1.0, 1) if form == "elliptic" else \
+        inputs.coef_uniform(E, 1.0, 10.0, 1)
+    ctx = B.Context(coords, cells, p, form, coef, factorized=True)
+    P = odogip.Problem(form, p, coords, cells, coef)
+    assert ctx.info.bytes_ahat_fp64 == E * ctx.info.n_sym * 8
+    A = ctx.ahat().cpu().numpy()
+    ref = pack(P)
+    assert np.all(np.abs(A - ref) <= 1e-14 * np.abs(ref).max(axis=(1, 2), keepdims=True))
+    u = inputs.rhs_normal(P.n, R, seed=5)
+    ug = torch.tensor(u if R > 1 else u[:, 0], device="cuda")
+    y = ctx.apply(ug).cpu().numpy().reshape(P.n, R)
+    assert np.all(np.abs(y - P.apply(u)) <= TOL64 * P.apply_abs(u))
+    u32 = u.astype(np.float32)
+    y32 = ctx.apply(torch.tensor(u32 if R > 1 else u32[:, 0], device="cuda"), prec="fp32")
+    y32 = y32.cpu().numpy().astype(np.float64).reshape(P.n, R)
+    u64 = u32.astype(np.float64)
+    assert np.all(np.abs(y32 - P.apply(u64)) <= TOL32 * P.apply_abs(u64))
+    if R == 1 and d == 2 and p == 2:
+        b = ctx.load()
+        x, info = ctx.solve(b, mode="mixed", tol=1e-10)
+        r = b.cpu().numpy() - P.apply(x.cpu().numpy())
+        assert np.linalg.norm(r) <= 1.01e-10 * np.linalg.norm(b.cpu().numpy())
+
+
+def test_factorized_rejects_colour(B):
+    coords, cells = inputs.lattice_mesh(2, 4)
+    with pytest.raises(B.DogipError) as e:
+        B.Context(coords, cells, 2, "elliptic", np.ones(len(cells)), factorized=True,
+                  scatter="colour")
+    assert e.value.code == B.EINVAL
