@@ -67,6 +67,8 @@ extern "C" {
 
 #define DOGIP_COEF_ELEM_SCALAR 0 /* one scalar per cell: m_T, or M_T = m_T I   */
 #define DOGIP_COEF_ELEM_TENSOR 1 /* one symmetric d x d tensor M_T per cell    */
+#define DOGIP_COEF_INCLUSIONS 2  /* isotropic field with spherical inclusions,
+                                    integrated per W node (dogip_set_coef_inclusions) */
 
 #define DOGIP_FP64 0        /* FP64 storage and arithmetic                     */
 #define DOGIP_FP32 1        /* FP32 A_T, vectors and arithmetic                */
@@ -142,6 +144,21 @@ DOGIP_API void dogip_destroy(dogip_ctx* ctx);
  */
 DOGIP_API int dogip_set_coef(dogip_ctx* ctx, int coef_kind, const double* coef,
                    void* cuda_stream);
+
+/*
+ * Element factors of a discontinuous isotropic coefficient m(x) -- `inside` in the
+ * union of n_incl balls (host centres [n_incl x dim], radii [n_incl]), `outside`
+ * elsewhere -- integrated per W node with a sub-element rule (Section 3.3: DoGIP
+ * takes the quadrature of rough coefficients out of the operator apply):
+ *   A_T,j = sigma_j |det R_T| R_T^-1 R_T^-T (elliptic, M = m I) or sigma_j |det R_T|
+ *   (projection), sigma_j = sum_q w_q m(F_T(x_q)) phi^W_j(x_q),
+ * with the collapsed Gauss rule of nq points per direction on the reference simplex
+ * (exact to degree 2 nq - 1; nq in 1..16).  Recomputes A_T and the Jacobi diagonal;
+ * the apply is unchanged.  Needs factorized = 0.  Synchronises cuda_stream.
+ */
+DOGIP_API int dogip_set_coef_inclusions(dogip_ctx* ctx, int n_incl, const double* centres,
+                                        const double* radii, double inside, double outside,
+                                        int nq, void* cuda_stream);
 
 /* ----------------------------------------------------------------- queries */
 typedef struct {

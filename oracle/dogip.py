@@ -18,7 +18,9 @@ with P the projector that zeroes boundary dofs, the operator is
 K~ = P K P + (I - P): boundary rows and columns replaced by the identity.
 
 Parity: pinned in the tests by the identity with the independently assembled
-matrix (1e-12), textbook P1 mass/stiffness, K 1 = 0, 1^T M 1 = |Omega|.
+matrix (1e-12), textbook P1 mass/stiffness, K 1 = 0, 1^T M 1 = |Omega|; the
+sub-element quadrature (``ahat_quadrature``) by the exact A_T for constant m and
+by the measure of a ball.
 """
 
 from __future__ import annotations
@@ -51,6 +53,30 @@ def ahat(form: str, p: int, coords: np.ndarray, cells: np.ndarray, coef: np.ndar
     M = coef[:, None, None] * np.eye(d)[None] if coef.ndim == 1 else coef
     K = np.einsum("erp,epq,esq->ers", Rinv, M, Rinv)  # R^-1 M R^-T
     return vol[:, None, None, None] * w[None, :, None, None] * K[:, None, :, :]
+
+
+def ahat_quadrature(form: str, p: int, coords: np.ndarray, cells: np.ndarray, m_func, nq: int):
+    """A_T^DoGIP of an isotropic coefficient m(x) that varies inside the cells
+    (Theorems 4 and 8 with the integral int_T m phi^W_j left to quadrature):
+      sigma_T,j = int_That m(F_T(x)) phi^W_j(x) dx ~ sum_q w_q m(F_T(x_q)) phi^W_j(x_q)
+    with the collapsed Gauss rule of ``nq`` points per direction, and
+      A_T,j = sigma_T,j |det R_T| R_T^-1 R_T^-T (elliptic, M = m I), sigma_T,j |det R_T|
+    (projection).  Returns the layout of ``ahat``.
+    """
+    from . import quadrature
+    d = cells.shape[1] - 1
+    q = refelem.w_degree(form, p)
+    pts, wq = quadrature.simplex_rule(d, nq)
+    phi, _ = refelem.vandermonde_eval_float(d, q, pts) if q > 0 else (np.ones((len(pts), 1)), None)
+    R, det, Rinv = geometry(coords, cells)
+    X = coords[cells][:, 0, :][:, None, :] + np.einsum("eij,qj->eqi", R, pts)
+    mq = m_func(X)                                   # [E, nq]
+    sig = np.einsum("q,eq,qj->ej", wq, mq, phi)      # [E, W]
+    vol = np.abs(det)
+    if form == "projection":
+        return vol[:, None] * sig
+    K = np.einsum("erp,esp->ers", Rinv, Rinv)        # R^-1 R^-T
+    return (vol[:, None] * sig)[:, :, None, None] * K[:, None, :, :]
 
 
 def apply(form: str, Bh: np.ndarray, Ah: np.ndarray, conn: np.ndarray, u: np.ndarray,

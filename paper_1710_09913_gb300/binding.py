@@ -105,6 +105,8 @@ _SIGS = {
                                    C.POINTER(SolveInfo), _vp, _vp]),
     "dogip_grad_coef": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "dogip_check": (C.c_int, [_vp, _vp]),
+    "dogip_set_coef_inclusions": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_double, C.c_double,
+                                            C.c_int, _vp]),
     "dogip_autotune": (C.c_int, [_vp, C.c_int, C.POINTER(TuneInfo), _vp]),
     "dogip_batch_solve": (C.c_int, [C.POINTER(_vp), C.c_int, C.POINTER(_vp), C.POINTER(_vp),
                                     C.POINTER(SolveOpts), C.POINTER(SolveInfo), _vp]),
@@ -270,6 +272,15 @@ class Context:
         import torch
         kind = COEF_ELEM_TENSOR if coef.dim() == 3 else COEF_ELEM_SCALAR
         _check(lib.dogip_set_coef(self._h, kind, _dptr(coef, torch.float64), _stream(stream)))
+        _check(lib.dogip_get_info(self._h, C.byref(self.info)))
+
+    def set_coef_inclusions(self, centres, radii, inside, outside, nq, stream=None):
+        """Element factors of an inclusion field by sub-element quadrature."""
+        centres = np.ascontiguousarray(centres, dtype=np.float64)
+        radii = np.ascontiguousarray(radii, dtype=np.float64)
+        _check(lib.dogip_set_coef_inclusions(self._h, len(radii), centres.ctypes.data_as(_vp),
+                                             radii.ctypes.data_as(_vp), float(inside),
+                                             float(outside), int(nq), _stream(stream)))
         _check(lib.dogip_get_info(self._h, C.byref(self.info)))
 
     def apply(self, u, y=None, prec="fp64", scatter=None, stream=None):

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "quad.h"
 
 namespace dogip {
 
@@ -440,6 +441,87 @@ void set_coef(Ctx& c, int coef_kind, const double* coef, cudaStream_t s) {
   cuda_check(cudaMemsetAsync(c.d_err, 0, sizeof(int), s), "memset err");
   launch_ahat(c, coef, coef_kind, s);
   check_coef_status(c, s);
+}
+
+
+// Equispaced Lagrange basis of degree q (Silvester's product form) at a reference
+// point, in double precision: phi_beta = prod_i prod_{m < beta_i} (q lambda_i - m)/(m+1).
+void w_basis_at(int d, int q, const double* x, std::vector<double>& out) {
+  out.clear();
+  if (q == 0) {
+    out.push_back(1.0);
+    return;
+  }
+  double lam[4];
+  lam[0] = 1.0;
+  for (int i = 0; i < d; ++i) {
+    lam[i + 1] = x[i];
+    lam[0] -= x[i];
+  }
+  for (auto& beta : local_betas(d, q)) {
+    double v = 1.0;
+    for (int i = 0; i <= d; ++i)
+      for (int m = 0; m < beta[i]; ++m) v *= (q * lam[i] - m) / (m + 1);
+    out.push_back(v);
+  }
+}
+
+void set_coef_inclusions(Ctx& c, int nb, const double* centres, const double* radii, double inside,
+                         double outside, int nq, cudaStream_t s) {
+  if (c.factorized) fail(DOGIP_EINVAL, "sub-element integration needs per-node storage (factorized = 0)");
+  if (nb < 0 || (nb > 0 && (!centres || !radii))) fail(DOGIP_EINVAL, "inclusion arrays required");
+  if (nq < 1 || nq > 16) fail(DOGIP_EINVAL, "points per direction must be in 1..16");
+  if (!(inside > 0.0) || !(outside > 0.0) || !std::isfinite(inside) || !std::isfinite(outside))
+    fail(DOGIP_EINVAL, "coefficient values must be positive and finite");
+  for (int b = 0; b < nb; ++b) {
+    if (!(radii[b] > 0.0) || !std::isfinite(radii[b])) fail(DOGIP_EINVAL, "radii must be positive");
+    for (int k = 0; k < c.d; ++k)
+      if (!std::isfinite(centres[b * c.d + k])) fail(DOGIP_EINVAL, "non-finite inclusion centre");
+  }
+  DeviceGuard guard(c.device);
+  std::vector<double> pts, wts;
+  simplex_rule(c.d, nq, pts, wts);
+  const int q = c.form == DOGIP_PROJECTION ? 2 * c.p : 2 * c.p - 2;
+  const int NQ = (int)wts.size();
+  std::vector<double> phi((size_t)NQ * c.WT), row;
+  for (int i = 0; i < NQ; ++i) {
+    w_basis_at(c.d, q, &pts[(size_t)i * c.d], row);
+    for (int j = 0; j < c.WT; ++j) phi[(size_t)i * c.WT + j] = row[j];
+  }
+  // one staging buffer (stream-ordered) for points, weights, table, balls
+  const size_t n_total = pts.size() + wts.size() + phi.size() + (size_t)nb * c.d + nb;
+  double* buf = nullptr;
+  cuda_check(cudaMallocAsync((void**)&buf, sizeof(double) * std::max<size_t>(n_total, 1), s),
+             "quadrature staging");
+  std::vector<double> host;
+  host.reserve(n_total);
+  host.insert(host.end(), pts.begin(), pts.end());
+  host.insert(host.end(), wts.begin(), wts.end());
+  host.insert(host.end(), phi.begin(), phi.end());
+  host.insert(host.end(), centres, centres + (size_t)nb * c.d);
+  host.insert(host.end(), radii, radii + nb);
+  QuadCoef qc;
+  qc.pts = buf;
+  qc.wts = buf + pts.size();
+  qc.phi = qc.wts + wts.size();
+  qc.nq = NQ;
+  qc.centres = qc.phi + phi.size();
+  qc.radii = qc.centres + (size_t)nb * c.d;
+  qc.nb = nb;
+  qc.inside = inside;
+  qc.outside = outside;
+  try {
+    cuda_check(cudaMemcpyAsync(buf, host.data(), sizeof(double) * n_total, cudaMemcpyHostToDevice, s),
+               "quadrature upload");
+    cuda_check(cudaMemsetAsync(c.d_err, 0, sizeof(int), s), "memset err");
+    launch_ahat_quad(c, qc, s);
+    cuda_check(cudaFreeAsync(buf, s), "quadrature staging free");
+  } catch (...) {
+    cudaFreeAsync(buf, s);
+    throw;
+  }
+  check_coef_status(c, s);
+  c.coef_kind = DOGIP_COEF_INCLUSIONS;
 }
 
 // ------------------------------------------------------------------- solve
@@ -1298,9 +1380,22 @@ int dogip_batch_solve(dogip_ctx* const* ctxs, int nprob, const double* const* b,
   });
 }
 
+int dogip_set_coef_inclusions(dogip_ctx* c, int n_incl, const double* centres,
+                              const double* radii, double inside, double outside, int nq,
+                              void* stream) {
+  return guarded([&] {
+    if (!c) fail(DOGIP_EINVAL, "ctx is required");
+    dogip::set_coef_inclusions(*c, n_incl, centres, radii, inside, outside, nq,
+                               (cudaStream_t)stream);
+    return DOGIP_OK;
+  });
+}
+
 int dogip_grad_coef(dogip_ctx* c, const double* u, const double* lam, double* dA, void* stream) {
   return guarded([&] {
     if (!c || !u || !lam || !dA) fail(DOGIP_EINVAL, "ctx, u, lam and dA are required");
+    if (c->coef_kind == DOGIP_COEF_INCLUSIONS)
+      fail(DOGIP_EINVAL, "the coefficient gradient needs element-wise coefficients");
     dogip::DeviceGuard g(c->device);
     dogip::launch_grad(*c, u, lam, dA, (cudaStream_t)stream);
     return DOGIP_OK;

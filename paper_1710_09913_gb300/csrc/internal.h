@@ -116,9 +116,22 @@ struct Failure {
 void set_last_error(const std::string& msg);  // message of dogip_last_error()
 void cuda_check(cudaError_t e, const char* what);
 
+// Device arrays of the sub-element quadrature of an inclusion coefficient.
+struct QuadCoef {
+  const double* pts;      // [nq x d] reference points
+  const double* wts;      // [nq]
+  const double* phi;      // [nq x W_T] W-basis values
+  int nq;
+  const double* centres;  // [nb x d]
+  const double* radii;    // [nb]
+  int nb;
+  double inside, outside;
+};
+
 // ---- kernel launchers (implemented in the .cu translation units) ----------
 // All take the processing-order state of ctx and enqueue on `s`.
 void launch_ahat(Ctx& c, const double* coef, int coef_kind, cudaStream_t s);
+void launch_ahat_quad(Ctx& c, const QuadCoef& qc, cudaStream_t s);
 void launch_apply(Ctx& c, const void* u, void* y, int R, int prec, int scatter,
                   cudaStream_t s, const int* skip);
 // The apply inside a CG iteration, q = K p.  With atomic scatter q must already be

@@ -630,6 +630,184 @@ __global__ void __launch_bounds__(128) k_ahat(AhatArgs a) {
   });
 }
 
+
+// Sub-element integration of a discontinuous coefficient (the niche the paper
+// names for DoGIP: quadrature is done once here, never in the apply).  For an
+// isotropic field m(x) given by spherical inclusions (value `inside` in any ball,
+// `outside` elsewhere) every W-node integral
+//   sigma_j = int_That m(F_T(x)) phi^W_j(x) dx ~ sum_q w_q m(F_T(x_q)) phi^W_j(x_q)
+// is taken with a composite collapsed Gauss rule of nq points, and
+//   A_T,j = sigma_j |det R_T| R_T^-1 R_T^-T (elliptic) or sigma_j |det R_T| (projection).
+struct AhatQuadArgs {
+  const double* coords;
+  const int32_t* cells;
+  const uint32_t* conn;
+  double* A64;
+  float* A32;
+  double* geo;
+  double* diag;
+  int* err;
+  int64_t E;
+  const double* qpts;   // [nq x D] reference points
+  const double* qw;     // [nq]
+  const double* phi;    // [nq x W] W-basis values at the points
+  int nq;
+  const double* centres;  // [nb x D]
+  const double* radii;    // [nb]
+  int nb;
+  double inside, outside;
+};
+
+template <int D, int P, int FORM>
+__global__ void __launch_bounds__(128) k_ahat_quad(AhatQuadArgs a) {
+  using TB = dogip_tab::Tab<D, P, FORM>;
+  constexpr int V = TB::V, W = TB::W, NB = TB::NB, NS = NSym<D, FORM>::value;
+  constexpr int kMaxCand = 16;
+  const int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (pos >= a.E) return;
+  double X[D + 1][D];
+  static_for<D + 1>([&](auto ic) {
+    constexpr int i = decltype(ic)::value;
+    const int64_t v = a.cells[pos * (D + 1) + i];
+    static_for<D>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      X[i][k] = a.coords[v * D + k];
+    });
+  });
+  double R[D][D], Ri[D][D];
+  static_for<D>([&](auto ic) {
+    constexpr int i = decltype(ic)::value;
+    static_for<D>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      R[i][k] = X[k + 1][i] - X[0][i];
+    });
+  });
+  const double det = det_inv<D>(R, Ri);
+  const double vol = fabs(det);
+  if (!(vol > 0.0) || !isfinite(det)) atomicOr(a.err, kErrGeometry);
+  // balls that can meet the cell: distance from centre to the bounding box <= r
+  double lo[D], hi[D];
+  static_for<D>([&](auto kc) {
+    constexpr int k = decltype(kc)::value;
+    lo[k] = hi[k] = X[0][k];
+    static_for<D>([&](auto ic) {
+      constexpr int i = decltype(ic)::value + 1;
+      lo[k] = fmin(lo[k], X[i][k]);
+      hi[k] = fmax(hi[k], X[i][k]);
+    });
+  });
+  int cand[kMaxCand];
+  int nc = 0;
+  bool overflow = false;
+  for (int b = 0; b < a.nb; ++b) {
+    double dd = 0.0;
+    for (int k = 0; k < D; ++k) {
+      const double c = a.centres[b * D + k];
+      const double e = c < lo[k] ? lo[k] - c : (c > hi[k] ? c - hi[k] : 0.0);
+      dd += e * e;
+    }
+    if (dd <= a.radii[b] * a.radii[b]) {
+      if (nc < kMaxCand) cand[nc++] = b;
+      else overflow = true;
+    }
+  }
+  double sig[W];
+  static_for<W>([&](auto jc) { sig[decltype(jc)::value] = 0.0; });
+  for (int q = 0; q < a.nq; ++q) {
+    double x[D];
+    static_for<D>([&](auto ic) {
+      constexpr int i = decltype(ic)::value;
+      x[i] = X[0][i];
+      static_for<D>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        x[i] = fma(R[i][k], a.qpts[q * D + k], x[i]);
+      });
+    });
+    double m = a.outside;
+    const int nt = overflow ? a.nb : nc;
+    for (int t = 0; t < nt; ++t) {
+      const int b = overflow ? t : cand[t];
+      double dd = 0.0;
+      for (int k = 0; k < D; ++k) {
+        const double e = x[k] - a.centres[b * D + k];
+        dd += e * e;
+      }
+      if (dd <= a.radii[b] * a.radii[b]) {
+        m = a.inside;
+        break;
+      }
+    }
+    const double wm = a.qw[q] * m;
+    static_for<W>([&](auto jc) {
+      constexpr int j = decltype(jc)::value;
+      sig[j] = fma(wm, a.phi[q * W + j], sig[j]);
+    });
+  }
+  double K[NS];
+  if constexpr (FORM == DOGIP_PROJECTION) {
+    K[0] = vol;
+  } else {
+    static_for<D>([&](auto rc) {
+      constexpr int r = decltype(rc)::value;
+      static_for<D>([&](auto sc) {
+        constexpr int s_ = decltype(sc)::value;
+        if constexpr (r <= s_) {
+          double acc = 0.0;
+          static_for<D>([&](auto pc) {
+            constexpr int p = decltype(pc)::value;
+            acc += Ri[r][p] * Ri[s_][p];
+          });
+          K[sym_idx(D, r, s_)] = vol * acc;
+        }
+      });
+    });
+  }
+  const int64_t tile = pos >> 5;
+  const int lane = (int)(pos & 31);
+  double* At = a.A64 + tile * ((int64_t)W * NS * kTile) + lane;
+  float* At32 = a.A32 ? a.A32 + tile * ((int64_t)W * NS * kTile) + lane : nullptr;
+  static_for<W>([&](auto jc) {
+    constexpr int j = decltype(jc)::value;
+    static_for<NS>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      const double v = sig[j] * K[k];
+      At[(j * NS + k) * kTile] = v;
+      if (At32) At32[(j * NS + k) * kTile] = (float)v;
+    });
+  });
+  double* g = a.geo + pos * (D * D + 1);
+  static_for<D>([&](auto ic) {
+    constexpr int i = decltype(ic)::value;
+    static_for<D>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      g[i * D + k] = Ri[i][k];
+    });
+  });
+  g[D * D] = vol;
+  const uint32_t* ct = a.conn + tile * (V * kTile) + lane;
+  static_for<V>([&](auto lc) {
+    constexpr int l = decltype(lc)::value;
+    const uint32_t cl = ct[l * kTile];
+    if (!(cl & kBndBit)) {
+      double acc = 0.0;
+      static_for<W>([&](auto jc) {
+        constexpr int j = decltype(jc)::value;
+        double qv = 0.0;
+        static_for<NB>([&](auto rc) {
+          constexpr int r = decltype(rc)::value;
+          static_for<NB>([&](auto sc) {
+            constexpr int s_ = decltype(sc)::value;
+            constexpr double br = TB::B[r][j][l], bs = TB::B[s_][j][l];
+            if constexpr (br != 0.0 && bs != 0.0) qv += br * bs * K[sym_idx(D, r, s_)];
+          });
+        });
+        acc += sig[j] * qv;
+      });
+      atomicAdd(a.diag + (cl & kIdMask), acc);
+    }
+  });
+}
+
 struct LoadArgs {
   const double* geo;
   const int64_t* perm;

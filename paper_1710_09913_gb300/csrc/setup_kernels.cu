@@ -69,6 +69,14 @@ void ahat_one(Ctx& c, const double* coef, int coef_kind, cudaStream_t s) {
 }
 
 template <int D, int P, int FORM>
+void ahat_quad_one(Ctx& c, const QuadCoef& qc, cudaStream_t s) {
+  AhatQuadArgs a{c.d_coords, c.d_cells, c.d_conn, c.d_A64, c.keep32 ? c.d_A32 : nullptr, c.d_geo,
+                 c.d_diag, c.d_err, c.E, qc.pts, qc.wts, qc.phi, qc.nq, qc.centres, qc.radii, qc.nb,
+                 qc.inside, qc.outside};
+  k_ahat_quad<D, P, FORM><<<(unsigned)((c.E + 127) / 128), 128, 0, s>>>(a);
+}
+
+template <int D, int P, int FORM>
 void load_one(Ctx& c, const double* f, double* b, cudaStream_t s) {
   LoadArgs a{c.d_geo, c.d_perm, f, c.d_conn, b, c.E};
   k_load<D, P, FORM><<<(unsigned)((c.E + 127) / 128), 128, 0, s>>>(a);
@@ -131,6 +139,18 @@ void launch_ahat(Ctx& c, const double* coef, int coef_kind, cudaStream_t s) {
 #undef CALL
   if (!ok_) fail(DOGIP_EUNSUPPORTED, "no compiled instance for this (dim, p, form)");
   cuda_check(cudaGetLastError(), "ahat kernel launch");
+  c.launches += 1;
+  launch_diag_finish(c, s);
+}
+
+void launch_ahat_quad(Ctx& c, const QuadCoef& qc, cudaStream_t s) {
+  bool ok_ = true;
+  cuda_check(cudaMemsetAsync(c.d_diag, 0, sizeof(double) * c.n, s), "memset diag");
+#define CALL(D, P, F) ahat_quad_one<D, P, F>(c, qc, s)
+  DOGIP_DISPATCH(c.d, c.p, c.form, CALL);
+#undef CALL
+  if (!ok_) fail(DOGIP_EUNSUPPORTED, "no compiled instance for this (dim, p, form)");
+  cuda_check(cudaGetLastError(), "quadrature ahat kernel launch");
   c.launches += 1;
   launch_diag_finish(c, s);
 }

@@ -187,17 +187,31 @@ def coef_tensor_lognormal(E: int, d: int, sigma: float, seed: int) -> np.ndarray
     return 0.5 * (A + A.transpose(0, 2, 1))
 
 
-def coef_inclusions(cent: np.ndarray, n_incl: int, rmin: float, rmax: float, seed: int,
-                    inside: float = 100.0, outside: float = 1.0) -> np.ndarray:
-    """Per-element scalar: ``inside`` if the element centroid lies in any of
-    ``n_incl`` balls (centres U[0,1]^d, radii U[rmin, rmax]), else ``outside``."""
-    d = cent.shape[1]
+def inclusion_balls(d: int, n_incl: int, rmin: float, rmax: float, seed: int):
+    """``n_incl`` balls: centres U[0,1]^d, radii U[rmin, rmax]."""
     ctr = uniform(seed, STREAM_INCL_CENTRE, n_incl * d).reshape(n_incl, d)
     rad = rmin + (rmax - rmin) * uniform(seed, STREAM_INCL_RADIUS, n_incl)
-    hit = np.zeros(cent.shape[0], dtype=bool)
-    for c, r in zip(ctr, rad):
-        hit |= np.sum((cent - c) ** 2, axis=1) <= r * r
-    return np.where(hit, inside, outside)
+    return ctr, rad
+
+
+def inclusion_field(centres: np.ndarray, radii: np.ndarray, inside: float, outside: float):
+    """The field m(x) = ``inside`` in the union of the balls (|x - c|^2 <= r^2),
+    ``outside`` elsewhere, as a function of points [..., d]."""
+    def m(X):
+        X = np.asarray(X, dtype=np.float64)
+        hit = np.zeros(X.shape[:-1], dtype=bool)
+        for c, r in zip(centres, radii):
+            hit |= np.sum((X - c) ** 2, axis=-1) <= r * r
+        return np.where(hit, inside, outside)
+    return m
+
+
+def coef_inclusions(cent: np.ndarray, n_incl: int, rmin: float, rmax: float, seed: int,
+                    inside: float = 100.0, outside: float = 1.0) -> np.ndarray:
+    """Per-element scalar: the inclusion field of ``inclusion_balls`` at the element
+    centroid."""
+    ctr, rad = inclusion_balls(cent.shape[1], n_incl, rmin, rmax, seed)
+    return inclusion_field(ctr, rad, inside, outside)(cent)
 
 
 def rhs_normal(n: int, R: int, seed: int) -> np.ndarray:

@@ -403,3 +403,42 @@ def test_factorized_rejects_colour(B):
         B.Context(coords, cells, 2, "elliptic", np.ones(len(cells)), factorized=True,
                   scatter="colour")
     assert e.value.code == B.EINVAL
+
+
+@pytest.mark.parametrize("d,p,form,nq", [(2, 2, "elliptic", 6), (2, 3, "projection", 5),
+                                         (3, 2, "elliptic", 4), (3, 1, "projection", 3),
+                                         (2, 1, "elliptic", 8)])
+def test_subelement_inclusions(B, d, p, form, nq):
+    """A_T of a discontinuous inclusion field integrated per W node by the sub-element
+    rule (dogip_set_coef_inclusions) equals the oracle's independent quadrature; the
+    apply with it matches the oracle apply; the solve meets its tolerance."""
+    N = 12 if d == 2 else 4
+    coords, cells = inputs.lattice_mesh(d, N, 0.2 if d == 2 else 0.1, 6)
+    ctr, rad = inputs.inclusion_balls(d, 20, 0.05, 0.2, seed=6)
+    ctx = B.Context(coords, cells, p, form, np.ones(len(cells)))
+    ctx.set_coef_inclusions(ctr, rad, 100.0, 1.0, nq)
+    P = odogip.Problem(form, p, coords, cells, np.ones(len(cells)))
+    P.Ah = odogip.ahat_quadrature(form, p, coords, cells,
+                                  inputs.inclusion_field(ctr, rad, 100.0, 1.0), nq)
+    A = ctx.ahat().cpu().numpy()
+    ref = pack(P)
+    assert np.all(np.abs(A - ref) <= 1e-12 * np.abs(ref).max(axis=(1, 2), keepdims=True))
+    u = inputs.rhs_normal(P.n, 1, seed=7)[:, 0]
+    y = ctx.apply(torch.tensor(u, device="cuda")).cpu().numpy()
+    assert np.all(np.abs(y - P.apply(u)) <= TOL64 * P.apply_abs(u))
+    b = ctx.load()
+    x, info = ctx.solve(b, mode="mixed", tol=1e-9)
+    r = b.cpu().numpy() - P.apply(x.cpu().numpy())
+    assert info["status"] == 0 and np.linalg.norm(r) <= 1.01e-9 * np.linalg.norm(b.cpu().numpy())
+    with pytest.raises(B.DogipError):  # no element-wise coefficient to differentiate
+        ctx.grad_coef(x, x)
+
+
+def test_subelement_constant_field_equals_elementwise(B):
+    coords, cells = inputs.lattice_mesh(2, 10, 0.2, 3)
+    a = B.Context(coords, cells, 3, "elliptic", np.full(len(cells), 2.5))
+    b = B.Context(coords, cells, 3, "elliptic", np.ones(len(cells)))
+    b.set_coef_inclusions(np.zeros((0, 2)), np.zeros(0), 7.0, 2.5, 4)
+    Aa, Ab = a.ahat().cpu().numpy(), b.ahat().cpu().numpy()
+    assert np.abs(Aa - Ab).max() <= 1e-13 * np.abs(Aa).max()
+    np.testing.assert_allclose(a.diag().cpu().numpy(), b.diag().cpu().numpy(), rtol=1e-13)

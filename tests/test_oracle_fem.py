@@ -216,3 +216,28 @@ def test_gradient(d, form, p):
                 fd = (b @ solve(cp) - b @ solve(cm)) / (2 * h)
                 an = g1[e, a_, c_] + (g1[e, c_, a_] if a_ != c_ else 0.0)
                 assert abs(fd - an) <= 1e-6 * np.abs(g1).max()
+
+
+@pytest.mark.parametrize("d,form,p", [(2, "elliptic", 2), (2, "projection", 2), (3, "elliptic", 2),
+                                      (2, "elliptic", 1), (3, "projection", 1)])
+def test_quadrature_ahat_constant_equals_exact(d, form, p):
+    """Sub-element quadrature of a constant coefficient reproduces the exact A_T
+    (the rule is exact to degree 2 nq - 1 >= the W degree)."""
+    c, t = inputs.lattice_mesh(d, 3, 0.2 if d == 2 else 0.1, 4)
+    nq = refelem.w_degree(form, p) // 2 + 1
+    Aq = dogip.ahat_quadrature(form, p, c, t, lambda X: np.full(X.shape[:-1], 3.5), nq)
+    Ae = dogip.ahat(form, p, c, t, np.full(len(t), 3.5))
+    np.testing.assert_allclose(Aq, Ae, rtol=0, atol=1e-13 * np.abs(Ae).max())
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_quadrature_ahat_measures_a_ball(d):
+    """sum over cells and W nodes of sigma_T,j |det R_T| = int m: for one ball of
+    radius r inside the domain with m = 1 in it and 0 outside, the measure of the
+    ball (pi r^2, 4/3 pi r^3) to the accuracy of the sub-element rule."""
+    N, r = (16, 0.3) if d == 2 else (6, 0.3)
+    c, t = inputs.lattice_mesh(d, N)
+    m = inputs.inclusion_field(np.full((1, d), 0.5), np.array([r]), 1.0, 1e-300)
+    A = dogip.ahat_quadrature("projection", 1, c, t, m, 12)
+    exact = np.pi * r * r if d == 2 else 4.0 / 3.0 * np.pi * r ** 3
+    assert abs(A.sum() - exact) <= 2e-3 * exact
