@@ -24,8 +24,8 @@ LIB = os.path.join(PKG, "libdogip.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "--expt-relaxed-constexpr", "-O3", "-lineinfo", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-fvisibility=hidden"]
-UNITS = ["host.cpp", "setup_kernels.cu", "vec.cu", "apply_d2.cu", "apply_d3a.cu", "apply_d3b.cu",
-         "noalloc.cu"]
+UNITS = ["host.cpp", "setup_kernels.cu", "setup_d2.cu", "setup_d3.cu", "vec.cu", "apply_d2.cu",
+         "apply_d3a.cu", "apply_d3b.cu", "noalloc.cu"]
 
 PMAX2, PMAX3 = 4, 3
 

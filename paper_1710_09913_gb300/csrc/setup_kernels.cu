@@ -2,9 +2,20 @@
 // export) and of the apply dispatcher, plus host access to the static tables.
 #include <cstring>
 
-#include "kernels.cuh"
+#include "setup_inst.cuh"
 
 namespace dogip {
+
+bool setup_d2(Ctx& c, const SetupCall& k, cudaStream_t s);
+bool setup_d3(Ctx& c, const SetupCall& k, cudaStream_t s);
+
+namespace {
+void setup_dispatch(Ctx& c, const SetupCall& k, cudaStream_t s, const char* what) {
+  const bool ok = c.d == 2 ? setup_d2(c, k, s) : setup_d3(c, k, s);
+  if (!ok) fail(DOGIP_EUNSUPPORTED, "no compiled instance for this (dim, p, form)");
+  cuda_check(cudaGetLastError(), what);
+}
+}  // namespace
 
 // Apply dispatchers (apply_d*.cu): 0 = not compiled, 1 = per-cell kernel, 2 = staged
 // kernel (which also wrote the Dirichlet rows).
@@ -61,34 +72,6 @@ __global__ void k_diag_inv(const double* diag, double* dinv64, float* dinv32, in
 namespace {
 
 template <int D, int P, int FORM>
-void ahat_one(Ctx& c, const double* coef, int coef_kind, cudaStream_t s) {
-  AhatArgs a{c.d_coords, c.factorized ? 1 : 0, c.d_cells, c.d_perm, coef, coef_kind, c.d_conn, c.d_A64,
-             c.keep32 ? c.d_A32 : nullptr, c.d_geo, c.d_diag, c.d_err, c.E};
-  const unsigned nb = (unsigned)((c.E + 127) / 128);
-  k_ahat<D, P, FORM><<<nb, 128, 0, s>>>(a);
-}
-
-template <int D, int P, int FORM>
-void ahat_quad_one(Ctx& c, const QuadCoef& qc, cudaStream_t s) {
-  AhatQuadArgs a{c.d_coords, c.d_cells, c.d_conn, c.d_A64, c.keep32 ? c.d_A32 : nullptr, c.d_geo,
-                 c.d_diag, c.d_err, c.E, qc.pts, qc.wts, qc.phi, qc.nq, qc.centres, qc.radii, qc.nb,
-                 qc.inside, qc.outside};
-  k_ahat_quad<D, P, FORM><<<(unsigned)((c.E + 127) / 128), 128, 0, s>>>(a);
-}
-
-template <int D, int P, int FORM>
-void load_one(Ctx& c, const double* f, double* b, cudaStream_t s) {
-  LoadArgs a{c.d_geo, c.d_perm, f, c.d_conn, b, c.E};
-  k_load<D, P, FORM><<<(unsigned)((c.E + 127) / 128), 128, 0, s>>>(a);
-}
-
-template <int D, int P, int FORM>
-void grad_one(Ctx& c, const double* u, const double* lam, double* dA, cudaStream_t s) {
-  GradArgs a{c.d_geo, c.d_perm, c.d_conn, u, lam, dA, c.coef_kind, c.E};
-  k_grad<D, P, FORM><<<(unsigned)((c.E + 127) / 128), 128, 0, s>>>(a);
-}
-
-template <int D, int P, int FORM>
 void info_one(int* NB, int* W, int* V, long long* nnz, long long* nnz1) {
   using TB = dogip_tab::Tab<D, P, FORM>;
   *NB = TB::NB;
@@ -132,25 +115,22 @@ void copy_one(double* B, double* w, double* iv) {
 }  // namespace
 
 void launch_ahat(Ctx& c, const double* coef, int coef_kind, cudaStream_t s) {
-  bool ok_ = true;
   cuda_check(cudaMemsetAsync(c.d_diag, 0, sizeof(double) * c.n, s), "memset diag");
-#define CALL(D, P, F) ahat_one<D, P, F>(c, coef, coef_kind, s)
-  DOGIP_DISPATCH(c.d, c.p, c.form, CALL);
-#undef CALL
-  if (!ok_) fail(DOGIP_EUNSUPPORTED, "no compiled instance for this (dim, p, form)");
-  cuda_check(cudaGetLastError(), "ahat kernel launch");
+  SetupCall k;
+  k.op = kSetupAhat;
+  k.coef = coef;
+  k.coef_kind = coef_kind;
+  setup_dispatch(c, k, s, "ahat kernel launch");
   c.launches += 1;
   launch_diag_finish(c, s);
 }
 
 void launch_ahat_quad(Ctx& c, const QuadCoef& qc, cudaStream_t s) {
-  bool ok_ = true;
   cuda_check(cudaMemsetAsync(c.d_diag, 0, sizeof(double) * c.n, s), "memset diag");
-#define CALL(D, P, F) ahat_quad_one<D, P, F>(c, qc, s)
-  DOGIP_DISPATCH(c.d, c.p, c.form, CALL);
-#undef CALL
-  if (!ok_) fail(DOGIP_EUNSUPPORTED, "no compiled instance for this (dim, p, form)");
-  cuda_check(cudaGetLastError(), "quadrature ahat kernel launch");
+  SetupCall k;
+  k.op = kSetupAhatQuad;
+  k.qc = &qc;
+  setup_dispatch(c, k, s, "quadrature ahat kernel launch");
   c.launches += 1;
   launch_diag_finish(c, s);
 }
@@ -166,35 +146,31 @@ void launch_diag_finish(Ctx& c, cudaStream_t s) {
 }
 
 void launch_load(Ctx& c, const double* f, double* b, cudaStream_t s) {
-  bool ok_ = true;
   cuda_check(cudaMemsetAsync(b, 0, sizeof(double) * c.n, s), "memset load");
-#define CALL(D, P, F) load_one<D, P, F>(c, f, b, s)
-  DOGIP_DISPATCH(c.d, c.p, c.form, CALL);
-#undef CALL
-  if (!ok_) fail(DOGIP_EUNSUPPORTED, "no compiled instance for this (dim, p, form)");
-  cuda_check(cudaGetLastError(), "load kernel launch");
+  SetupCall k;
+  k.op = kSetupLoad;
+  k.f = f;
+  k.b = b;
+  setup_dispatch(c, k, s, "load kernel launch");
   c.launches += 1;
 }
 
 void launch_grad(Ctx& c, const double* u, const double* lam, double* dA, cudaStream_t s) {
-  bool ok_ = true;
-#define CALL(D, P, F) grad_one<D, P, F>(c, u, lam, dA, s)
-  DOGIP_DISPATCH(c.d, c.p, c.form, CALL);
-#undef CALL
-  if (!ok_) fail(DOGIP_EUNSUPPORTED, "no compiled instance for this (dim, p, form)");
-  cuda_check(cudaGetLastError(), "gradient kernel launch");
+  SetupCall k;
+  k.op = kSetupGrad;
+  k.u = u;
+  k.lam = lam;
+  k.dA = dA;
+  setup_dispatch(c, k, s, "gradient kernel launch");
   c.launches += 1;
 }
 
 void launch_export_ahat(const Ctx& c, double* out, cudaStream_t s) {
   if (c.factorized) {
-    bool ok_ = true;
-    const unsigned nb = (unsigned)((c.E + 127) / 128);
-#define CALL(D, P, F) k_export_fact<D, P, F><<<nb, 128, 0, s>>>(c.d_A64, c.d_perm, out, c.E)
-    DOGIP_DISPATCH(c.d, c.p, c.form, CALL);
-#undef CALL
-    if (!ok_) fail(DOGIP_EUNSUPPORTED, "no compiled instance for this (dim, p, form)");
-    cuda_check(cudaGetLastError(), "export kernel launch");
+    SetupCall k;
+    k.op = kSetupExportFact;
+    k.out = out;
+    setup_dispatch(const_cast<Ctx&>(c), k, s, "export kernel launch");
     return;
   }
   const int nsw = c.WT * c.NS;
