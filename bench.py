@@ -635,6 +635,110 @@ def main():
         fact[f"P{p}"] = out
         del cf
 
+    # the conventional quadrature-point matrix-free apply on the same GPU (comparator):
+    # geometry from the vertex coordinates at every apply, the cell's coefficient, and
+    # a collapsed Gauss-Jacobi rule of p^2 points (stiffness, element-constant M_T)
+    qp = {}
+    for p in P_LIST:
+        c = ctxs[p]
+        c.set_coef(A_dev)
+        inf = c.info
+        out = {"points_per_cell": p * p, "dogip_w_nodes": inf.w_loc}
+        for prec, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
+            u = torch.randn(c.n, dtype=dt, device="cuda")
+            y = torch.empty_like(u)
+            for _ in range(3):
+                c.apply_qp(u, y, prec=prec)
+            reps = 30 if prec == "fp32" else 10
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(reps):
+                c.apply_qp(u, y, prec=prec)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1) / reps
+            s_ = dt.itemsize
+            byt = E * (inf.v_loc * 4 + 3 * 4 + inf.n_sym * s_) + len(coords) * 2 * 8 + 2 * c.n * s_
+            out[f"apply_{prec}_ms"] = round(ms, 4)
+            out[f"apply_{prec}_gdofs"] = round(c.n / ms / 1e6, 3)
+            out[f"apply_{prec}_GBps"] = round(byt / ms / 1e6, 1)
+            out[f"dogip_apply_{prec}_ms"] = applies[f"P{p}_{prec}"]["ms"]
+        qp[f"P{p}"] = out
+
+    # global double grid of the weighted projection (one A_diag value per global W node)
+    # against the element-wise projection on the same mesh (scalar lognormal m)
+    gw = {}
+    from paper_1710_09913_gb300 import inputs as _inp
+    m_wp = _inp.coef_lognormal(E, 1.0, seed=7)
+    for p in P_LIST:
+        out = {}
+        for tag, kw in (("elementwise", {}), ("global", {"global_w": True})):
+            c = B.Context(coords, cells, p, "projection", m_wp, **kw)
+            c.autotune()
+            inf = c.info
+            o = {"bytes_ahat_fp32": int(inf.bytes_ahat_fp32), "bytes_index": int(inf.bytes_conn)}
+            for prec, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
+                u = torch.randn(c.n, dtype=dt, device="cuda")
+                y = torch.empty_like(u)
+                for _ in range(3):
+                    c.apply(u, y, prec=prec)
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                ev0.record(stream)
+                for _ in range(20):
+                    c.apply(u, y, prec=prec)
+                ev1.record(stream)
+                torch.cuda.synchronize()
+                o[f"apply_{prec}_ms"] = round(ev0.elapsed_time(ev1) / 20, 4)
+            b = c.load()
+            ux = torch.zeros_like(b)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            _, info = c.solve(b, ux, mode="mixed", tol=TOL, check_every=args.check_every)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            o.update(mixed_ms=round(ev0.elapsed_time(ev1), 2), mixed_iters=info["iterations"])
+            if tag == "global":
+                o["n_w_global"] = int(inf.n_wglobal)
+            out[tag] = o
+            del c
+        gw[f"P{p}"] = out
+
+    # higher orders of Tables 3-4 (run-time-table kernels), same mesh and tensors
+    hi_ord = {}
+    for p in (5, 6, 7, 8):
+        c = B.Context(coords, cells, p, "elliptic", A)
+        inf = c.info
+        out = {"dofs": c.n, "w_loc": inf.w_loc, "v_loc": inf.v_loc}
+        for prec, dt, s_ in (("fp32", torch.float32, 4), ("fp64", torch.float64, 8)):
+            u = torch.randn(c.n, dtype=dt, device="cuda")
+            y = torch.empty_like(u)
+            for _ in range(2):
+                c.apply(u, y, prec=prec)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(5):
+                c.apply(u, y, prec=prec)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1) / 5
+            byt = E * inf.w_loc * inf.n_sym * s_ + E * inf.v_loc * 4 + 2 * c.n * s_
+            flops = E * (2 * 2 * inf.w_loc * inf.v_loc * 2 + (2 * 4 - 2) * inf.w_loc)
+            out[f"apply_{prec}_ms"] = round(ms, 4)
+            out[f"apply_{prec}_gdofs"] = round(c.n / ms / 1e6, 3)
+            out[f"apply_{prec}_GBps"] = round(byt / ms / 1e6, 1)
+            out[f"apply_{prec}_TFLOPs_dense"] = round(flops / ms / 1e9, 3)
+        hi_ord[f"P{p}"] = out
+        del c
+        torch.cuda.empty_cache()
+
     dom = applies["P4_fp32"]
     roofline = {"bound": "hbm", "achieved": dom["GBps"], "peak": hbm, "unit": "GB/s",
                 "frac": round(dom["GBps"] / hbm, 4), "traffic": None,
@@ -688,7 +792,8 @@ def main():
                 "value_definition": "sum_p n_p x operator applies / step time (applies inside the "
                                     "mixed solves, FP32 inner and FP64 residual)",
                 "time_to_tol": t2t, "apply": applies, "csr_baseline": csr, "batch_uneven": batch,
-                "cube_p2_16rhs": multi, "factorized": fact,
+                "cube_p2_16rhs": multi, "factorized": fact, "quadrature_point_comparator": qp,
+                "global_double_grid_projection": gw, "high_order": hi_ord,
                 "roofline": roofline,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks}
         print(json.dumps(line), flush=True)

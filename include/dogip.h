@@ -108,6 +108,12 @@ typedef struct {
                       m_T |det R_T|): only K_T is stored (d(d+1)/2 or 1 values
                       per cell) and w_j is applied inside the kernel.  Needs
                       scatter = ATOMIC.                                         */
+  int global_w;    /* 0 (default): element-wise DoGIP.  1 (projection only): the
+                      global double grid of §2.2, Theorem "DoGIP for weighted
+                      projection": W = C_{N,2p} continuous, K = B^* A_diag B with
+                      A_diag,ii = int m phi_W^i stored once per global W node
+                      (instead of W_T values per cell); needs factorized = 0,
+                      scatter = ATOMIC and no Dirichlet rows.                    */
 } dogip_opts;
 
 /* Fill *o with the defaults above.  Never fails for o != NULL. */
@@ -172,6 +178,9 @@ typedef struct {
   int64_t bytes_ahat_fp64, bytes_ahat_fp32, bytes_conn;
   int64_t kernel_launches; /* kernels this context has launched so far,
                               counting every node of replayed CUDA graphs   */
+  int64_t n_wglobal;       /* global W nodes (global_w), else 0; then the
+                              bytes_ahat_* fields count A_diag and bytes_conn
+                              includes the W-node map                        */
 } dogip_info;
 
 DOGIP_API int dogip_get_info(const dogip_ctx* ctx, dogip_info* info);
@@ -188,6 +197,14 @@ DOGIP_API int dogip_get_boundary(const dogip_ctx* ctx, uint8_t* host_out);
 DOGIP_API int dogip_get_ahat(const dogip_ctx* ctx, double* dev_out, void* cuda_stream);
 /* Jacobi diagonal of the operator (1 on Dirichlet rows): device [n_dofs]. Async. */
 DOGIP_API int dogip_get_diag(const dogip_ctx* ctx, double* dev_out, void* cuda_stream);
+
+/* Global double grid only (global_w = 1):
+ * A_diag: device double [n_W] (n_W = info.n_wglobal).  Async.
+ * W-node map: host int32 [n_cells x W_T] global W-node ids (first appearance,
+ * like the dof map, at order 2p) and host uint8 [n_cells x W_T] owner flags (1 in
+ * the first cell containing the node); either pointer may be NULL. */
+DOGIP_API int dogip_get_ahat_global(const dogip_ctx* ctx, double* dev_out, void* cuda_stream);
+DOGIP_API int dogip_get_wdofmap(const dogip_ctx* ctx, int32_t* host_ids, uint8_t* host_owner);
 
 /*
  * Reference tables of the library, independent of any context (host):
@@ -208,10 +225,29 @@ DOGIP_API int dogip_get_tables(int dim, int p, int form, double* bhat, double* w
  *   prec  : DOGIP_FP64 or DOGIP_FP32 (the latter needs keep_fp32).
  *   scatter: DOGIP_SCATTER_ATOMIC, or DOGIP_SCATTER_COLOUR (needs a context
  *           set up with scatter = COLOUR), or -1 for the context default.
- * Asynchronous on cuda_stream; no host synchronisation.
+ * Asynchronous on cuda_stream; no host synchronisation.  A global_w context keeps
+ * an [n_W x nrhs] scratch; a call with more right-hand sides than before grows it
+ * (allocation and a sync of the context's stream), so such a call is not capturable:
+ * make the first call with the largest nrhs outside stream capture.
  */
 DOGIP_API int dogip_apply(dogip_ctx* ctx, const void* u, void* y, int nrhs, int prec,
                 int scatter, void* cuda_stream);
+
+/*
+ * Comparator, not the DoGIP path: the conventional quadrature-point matrix-free
+ * apply that the paper sets DoGIP against (§1 "alternative approaches", §3.3).
+ * y = K u with, per cell, the geometry R_T, |det R_T|, R_T^-1 recomputed from the
+ * vertex coordinates at every call, the cell's coefficient read from a per-cell
+ * stream, and the integral evaluated at the points of the collapsed Gauss-Jacobi
+ * rule with p + 1 (projection) or p (elliptic) points per direction, exact for
+ * element-constant coefficients; the result equals dogip_apply's up to rounding.
+ * Same arguments, layout and Dirichlet rows as dogip_apply; atomic scatter.
+ * Errors: DOGIP_EINVAL (arguments), DOGIP_EUNSUPPORTED after
+ * dogip_set_coef_inclusions (the per-cell coefficient no longer describes the
+ * field; dogip_set_coef restores it).  Asynchronous on cuda_stream.
+ */
+DOGIP_API int dogip_apply_qp(dogip_ctx* ctx, const void* u, void* y, int nrhs, int prec,
+                             void* cuda_stream);
 
 /*
  * Load vector of an element-wise constant source: b_i = sum_T f_T int_T phi_i

@@ -52,7 +52,7 @@ class Mesh(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("dirichlet", C.c_int), ("scatter", C.c_int), ("keep_fp32", C.c_int),
-                ("device", C.c_int), ("factorized", C.c_int)]
+                ("device", C.c_int), ("factorized", C.c_int), ("global_w", C.c_int)]
 
 
 class Info(C.Structure):
@@ -62,7 +62,7 @@ class Info(C.Structure):
                 ("w_loc", C.c_int), ("n_sym", C.c_int), ("n_colours", C.c_int),
                 ("nnz_b", C.c_int64), ("nnz_pm1_b", C.c_int64), ("bytes_ahat_fp64", C.c_int64),
                 ("bytes_ahat_fp32", C.c_int64), ("bytes_conn", C.c_int64),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("n_wglobal", C.c_int64)]
 
 
 class TuneInfo(C.Structure):
@@ -95,8 +95,11 @@ _SIGS = {
     "dogip_get_boundary": (C.c_int, [_vp, _vp]),
     "dogip_get_ahat": (C.c_int, [_vp, _vp, _vp]),
     "dogip_get_diag": (C.c_int, [_vp, _vp, _vp]),
+    "dogip_get_ahat_global": (C.c_int, [_vp, _vp, _vp]),
+    "dogip_get_wdofmap": (C.c_int, [_vp, _vp, _vp]),
     "dogip_get_tables": (C.c_int, [C.c_int, C.c_int, C.c_int, _vp, _vp, _vp]),
     "dogip_apply": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp]),
+    "dogip_apply_qp": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, _vp]),
     "dogip_load": (C.c_int, [_vp, _vp, _vp, _vp]),
     "dogip_solve_opts_default": (C.c_int, [C.POINTER(SolveOpts)]),
     "dogip_solve": (C.c_int, [_vp, _vp, _vp, C.c_int, C.POINTER(SolveOpts), C.POINTER(SolveInfo),
@@ -195,7 +198,7 @@ class Context:
     """A DoGIP operator on one mesh (wraps ``dogip_ctx``)."""
 
     def __init__(self, coords, cells, p, form, coef, *, dirichlet=None, scatter="atomic",
-                 keep_fp32=True, device=None, factorized=False):
+                 keep_fp32=True, device=None, factorized=False, global_w=False):
         coords = np.ascontiguousarray(coords, dtype=np.float64)
         cells = np.ascontiguousarray(cells, dtype=np.int32)
         coef = np.ascontiguousarray(coef, dtype=np.float64)
@@ -212,6 +215,7 @@ class Context:
         if device is not None:
             o.device = int(device)
         o.factorized = int(bool(factorized))
+        o.global_w = int(bool(global_w))
         kind = COEF_ELEM_TENSOR if coef.ndim == 3 else COEF_ELEM_SCALAR
         h = C.c_void_p()
         _check(lib.dogip_setup(C.byref(mesh), int(p), FORMS.get(form, form), kind,
@@ -261,6 +265,20 @@ class Context:
         _check(lib.dogip_get_ahat(self._h, _dptr(out), _stream(stream)))
         return out
 
+    def ahat_global(self, stream=None):
+        """A_diag of the global double grid (global_w contexts): [n_W] float64."""
+        import torch
+        out = torch.empty(self.info.n_wglobal, dtype=torch.float64, device="cuda")
+        _check(lib.dogip_get_ahat_global(self._h, _dptr(out), _stream(stream)))
+        return out
+
+    def wdofmap(self):
+        """(W-node ids [E, W_T] int32, owner flags [E, W_T] bool) of a global_w context."""
+        ids = np.zeros((self.E, self.info.w_loc), dtype=np.int32)
+        own = np.zeros((self.E, self.info.w_loc), dtype=np.uint8)
+        _check(lib.dogip_get_wdofmap(self._h, ids.ctypes.data_as(_vp), own.ctypes.data_as(_vp)))
+        return ids, own.astype(bool)
+
     def diag(self, stream=None):
         import torch
         out = torch.empty(self.n, dtype=torch.float64, device="cuda")
@@ -295,6 +313,20 @@ class Context:
             y = torch.empty_like(u)
         _check(lib.dogip_apply(self._h, _dptr(u, dt), _dptr(y, dt), R, pr, SCATTERS[scatter],
                                _stream(stream)))
+        return y
+
+    def apply_qp(self, u, y=None, prec="fp64", stream=None):
+        """Comparator: the quadrature-point matrix-free apply (dogip_apply_qp), same
+        result as ``apply`` up to rounding."""
+        import torch
+        pr = PRECS.get(prec, prec)
+        dt = torch.float64 if pr == FP64 else torch.float32
+        R = 1 if u.dim() == 1 else u.shape[1]
+        if u.shape[0] != self.n:
+            raise ValueError("u has the wrong number of dofs")
+        if y is None:
+            y = torch.empty_like(u)
+        _check(lib.dogip_apply_qp(self._h, _dptr(u, dt), _dptr(y, dt), R, pr, _stream(stream)))
         return y
 
     def load(self, f=None, b=None, stream=None):

@@ -25,9 +25,11 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "--expt-relaxed-constexpr", "-O3", "-lineinfo", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-fvisibility=hidden"]
 UNITS = ["host.cpp", "setup_kernels.cu", "setup_d2.cu", "setup_d3.cu", "vec.cu", "apply_d2.cu",
-         "apply_d3a.cu", "apply_d3b.cu", "noalloc.cu"]
+         "apply_d3a.cu", "apply_d3b.cu", "apply_qp2.cu", "apply_qp3.cu", "apply_gw.cu",
+         "apply_hi.cu", "noalloc.cu"]
 
-PMAX2, PMAX3 = 4, 3
+PMAX2, PMAX3 = 4, 3  # orders with compile-time tables (unrolled kernels)
+PHI2, PHI3 = 8, 4  # highest orders, served by the run-time-table kernels
 
 
 def _nvcc() -> str:
@@ -66,6 +68,9 @@ def build(verbose: bool = False, force: bool = False) -> str:
     _run(["g++", "-O2", "-std=c++17", "-o", gen, os.path.join(CSRC, "gen_tables.cpp")])
     hdr = _run([gen, str(PMAX2), str(PMAX3)])
     with open(os.path.join(BUILD, "tables_gen.h"), "w") as f:
+        f.write(hdr)
+    hdr = _run([gen, "--hi", str(PMAX2 + 1), str(PHI2), str(PMAX3 + 1), str(PHI3)])
+    with open(os.path.join(BUILD, "tables_hi.h"), "w") as f:
         f.write(hdr)
     objs = []
 

@@ -10,46 +10,103 @@
 // and the W-basis integrals w_j = int_That phi^W_j, expanded in barycentric
 // monomials and integrated with int_That lambda^k = prod k_i! / (|k| + d)!.
 // Each exact value is rounded once to double (correct rounding of n / d).
+//
+// For the quadrature-point matrix-free comparator it also emits TabQ<d, p, form>:
+// the same basis values / reference gradients at the points of the collapsed
+// Gauss-Jacobi rule with n points per direction (n = p + 1 for the mass integrand
+// of degree 2p, n = p for the stiffness integrand of degree 2p - 2; exact for
+// element-constant coefficients), evaluated in double, and the rule's weights.
 // Output: a C++ header on stdout.
+#include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
+#include <string>
 #include <vector>
+
+#include "quad.h"
 
 namespace {
 
+using I128 = __int128;
+using U128 = unsigned __int128;
+
 struct Rat {
-  long long n = 0, d = 1;
+  I128 n = 0, d = 1;
 };
-long long gabs(long long a) { return a < 0 ? -a : a; }
-long long ggcd(long long a, long long b) {
+[[noreturn]] void overflow() {
+  std::fprintf(stderr, "gen_tables: rational overflow\n");
+  std::exit(2);
+}
+I128 gabs(I128 a) { return a < 0 ? -a : a; }
+I128 ggcd(I128 a, I128 b) {
   a = gabs(a);
   b = gabs(b);
   while (b) {
-    long long t = a % b;
+    I128 t = a % b;
     a = b;
     b = t;
   }
   return a;
 }
-Rat mk(long long n, long long d) {
+I128 mul(I128 a, I128 b) {
+  I128 r;
+  if (__builtin_mul_overflow(a, b, &r)) overflow();
+  return r;
+}
+I128 add(I128 a, I128 b) {
+  I128 r;
+  if (__builtin_add_overflow(a, b, &r)) overflow();
+  return r;
+}
+Rat mk(I128 n, I128 d) {
   if (d < 0) { n = -n; d = -d; }
-  long long g = ggcd(n, d);
+  I128 g = ggcd(n, d);
   if (g == 0) g = 1;
   return Rat{n / g, d / g};
 }
 Rat operator*(Rat a, Rat b) {
-  long long g1 = ggcd(a.n, b.d), g2 = ggcd(b.n, a.d);
+  I128 g1 = ggcd(a.n, b.d), g2 = ggcd(b.n, a.d);
   if (g1 == 0) g1 = 1;
   if (g2 == 0) g2 = 1;
-  return mk((a.n / g1) * (b.n / g2), (a.d / g2) * (b.d / g1));
+  return mk(mul(a.n / g1, b.n / g2), mul(a.d / g2, b.d / g1));
 }
 Rat operator+(Rat a, Rat b) {
-  long long g = ggcd(a.d, b.d);
-  return mk(a.n * (b.d / g) + b.n * (a.d / g), (a.d / g) * b.d);
+  I128 g = ggcd(a.d, b.d);
+  return mk(add(mul(a.n, b.d / g), mul(b.n, a.d / g)), mul(a.d / g, b.d));
 }
 Rat operator-(Rat a, Rat b) { return a + Rat{-b.n, b.d}; }
-double dbl(Rat a) { return (double)a.n / (double)a.d; }
+
+// n / d rounded once to the nearest double (ties to even): binary long division to
+// 55 significant bits plus a sticky bit.
+double dbl(Rat a) {
+  if (a.n == 0) return 0.0;
+  const bool neg = a.n < 0;
+  U128 n = (U128)(neg ? -a.n : a.n), d = (U128)a.d;
+  U128 q = n / d, r = n % d;
+  auto bitlen = [](U128 x) {
+    int b = 0;
+    while (x) { ++b; x >>= 1; }
+    return b;
+  };
+  if (bitlen(q) > 55) overflow();  // table values are far below 2^55
+  uint64_t m = (uint64_t)q;
+  int e = 0;
+  while (bitlen(m) < 55) {
+    r <<= 1;  // r < d < 2^127
+    const uint64_t bit = r >= d ? 1u : 0u;
+    if (bit) r -= d;
+    m = (m << 1) | bit;
+    --e;
+  }
+  const bool sticky = r != 0;
+  uint64_t mant = m >> 2;
+  const unsigned rem = (unsigned)(m & 3u);
+  if (rem > 2 || (rem == 2 && (sticky || (mant & 1u)))) ++mant;
+  const double v = std::ldexp((double)mant, e + 2);
+  return neg ? -v : v;
+}
 
 int binom(int n, int k) {
   long long r = 1;
@@ -122,8 +179,8 @@ std::vector<Rat> poly(int q, int b) {
   return c;
 }
 
-long long fact(int n) {
-  long long r = 1;
+I128 fact(int n) {
+  I128 r = 1;
   for (int i = 2; i <= n; ++i) r *= i;
   return r;
 }
@@ -141,7 +198,7 @@ std::vector<Rat> w_integrals(int D, int q) {
     while (true) {
       Rat c{1, 1};
       int tot = 0;
-      long long num = 1;
+      I128 num = 1;
       for (int i = 0; i <= D; ++i) { c = c * P[i][k[i]]; tot += k[i]; num *= fact(k[i]); }
       if (c.n != 0) s = s + c * mk(num, fact(tot + D));
       int i = D;
@@ -153,19 +210,26 @@ std::vector<Rat> w_integrals(int D, int q) {
   return out;
 }
 
-void emit(int D, int p, int form) {
-  const int q = form == 0 ? 2 * p : 2 * p - 2;
-  const int NB = form == 0 ? 1 : D;
-  auto V = multi(D, p), W = multi(D, q);
-  if (q == 0) W = {std::vector<int>(D, 0)};
-  const int VT = (int)V.size(), WT = (int)W.size();
-  std::vector<double> B((size_t)NB * WT * VT);
+struct Tables {
+  int VT = 0, WT = 0, NB = 0, q = 0;
   long long nnz = 0, nnz1 = 0;
-  for (int j = 0; j < WT; ++j) {
-    auto lam = bary_of_node(D, q, W[j]);
-    for (int l = 0; l < VT; ++l) {
+  std::vector<double> B, w, iv;
+};
+
+Tables compute(int D, int p, int form) {
+  Tables t;
+  t.q = form == 0 ? 2 * p : 2 * p - 2;
+  t.NB = form == 0 ? 1 : D;
+  auto V = multi(D, p), W = multi(D, t.q);
+  if (t.q == 0) W = {std::vector<int>(D, 0)};
+  t.VT = (int)V.size();
+  t.WT = (int)W.size();
+  t.B.assign((size_t)t.NB * t.WT * t.VT, 0.0);
+  for (int j = 0; j < t.WT; ++j) {
+    auto lam = bary_of_node(D, t.q, W[j]);
+    for (int l = 0; l < t.VT; ++l) {
       auto be = beta_of(D, p, V[l]);
-      std::vector<Rat> vals(NB);
+      std::vector<Rat> vals(t.NB);
       if (form == 0) {
         Rat v{1, 1};
         for (int i = 0; i <= D; ++i) v = v * fac(p, be[i], lam[i]);
@@ -180,40 +244,150 @@ void emit(int D, int p, int form) {
         }
         for (int r = 0; r < D; ++r) vals[r] = dl[r + 1] - dl[0];
       }
-      for (int r = 0; r < NB; ++r) {
-        B[((size_t)r * WT + j) * VT + l] = dbl(vals[r]);
-        if (vals[r].n != 0) ++nnz;
-        if (gabs(vals[r].n) == 1 && vals[r].d == 1) ++nnz1;
+      for (int r = 0; r < t.NB; ++r) {
+        t.B[((size_t)r * t.WT + j) * t.VT + l] = dbl(vals[r]);
+        if (vals[r].n != 0) ++t.nnz;
+        if (gabs(vals[r].n) == 1 && vals[r].d == 1) ++t.nnz1;
       }
     }
   }
-  auto w = w_integrals(D, q);
-  auto iv = w_integrals(D, p);
+  for (auto& x : w_integrals(D, t.q)) t.w.push_back(dbl(x));
+  for (auto& x : w_integrals(D, p)) t.iv.push_back(dbl(x));
+  return t;
+}
+
+void print_array(const char* name, const std::vector<double>& v) {
+  std::printf("static const double %s[%zu] = {", name, v.size());
+  for (size_t i = 0; i < v.size(); ++i) std::printf("%s%.17g", i ? "," : "", v[i]);
+  std::printf("};\n");
+}
+
+void emit(int D, int p, int form) {
+  const Tables t = compute(D, p, form);
   std::printf("template <> struct Tab<%d, %d, %d> {\n", D, p, form);
-  std::printf("  static constexpr int D = %d, P = %d, FORM = %d, Q = %d;\n", D, p, form, q);
-  std::printf("  static constexpr int V = %d, W = %d, NB = %d;\n", VT, WT, NB);
-  std::printf("  static constexpr long long NNZ = %lld, NNZ1 = %lld;\n", nnz, nnz1);
-  std::printf("  static constexpr double B[%d][%d][%d] = {", NB, WT, VT);
+  std::printf("  static constexpr int D = %d, P = %d, FORM = %d, Q = %d;\n", D, p, form, t.q);
+  std::printf("  static constexpr int V = %d, W = %d, NB = %d;\n", t.VT, t.WT, t.NB);
+  std::printf("  static constexpr long long NNZ = %lld, NNZ1 = %lld;\n", t.nnz, t.nnz1);
+  std::printf("  static constexpr double B[%d][%d][%d] = {", t.NB, t.WT, t.VT);
+  for (size_t i = 0; i < t.B.size(); ++i) std::printf("%s%.17g", i ? "," : "", t.B[i]);
+  std::printf("};\n  static constexpr double w[%d] = {", t.WT);
+  for (int j = 0; j < t.WT; ++j) std::printf("%s%.17g", j ? "," : "", t.w[j]);
+  std::printf("};\n  static constexpr double iv[%d] = {", t.VT);
+  for (int l = 0; l < t.VT; ++l) std::printf("%s%.17g", l ? "," : "", t.iv[l]);
+  std::printf("};\n};\n");
+}
+
+// Runtime tables of the higher orders served by the generic kernels (plain arrays).
+void emit_hi(int pmin2, int pmax2, int pmin3, int pmax3) {
+  std::printf("// Generated by gen_tables.cpp at build time.  Do not edit.\n");
+  std::printf("#pragma once\nnamespace dogip_hi {\n");
+  std::printf("struct HiTab {\n  int d, p, form, V, W, NB;\n  long long nnz, nnz1;\n"
+              "  const double* B;\n  const double* w;\n  const double* iv;\n};\n");
+  std::vector<std::string> rows;
+  for (int D = 2; D <= 3; ++D)
+    for (int p = (D == 2 ? pmin2 : pmin3); p <= (D == 2 ? pmax2 : pmax3); ++p)
+      for (int form = 0; form < 2; ++form) {
+        const Tables t = compute(D, p, form);
+        char nb[64], nw[64], ni[64], row[512];
+        std::snprintf(nb, sizeof nb, "B_%d_%d_%d", D, p, form);
+        std::snprintf(nw, sizeof nw, "w_%d_%d_%d", D, p, form);
+        std::snprintf(ni, sizeof ni, "iv_%d_%d_%d", D, p, form);
+        print_array(nb, t.B);
+        print_array(nw, t.w);
+        print_array(ni, t.iv);
+        std::snprintf(row, sizeof row, "  {%d, %d, %d, %d, %d, %d, %lld, %lld, %s, %s, %s},", D, p,
+                      form, t.VT, t.WT, t.NB, t.nnz, t.nnz1, nb, nw, ni);
+        rows.push_back(row);
+      }
+  std::printf("static const HiTab kHiTabs[] = {\n");
+  for (auto& r : rows) std::printf("%s\n", r.c_str());
+  std::printf("};\nconstexpr int kNumHi = %zu;\n}  // namespace dogip_hi\n", rows.size());
+}
+
+// Double-precision versions of fac / dfac for irrational points.
+double facd(int p, int b, double t) {
+  double v = 1.0;
+  for (int m = 0; m < b; ++m) v *= (p * t - m) / (m + 1);
+  return v;
+}
+double dfacd(int p, int b, double t) {
+  double s = 0.0;
+  for (int m = 0; m < b; ++m) {
+    double term = (double)p / (m + 1);
+    for (int j = 0; j < b; ++j)
+      if (j != m) term *= (p * t - j) / (j + 1);
+    s += term;
+  }
+  return s;
+}
+
+void emit_qp(int D, int p, int form) {
+  const int n = form == 0 ? p + 1 : p;
+  const int NB = form == 0 ? 1 : D;
+  std::vector<double> pts, wts;
+  dogip::simplex_rule(D, n, pts, wts);
+  const int QT = (int)wts.size();
+  auto V = multi(D, p);
+  const int VT = (int)V.size();
+  std::vector<double> B((size_t)NB * QT * VT);
+  for (int j = 0; j < QT; ++j) {
+    double lam[4];
+    lam[0] = 1.0;
+    for (int i = 0; i < D; ++i) {
+      lam[i + 1] = pts[(size_t)j * D + i];
+      lam[0] -= lam[i + 1];
+    }
+    for (int l = 0; l < VT; ++l) {
+      auto be = beta_of(D, p, V[l]);
+      double vals[3];
+      if (form == 0) {
+        double v = 1.0;
+        for (int i = 0; i <= D; ++i) v *= facd(p, be[i], lam[i]);
+        vals[0] = v;
+      } else {
+        double dl[4];
+        for (int i = 0; i <= D; ++i) {
+          double v = dfacd(p, be[i], lam[i]);
+          for (int k = 0; k <= D; ++k)
+            if (k != i) v *= facd(p, be[k], lam[k]);
+          dl[i] = v;
+        }
+        for (int r = 0; r < D; ++r) vals[r] = dl[r + 1] - dl[0];
+      }
+      for (int r = 0; r < NB; ++r) B[((size_t)r * QT + j) * VT + l] = vals[r];
+    }
+  }
+  std::printf("template <> struct TabQ<%d, %d, %d> {\n", D, p, form);
+  std::printf("  static constexpr int D = %d, P = %d, FORM = %d, N1 = %d;\n", D, p, form, n);
+  std::printf("  static constexpr int V = %d, W = %d, NB = %d;\n", VT, QT, NB);
+  std::printf("  static constexpr double B[%d][%d][%d] = {", NB, QT, VT);
   for (size_t i = 0; i < B.size(); ++i) std::printf("%s%.17g", i ? "," : "", B[i]);
-  std::printf("};\n  static constexpr double w[%d] = {", WT);
-  for (int j = 0; j < WT; ++j) std::printf("%s%.17g", j ? "," : "", dbl(w[j]));
-  std::printf("};\n  static constexpr double iv[%d] = {", VT);
-  for (int l = 0; l < VT; ++l) std::printf("%s%.17g", l ? "," : "", dbl(iv[l]));
+  std::printf("};\n  static constexpr double w[%d] = {", QT);
+  for (int j = 0; j < QT; ++j) std::printf("%s%.17g", j ? "," : "", wts[j]);
   std::printf("};\n};\n");
 }
 
 }  // namespace
 
 int main(int argc, char** argv) {
+  if (argc > 1 && std::string(argv[1]) == "--hi") {
+    // --hi pmin2 pmax2 pmin3 pmax3
+    emit_hi(std::atoi(argv[2]), std::atoi(argv[3]), std::atoi(argv[4]), std::atoi(argv[5]));
+    return 0;
+  }
   int pmax2 = argc > 1 ? std::atoi(argv[1]) : 4;
   int pmax3 = argc > 2 ? std::atoi(argv[2]) : 4;
   std::printf("// Generated by gen_tables.cpp at build time.  Do not edit.\n");
   std::printf("#pragma once\nnamespace dogip_tab {\n");
   std::printf("template <int D, int P, int FORM> struct Tab;\n");
+  std::printf("template <int D, int P, int FORM> struct TabQ;\n");
   std::printf("constexpr int PMAX2 = %d, PMAX3 = %d;\n", pmax2, pmax3);
   for (int D = 2; D <= 3; ++D)
     for (int p = 1; p <= (D == 2 ? pmax2 : pmax3); ++p)
-      for (int form = 0; form < 2; ++form) emit(D, p, form);
+      for (int form = 0; form < 2; ++form) {
+        emit(D, p, form);
+        emit_qp(D, p, form);
+      }
   std::printf("}  // namespace dogip_tab\n");
   return 0;
 }

@@ -134,16 +134,19 @@ std::vector<std::vector<int>> local_betas(int d, int p) {
   return out;
 }
 
-// Dof map by first appearance: node identity = multiset {(v_i, beta_i): beta_i > 0}.
-void build_dofmap(Ctx& c, const int32_t* cells) {
-  const int d = c.d, V = c.VT;
-  auto betas = local_betas(d, c.p);
-  c.dofmap.assign((size_t)c.E * V, 0);
-  KeyTable tab((size_t)c.E * V / 2 + 64);
+// Node numbering by first appearance: node identity = multiset {(v_i, beta_i): beta_i > 0}
+// of the order-q nodes; ids[e * V_q + l]; first[...] = 1 where the cell introduces the node.
+int64_t number_nodes(int d, int q, int64_t E, const int32_t* cells, std::vector<int32_t>& ids,
+                     std::vector<uint8_t>* first) {
+  auto betas = local_betas(d, q);
+  const int V = (int)betas.size();
+  ids.assign((size_t)E * V, 0);
+  if (first) first->assign((size_t)E * V, 0);
+  KeyTable tab((size_t)E * V / 2 + 64);
   int32_t next = 0;
   uint64_t key[4];
   std::pair<uint64_t, int> pr[4];
-  for (int64_t e = 0; e < c.E; ++e) {
+  for (int64_t e = 0; e < E; ++e) {
     const int32_t* cv = cells + e * (d + 1);
     for (int l = 0; l < V; ++l) {
       int m = 0;
@@ -154,13 +157,18 @@ void build_dofmap(Ctx& c, const int32_t* cells) {
       bool ins = false;
       const int32_t id = tab.find_or_insert(key, next, &ins);
       if (ins) {
-        if (next == (int32_t)kIdMask) fail(DOGIP_EINVAL, "too many dofs (>= 2^30)");
+        if (next == (int32_t)kIdMask) fail(DOGIP_EINVAL, "too many nodes (>= 2^30)");
         ++next;
+        if (first) (*first)[(size_t)e * V + l] = 1;
       }
-      c.dofmap[(size_t)e * V + l] = id;
+      ids[(size_t)e * V + l] = id;
     }
   }
-  c.n = next;
+  return next;
+}
+
+void build_dofmap(Ctx& c, const int32_t* cells) {
+  c.n = number_nodes(c.d, c.p, c.E, cells, c.dofmap, nullptr);
 }
 
 // Boundary dofs: nodes with beta_i = 0 for a local facet i (opposite vertex i)
@@ -252,7 +260,10 @@ void free_ctx(Ctx* c) {
   for (void* p : {(void*)c->d_coords, (void*)c->d_cells, (void*)c->d_perm, (void*)c->d_conn,
                   (void*)c->d_A64, (void*)c->d_A32, (void*)c->d_geo, (void*)c->d_diag,
                   (void*)c->d_dinv64, (void*)c->d_dinv32, (void*)c->d_bnd, (void*)c->d_coef,
-                  (void*)c->d_err, (void*)c->d_kerr})
+                  (void*)c->d_qp64, (void*)c->d_qp32, (void*)c->d_err, (void*)c->d_kerr,
+                  (void*)c->d_connW, (void*)c->d_Aw64, (void*)c->d_Aw32, (void*)c->d_w64,
+                  (void*)c->d_w32, (void*)c->d_hiB64, (void*)c->d_hiB32, (void*)c->d_hiW,
+                  (void*)c->d_hiIV})
     if (p) cudaFree(p);
   if (c->stream) cudaStreamDestroy(c->stream);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
@@ -273,6 +284,23 @@ struct DeviceGuard {
     if (prev >= 0 && cur != prev) cudaSetDevice(prev);
   }
 };
+
+}  // namespace
+void ensure_w_scratch(Ctx& c, int R) {
+  if (!c.global_w || R <= c.w_cap) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cuda_check(cudaStreamIsCapturing(c.stream, &cs), "capture status");
+  if (cs != cudaStreamCaptureStatusNone) fail(DOGIP_EINVAL, "global double-grid scratch grows during capture");
+  cuda_check(cudaStreamSynchronize(c.stream), "scratch sync");
+  if (c.d_w64) cudaFree(c.d_w64);
+  if (c.d_w32) cudaFree(c.d_w32);
+  c.d_w64 = nullptr;
+  c.d_w32 = nullptr;
+  c.d_w64 = dev_alloc<double>((size_t)c.nW * R);
+  c.d_w32 = dev_alloc<float>((size_t)c.nW * R);
+  c.w_cap = R;
+}
+namespace {
 
 void check_coef_status(Ctx& c, cudaStream_t s) {
   int err = 0;
@@ -307,7 +335,7 @@ Ctx* setup(const dogip_mesh* m, int p, int form, int coef_kind, const double* co
   int NB, W, V;
   long long nnz, nnz1;
   if (!table_info(m->dim, p, form, &NB, &W, &V, &nnz, &nnz1))
-    fail(DOGIP_EUNSUPPORTED, "p outside the compiled range (1..4)");
+    fail(DOGIP_EUNSUPPORTED, "p outside the built range (2D 1..8, 3D 1..4)");
   const int d = m->dim;
   for (int64_t k = 0; k < m->n_cells * (d + 1); ++k)
     if (m->cells[k] < 0 || m->cells[k] >= m->n_vertices)
@@ -338,11 +366,21 @@ Ctx* setup(const dogip_mesh* m, int p, int form, int coef_kind, const double* co
     c->factorized = o.factorized != 0;
     if (c->factorized && c->scatter == DOGIP_SCATTER_COLOUR)
       fail(DOGIP_EINVAL, "factorized storage needs atomic scatter");
+    c->hi = !table_is_compiled(d, p, form);
+    if (c->hi && c->factorized) fail(DOGIP_EUNSUPPORTED, "factorized storage is built for p <= 4 (3D: 3)");
+    c->global_w = o.global_w != 0;
+    if (c->hi && c->global_w) fail(DOGIP_EUNSUPPORTED, "the global double grid is built for p <= 4 (3D: 3)");
+    if (c->global_w) {
+      if (form != DOGIP_PROJECTION) fail(DOGIP_EINVAL, "the global double grid is for the projection");
+      if (c->factorized || c->scatter == DOGIP_SCATTER_COLOUR || c->dirichlet)
+        fail(DOGIP_EINVAL, "the global double grid needs factorized = 0, atomic scatter, no Dirichlet rows");
+    }
     c->E = m->n_cells;
     c->Epad = (c->E + kTile - 1) / kTile * kTile;
     c->nv = m->n_vertices;
 
     build_dofmap(*c, m->cells);
+    if (c->global_w) c->nW = number_nodes(d, 2 * p, c->E, m->cells, c->wdofmap, &c->wowner);
     build_boundary(*c, m->cells);
     build_colouring(*c, m->cells);
 
@@ -384,15 +422,29 @@ Ctx* setup(const dogip_mesh* m, int p, int form, int coef_kind, const double* co
     c->d_cells = dev_alloc<int32_t>(pcells.size());
     c->d_perm = dev_alloc<int64_t>(c->E);
     c->d_conn = dev_alloc<uint32_t>(conn.size());
-    const size_t nA = (size_t)c->Epad * (c->factorized ? 1 : W) * c->NS;
-    c->d_A64 = dev_alloc<double>(nA);
-    if (c->keep32) c->d_A32 = dev_alloc<float>(nA);
+    const size_t nA = c->global_w ? 0 : (size_t)c->Epad * (c->factorized ? 1 : W) * c->NS;
+    if (nA) c->d_A64 = dev_alloc<double>(nA);
+    if (nA && c->keep32) c->d_A32 = dev_alloc<float>(nA);
+    std::vector<uint32_t> connW;
+    if (c->global_w) {
+      connW.assign((size_t)c->Epad * W, 0u);
+      for (int64_t e = 0; e < c->E; ++e)  // processing order = caller order (atomic scatter)
+        for (int j = 0; j < W; ++j)
+          connW[(size_t)(e / kTile) * W * kTile + (size_t)j * kTile + e % kTile] =
+              (uint32_t)c->wdofmap[(size_t)e * W + j] | (c->wowner[(size_t)e * W + j] ? kBndBit : 0u);
+      c->d_connW = dev_alloc<uint32_t>(connW.size());
+      c->d_Aw64 = dev_alloc<double>(c->nW);
+      if (c->keep32) c->d_Aw32 = dev_alloc<float>(c->nW);
+      ensure_w_scratch(*c, 1);
+    }
     c->d_geo = dev_alloc<double>((size_t)c->E * (d * d + 1));
     c->d_diag = dev_alloc<double>(c->n);
     c->d_dinv64 = dev_alloc<double>(c->n);
     c->d_dinv32 = dev_alloc<float>(c->n);
     c->d_bnd = dev_alloc<int32_t>(bnd.size());
     c->d_coef = dev_alloc<double>(ncoef);
+    c->d_qp64 = dev_alloc<double>((size_t)c->E * c->NS);
+    if (c->keep32) c->d_qp32 = dev_alloc<float>((size_t)c->E * c->NS);
     c->d_err = dev_alloc<int>(1);
     c->d_kerr = dev_alloc<int>(1);
     if (const char* v = std::getenv("DOGIP_APPLY_VARIANT")) c->apply_variant = std::atoi(v);
@@ -416,12 +468,35 @@ Ctx* setup(const dogip_mesh* m, int p, int form, int coef_kind, const double* co
     cuda_check(cudaMemcpyAsync(c->d_coef, coef, sizeof(double) * ncoef, cudaMemcpyHostToDevice, s),
                "upload coefficients");
     // padding of A_T stays zero
-    cuda_check(cudaMemsetAsync(c->d_A64, 0, sizeof(double) * nA, s), "memset A");
-    if (c->keep32) cuda_check(cudaMemsetAsync(c->d_A32, 0, sizeof(float) * nA, s), "memset A32");
+    if (nA) cuda_check(cudaMemsetAsync(c->d_A64, 0, sizeof(double) * nA, s), "memset A");
+    if (nA && c->keep32) cuda_check(cudaMemsetAsync(c->d_A32, 0, sizeof(float) * nA, s), "memset A32");
+    if (c->global_w)
+      cuda_check(cudaMemcpyAsync(c->d_connW, connW.data(), sizeof(uint32_t) * connW.size(),
+                                 cudaMemcpyHostToDevice, s), "upload W nodes");
+    std::vector<float> hiB32;
+    if (c->hi) {  // run-time reference tables of the higher orders
+      const double *hB, *hw, *hiv;
+      hi_table(d, p, form, nullptr, nullptr, nullptr, nullptr, nullptr, &hB, &hw, &hiv);
+      const size_t nb = (size_t)NB * W * V;
+      c->d_hiB64 = dev_alloc<double>(nb);
+      c->d_hiB32 = dev_alloc<float>(nb);
+      c->d_hiW = dev_alloc<double>(W);
+      c->d_hiIV = dev_alloc<double>(V);
+      hiB32.assign(hB, hB + nb);
+      cuda_check(cudaMemcpyAsync(c->d_hiB64, hB, sizeof(double) * nb, cudaMemcpyHostToDevice, s),
+                 "upload tables");
+      cuda_check(cudaMemcpyAsync(c->d_hiB32, hiB32.data(), sizeof(float) * nb,
+                                 cudaMemcpyHostToDevice, s), "upload tables");
+      cuda_check(cudaMemcpyAsync(c->d_hiW, hw, sizeof(double) * W, cudaMemcpyHostToDevice, s),
+                 "upload tables");
+      cuda_check(cudaMemcpyAsync(c->d_hiIV, hiv, sizeof(double) * V, cudaMemcpyHostToDevice, s),
+                 "upload tables");
+    }
     cuda_check(cudaMemsetAsync(c->d_err, 0, sizeof(int), s), "memset err");
     cuda_check(cudaMemsetAsync(c->d_kerr, 0, sizeof(int), s), "memset kernel err");
     launch_ahat(*c, c->d_coef, coef_kind, s);
     check_coef_status(*c, s);
+    c->qp_ok = !c->hi;
     prepare_apply(*c);
   } catch (...) {
     free_ctx(c);
@@ -441,6 +516,7 @@ void set_coef(Ctx& c, int coef_kind, const double* coef, cudaStream_t s) {
   cuda_check(cudaMemsetAsync(c.d_err, 0, sizeof(int), s), "memset err");
   launch_ahat(c, coef, coef_kind, s);
   check_coef_status(c, s);
+  c.qp_ok = !c.hi;
 }
 
 
@@ -469,6 +545,8 @@ void w_basis_at(int d, int q, const double* x, std::vector<double>& out) {
 void set_coef_inclusions(Ctx& c, int nb, const double* centres, const double* radii, double inside,
                          double outside, int nq, cudaStream_t s) {
   if (c.factorized) fail(DOGIP_EINVAL, "sub-element integration needs per-node storage (factorized = 0)");
+  if (c.global_w) fail(DOGIP_EUNSUPPORTED, "sub-element integration is not built for the global double grid");
+  if (c.hi) fail(DOGIP_EUNSUPPORTED, "sub-element integration is built for p <= 4 (3D: 3)");
   if (nb < 0 || (nb > 0 && (!centres || !radii))) fail(DOGIP_EINVAL, "inclusion arrays required");
   if (nq < 1 || nq > 16) fail(DOGIP_EINVAL, "points per direction must be in 1..16");
   if (!(inside > 0.0) || !(outside > 0.0) || !std::isfinite(inside) || !std::isfinite(outside))
@@ -479,6 +557,7 @@ void set_coef_inclusions(Ctx& c, int nb, const double* centres, const double* ra
       if (!std::isfinite(centres[b * c.d + k])) fail(DOGIP_EINVAL, "non-finite inclusion centre");
   }
   DeviceGuard guard(c.device);
+  c.qp_ok = false;  // the comparator's per-cell coefficient no longer describes the field
   std::vector<double> pts, wts;
   simplex_rule(c.d, nq, pts, wts);
   const int q = c.form == DOGIP_PROJECTION ? 2 * c.p : 2 * c.p - 2;
@@ -623,6 +702,7 @@ int solve(Ctx& c, const double* b, double* u, int R, const dogip_solve_opts* opt
     fail(DOGIP_EINVAL, "colour scatter needs a context set up with scatter = COLOUR");
   const int chunk = std::max(1, o.check_every);
   DeviceGuard guard(c.device);
+  ensure_w_scratch(c, R);
   vec_alloc(c.work, c.n, R);
   SolveWork& w = c.work;
   cudaStream_t s = c.stream;
@@ -838,7 +918,10 @@ int batch_solve(Ctx* const* ctxs, int np, const double* const* b, double* const*
       if (cs[j] == cs[i]) fail(DOGIP_EINVAL, "a context appears twice in the batch");
   }
   DeviceGuard guard(dev);
-  for (Ctx* c : cs) vec_alloc(c->work, c->n, 1);
+  for (Ctx* c : cs) {
+    ensure_w_scratch(*c, 1);
+    vec_alloc(c->work, c->n, 1);
+  }
   cudaStream_t main = nullptr;
   cuda_check(cudaStreamCreateWithFlags(&main, cudaStreamNonBlocking), "batch stream");
   cudaEvent_t ev = nullptr;
@@ -1034,7 +1117,7 @@ void tune_store_locked(const TuneKey& k, const TuneChoice& ch) {
 
 int autotune(Ctx& c, int force, cudaStream_t s) {
   DeviceGuard guard(c.device);
-  if (c.factorized) return 0;  // one kernel only
+  if (c.factorized || c.global_w || c.hi) return 0;  // one kernel only
   int logE = 0;
   while ((int64_t(1) << logE) < c.E) ++logE;
   int tuned = 0;
@@ -1143,6 +1226,7 @@ int dogip_opts_default(dogip_opts* o) {
   o->keep_fp32 = 1;
   o->device = -1;
   o->factorized = 0;
+  o->global_w = 0;
   return DOGIP_OK;
 }
 
@@ -1201,9 +1285,10 @@ int dogip_get_info(const dogip_ctx* c, dogip_info* i) {
     i->nnz_b = c->nnzb;
     i->nnz_pm1_b = c->nnzb1;
     const int64_t per = (int64_t)(c->factorized ? 1 : c->WT) * c->NS;
-    i->bytes_ahat_fp64 = (int64_t)c->E * per * 8;
-    i->bytes_ahat_fp32 = (int64_t)c->E * per * 4;
-    i->bytes_conn = (int64_t)c->E * c->VT * 4;
+    i->bytes_ahat_fp64 = c->global_w ? c->nW * 8 : (int64_t)c->E * per * 8;
+    i->bytes_ahat_fp32 = c->global_w ? c->nW * 4 : (int64_t)c->E * per * 4;
+    i->bytes_conn = (int64_t)c->E * (c->VT + (c->global_w ? c->WT : 0)) * 4;
+    i->n_wglobal = c->global_w ? c->nW : 0;
     i->kernel_launches = c->launches;
     return DOGIP_OK;
   });
@@ -1239,8 +1324,31 @@ int dogip_get_boundary(const dogip_ctx* c, uint8_t* out) {
 int dogip_get_ahat(const dogip_ctx* c, double* out, void* stream) {
   return guarded([&] {
     if (!c || !out) fail(DOGIP_EINVAL, "ctx and output are required");
+    if (c->global_w) fail(DOGIP_EINVAL, "global double grid: use dogip_get_ahat_global");
     dogip::DeviceGuard g(c->device);
     dogip::launch_export_ahat(*c, out, (cudaStream_t)stream);
+    return DOGIP_OK;
+  });
+}
+
+int dogip_get_ahat_global(const dogip_ctx* c, double* out, void* stream) {
+  return guarded([&] {
+    if (!c || !out) fail(DOGIP_EINVAL, "ctx and output are required");
+    if (!c->global_w) fail(DOGIP_EINVAL, "context has no global double grid");
+    dogip::DeviceGuard g(c->device);
+    dogip::cuda_check(cudaMemcpyAsync(out, c->d_Aw64, sizeof(double) * c->nW,
+                                      cudaMemcpyDeviceToDevice, (cudaStream_t)stream),
+                      "copy A_diag");
+    return DOGIP_OK;
+  });
+}
+
+int dogip_get_wdofmap(const dogip_ctx* c, int32_t* ids, uint8_t* owner) {
+  return guarded([&] {
+    if (!c) fail(DOGIP_EINVAL, "ctx is required");
+    if (!c->global_w) fail(DOGIP_EINVAL, "context has no global double grid");
+    if (ids) std::memcpy(ids, c->wdofmap.data(), sizeof(int32_t) * c->wdofmap.size());
+    if (owner) std::memcpy(owner, c->wowner.data(), c->wowner.size());
     return DOGIP_OK;
   });
 }
@@ -1302,7 +1410,23 @@ int dogip_apply(dogip_ctx* c, const void* u, void* y, int nrhs, int prec, int sc
     if (scatter == DOGIP_SCATTER_COLOUR && c->scatter != DOGIP_SCATTER_COLOUR)
       fail(DOGIP_EINVAL, "colour scatter needs a context set up with scatter = COLOUR");
     dogip::DeviceGuard g(c->device);
+    dogip::ensure_w_scratch(*c, nrhs);
     dogip::launch_apply(*c, u, y, nrhs, prec, scatter, (cudaStream_t)stream, nullptr);
+    return DOGIP_OK;
+  });
+}
+
+int dogip_apply_qp(dogip_ctx* c, const void* u, void* y, int nrhs, int prec, void* stream) {
+  return guarded([&] {
+    if (!c || !u || !y) fail(DOGIP_EINVAL, "ctx, u and y are required");
+    if (nrhs < 1) fail(DOGIP_EINVAL, "nrhs must be >= 1");
+    if (prec != DOGIP_FP64 && prec != DOGIP_FP32) fail(DOGIP_EINVAL, "unknown precision");
+    if (prec == DOGIP_FP32 && !c->keep32) fail(DOGIP_EINVAL, "context has no FP32 copy");
+    if (!c->qp_ok)
+      fail(DOGIP_EUNSUPPORTED,
+           "the quadrature-point apply needs element-constant coefficients (not sub-element)");
+    dogip::DeviceGuard g(c->device);
+    dogip::launch_apply_qp(*c, u, y, nrhs, prec, (cudaStream_t)stream);
     return DOGIP_OK;
   });
 }

@@ -88,6 +88,26 @@ struct dogip_ctx {
   float* d_dinv32 = nullptr;   // [n]
   int32_t* d_bnd = nullptr;    // [nbnd] boundary dof list
   double* d_coef = nullptr;    // caller order copy of the setup coefficients
+  double* d_qp64 = nullptr;    // [E][NS] processing order: coefficient stream of the
+  float* d_qp32 = nullptr;     //   quadrature-point comparator (dogip_apply_qp)
+  bool qp_ok = false;          // element-constant coefficients are set (not sub-element)
+  // orders above the compiled tables (2D p 5..8, 3D p 4): run-time tables
+  bool hi = false;
+  double* d_hiB64 = nullptr;  // [NB][W][V]
+  float* d_hiB32 = nullptr;
+  double* d_hiW = nullptr;    // [W]
+  double* d_hiIV = nullptr;   // [V]
+  // global double grid for the weighted projection (dogip_opts.global_w)
+  bool global_w = false;
+  int64_t nW = 0;                   // W nodes (continuous P_2p space)
+  std::vector<int32_t> wdofmap;     // [E x W_T] caller order
+  std::vector<uint8_t> wowner;      // [E x W_T] 1 where the cell owns the node
+  uint32_t* d_connW = nullptr;      // AoSoA [Epad/32][W_T][32], bit 31 = owner
+  double* d_Aw64 = nullptr;         // A_diag [nW]
+  float* d_Aw32 = nullptr;
+  double* d_w64 = nullptr;          // scratch [nW x w_cap]
+  float* d_w32 = nullptr;
+  int w_cap = 0;
   int* d_err = nullptr;        // validation flags
   int* d_kerr = nullptr;       // kernel wait timeouts (bounded mbarrier waits)
   int apply_variant = 1;       // 1: bulk-async staged apply; 0: one thread per cell
@@ -142,6 +162,24 @@ void launch_load(Ctx& c, const double* f, double* b, cudaStream_t s);
 void launch_grad(Ctx& c, const double* u, const double* lam, double* dA,
                  cudaStream_t s);
 void launch_export_ahat(const Ctx& c, double* out, cudaStream_t s);
+// Run-time-table kernels of the higher orders (apply_hi.cu).
+struct AhatArgs;
+struct LoadArgs;
+int apply_hi(const Ctx& c, const void* u, void* y, int R, int prec, bool atomic, int64_t e0,
+             int64_t e1, cudaStream_t s, const int* skip);
+bool ahat_hi(const Ctx& c, AhatArgs& a, cudaStream_t s);
+bool load_hi(const Ctx& c, LoadArgs& a, cudaStream_t s);
+bool hi_table(int d, int p, int form, int* NB, int* W, int* V, long long* nnz, long long* nnz1,
+              const double** B, const double** w, const double** iv);
+bool table_is_compiled(int d, int p, int form);
+// Global double-grid apply of the weighted projection (two kernels); false when no
+// instance exists.  The scratch must hold R right-hand sides (ensure_w_scratch).
+bool apply_gw(const Ctx& c, const void* u, void* y, int R, int prec, cudaStream_t s,
+              const int* skip);
+void ensure_w_scratch(Ctx& c, int R);
+void narrow_copy(const double* a, float* b, int64_t n, cudaStream_t s);
+// Quadrature-point matrix-free apply (comparator): y = K~ u, atomic scatter.
+void launch_apply_qp(Ctx& c, const void* u, void* y, int R, int prec, cudaStream_t s);
 void launch_dirichlet_copy(const Ctx& c, const void* u, void* y, int R, int prec,
                            cudaStream_t s, const int* skip);
 void launch_diag_finish(Ctx& c, cudaStream_t s);

@@ -201,7 +201,10 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> a) {
 // S-stage ring.  A producer warp refills a stage as soon as every consumer warp has
 // released it (per-stage full/empty mbarriers), so the TPC consumer warps run
 // decoupled, one warp per tile (one thread per cell), looping over the right-hand
-// sides and reusing A_T from shared memory.  The u gathers and the atomic
+// sides and reusing A_T from shared memory.  A stage carries the A_T tiles of its
+// chunk and the conn tiles of the CTA's next chunk (the first chunk's conn comes in a
+// separate prologue copy), so each warp issues the u gathers of its next unit of
+// work before the arithmetic of the current one.  The gathers and the atomic
 // scatter go to L2; the Dirichlet rows y_b = u_b are written at the end.  Every wait
 // is bounded by a clock budget; on expiry the kernel raises an error flag, drains its
 // copies in flight (bounded again) and returns.
@@ -265,16 +268,21 @@ struct TmaCfg {
   static constexpr int V = TB::V, W = TB::W, NS = NSym<D, FORM>::value;
   static constexpr uint32_t A_TILE = (FACT ? 1 : W) * NS * kTile * sizeof(T);
   static constexpr uint32_t C_TILE = V * kTile * 4;
-  static constexpr uint32_t kBudget = 200 * 1024;  // shared memory for the ring
-  static constexpr int TPC = (2 * 8 * (A_TILE + C_TILE) <= kBudget) ? 8 : 4;  // warps per CTA
+  // shared memory for the ring plus the prologue (227 KB per CTA at most)
+  static constexpr uint32_t kBudget = 224 * 1024;
+  // consumer warps per CTA: the largest of 8, 4, 2 that leaves a double-buffered ring
+  static constexpr uint32_t need(int tpc) { return tpc * (2 * (A_TILE + C_TILE) + C_TILE); }
+  static constexpr int TPC = need(8) <= kBudget ? 8 : (need(4) <= kBudget ? 4 : 2);
+  // a stage holds the Â tiles of chunk k and the conn tiles of the CTA's next chunk
   static constexpr uint32_t CHUNK = TPC * (A_TILE + C_TILE);
-  static constexpr int S0 = (int)(kBudget / CHUNK);
+  static constexpr uint32_t PRO = TPC * C_TILE;  // conn of the CTA's first chunk
+  static constexpr int S0 = (int)((kBudget - PRO) / CHUNK);
   static constexpr int S = S0 > 4 ? 4 : (S0 < 2 ? 2 : S0);  // pipeline stages
-  static constexpr uint32_t SMEM = S * CHUNK + 2 * S * 8 + 128;  // ring + full/empty bars
+  static constexpr uint32_t SMEM = S * CHUNK + PRO + (2 * S + 1) * 8 + 128;  // + bars, align
   static constexpr int THREADS = (TPC + 1) * 32;  // TPC consumer warps + 1 producer warp
-  // Instances whose double-buffered 4-warp ring does not fit (3D P3 FP64) use the
+  // Instances whose double-buffered 2-warp ring does not fit (3D P3 FP64) use the
   // one-thread-per-cell kernel instead.
-  static constexpr bool OK = 2 * CHUNK <= kBudget;
+  static constexpr bool OK = need(TPC) <= kBudget;
 };
 
 template <typename T>
@@ -300,29 +308,43 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T, FACT>::THREADS)
   static_assert(C::OK, "stage does not fit in shared memory");
   using TB = typename C::TB;
   constexpr int V = C::V, W = C::W, NB = TB::NB, NS = C::NS;
+  // prefetch the next unit's gathers where the extra V live values fit the registers
+  constexpr bool PF = sizeof(T) * V <= 64;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base =
       (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
-  uint64_t* full = (uint64_t*)(base + C::S * C::CHUNK);  // chunk landed (tx count)
-  uint64_t* empty = full + C::S;                          // all consumer warps done with it
+  unsigned char* pro_buf = base + C::S * C::CHUNK;           // conn of the first chunk
+  uint64_t* full = (uint64_t*)(pro_buf + C::PRO);            // chunk landed (tx count)
+  uint64_t* empty = full + C::S;                             // all consumer warps done with it
+  uint64_t* pro = empty + C::S;                              // prologue landed
   if (a.skip != nullptr && *a.skip) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t G = gridDim.x;
+  const int64_t G = gridDim.x, k0 = blockIdx.x;
   if (tid == 0) {
     for (int s = 0; s < C::S; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], C::TPC);
     }
+    mbar_init(pro, 1);
     mbar_fence_init();
   }
   __syncthreads();
   if (warp == C::TPC) {
-    // ---- producer warp: keep the ring full
+    // ---- producer warp: keep the ring full.  Stage s of chunk k receives the Â
+    // tiles of k and the conn tiles of k + G (this CTA's next chunk), so that the
+    // consumers can start the next chunk's gathers before they compute chunk k.
     if (lane == 0) {
       int failed = 0;
       int64_t issued = 0;  // chunks whose copies were issued
+      const bool pro_issued = k0 < a.nchunks;
+      if (pro_issued) {
+        const int nt0 = (int)min((int64_t)C::TPC, a.ntiles - k0 * C::TPC);
+        mbar_expect_tx(pro, (uint32_t)nt0 * C::C_TILE);
+        bulk_copy_g2s(pro_buf, (const unsigned char*)a.conn + k0 * C::TPC * C::C_TILE,
+                      (uint32_t)nt0 * C::C_TILE, pro);
+      }
       for (int64_t i = 0;; ++i) {
-        const int64_t k = blockIdx.x + i * G;
+        const int64_t k = k0 + i * G;
         if (k >= a.nchunks) break;
         const int s = (int)(i % C::S);
         if (i >= C::S &&
@@ -333,46 +355,62 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T, FACT>::THREADS)
         fence_proxy_async_smem();
         issued = i + 1;
         if (k == a.test_skip_chunk) continue;  // test hook: this chunk never lands
-        const int64_t t0 = k * C::TPC;
+        const int64_t t0 = k * C::TPC, kn = k + G;
         const int nt = (int)min((int64_t)C::TPC, a.ntiles - t0);
+        const int ntn = kn < a.nchunks ? (int)min((int64_t)C::TPC, a.ntiles - kn * C::TPC) : 0;
         unsigned char* sa = base + (size_t)s * C::CHUNK;
         unsigned char* sc = sa + C::TPC * C::A_TILE;
-        mbar_expect_tx(&full[s], (uint32_t)nt * (C::A_TILE + C::C_TILE));
+        mbar_expect_tx(&full[s], (uint32_t)nt * C::A_TILE + (uint32_t)ntn * C::C_TILE);
         bulk_copy_g2s(sa, (const unsigned char*)a.A + t0 * C::A_TILE, (uint32_t)nt * C::A_TILE,
                       &full[s]);
-        bulk_copy_g2s(sc, (const unsigned char*)a.conn + t0 * C::C_TILE,
-                      (uint32_t)nt * C::C_TILE, &full[s]);
+        if (ntn > 0)
+          bulk_copy_g2s(sc, (const unsigned char*)a.conn + kn * C::TPC * C::C_TILE,
+                        (uint32_t)ntn * C::C_TILE, &full[s]);
       }
       // drain: wait (bounded) until the last copies issued have landed
+      if (pro_issued) mbar_wait_bounded(pro, 0u, a.wait_budget);
       for (int64_t q = issued - C::S; q < issued; ++q) {
         if (q < 0) continue;
-        if (blockIdx.x + q * G == a.test_skip_chunk) continue;
+        if (k0 + q * G == a.test_skip_chunk) continue;
         mbar_wait_bounded(&full[q % C::S], (uint32_t)((q / C::S) & 1), a.wait_budget);
       }
       if (failed) atomicOr(a.err, 1);
     }
   } else {
-    // ---- consumer warps: warp w computes tile w of every chunk
+    // ---- consumer warps: warp w computes tile w of every chunk.  A unit of work
+    // is (chunk, rhs); the u gathers of the next unit are issued before the
+    // arithmetic of the current one, so their latency hides behind it.
     int failed = 0;
-    for (int64_t i = 0;; ++i) {
-      const int64_t k = blockIdx.x + i * G;
+    uint32_t c[V], cn[V];
+    T ul[V];
+    bool active = false;
+    if (k0 < a.nchunks) {
+      failed = __any_sync(0xffffffffu, mbar_wait_bounded(pro, 0u, a.wait_budget) ? 0 : 1);
+      if (!failed) {
+        const int64_t tile = k0 * C::TPC + warp;
+        active = tile < a.ntiles && tile * kTile + lane < a.E;
+        const uint32_t* sC = (const uint32_t*)(pro_buf + warp * C::C_TILE) + lane;
+        static_for<V>([&](auto lc) {
+          constexpr int l = decltype(lc)::value;
+          c[l] = active ? sC[l * kTile] : kBndBit;
+          if constexpr (PF)
+            ul[l] = (c[l] & kBndBit) ? T(0) : __ldg(a.u + (int64_t)(c[l] & kIdMask) * a.R);
+        });
+      }
+    }
+    for (int64_t i = 0; !failed; ++i) {
+      const int64_t k = k0 + i * G;
       if (k >= a.nchunks) break;
       const int s = (int)(i % C::S);
       const uint32_t parity = (uint32_t)((i / C::S) & 1);
       failed = __any_sync(0xffffffffu, mbar_wait_bounded(&full[s], parity, a.wait_budget) ? 0 : 1);
       if (failed) break;
-      const int64_t tile = k * C::TPC + warp;
-      const int64_t e = tile * kTile + lane;
-      const bool active = tile < a.ntiles && e < a.E;
       const T* sA = (const T*)(base + (size_t)s * C::CHUNK + warp * C::A_TILE) + lane;
-      const uint32_t* sC =
+      const uint32_t* sCn =
           (const uint32_t*)(base + (size_t)s * C::CHUNK + C::TPC * C::A_TILE + warp * C::C_TILE) +
           lane;
-      uint32_t c[V];
-      static_for<V>([&](auto lc) {
-        constexpr int l = decltype(lc)::value;
-        c[l] = active ? sC[l * kTile] : kBndBit;
-      });
+      const int64_t kn = k + G, tile_n = kn * C::TPC + warp;
+      const bool active_n = kn < a.nchunks && tile_n < a.ntiles && tile_n * kTile + lane < a.E;
       T kf[NS];  // factorised K_T (FACT only)
       if constexpr (FACT) {
         static_for<NS>([&](auto kc) {
@@ -381,11 +419,34 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T, FACT>::THREADS)
         });
       }
       for (int r = 0; r < a.R; ++r) {
-        if (active) {
-          T ul[V], Y[V];
+        // next unit: (this chunk, r + 1) or (next chunk, rhs 0)
+        T un[V];
+        if (r + 1 < a.R) {
+          if constexpr (PF) {
+            static_for<V>([&](auto lc) {
+              constexpr int l = decltype(lc)::value;
+              un[l] = (c[l] & kBndBit) ? T(0)
+                                       : __ldg(a.u + (int64_t)(c[l] & kIdMask) * a.R + (r + 1));
+            });
+          }
+        } else {
+          static_for<V>([&](auto lc) {
+            constexpr int l = decltype(lc)::value;
+            cn[l] = active_n ? sCn[l * kTile] : kBndBit;
+            if constexpr (PF)
+              un[l] = (cn[l] & kBndBit) ? T(0) : __ldg(a.u + (int64_t)(cn[l] & kIdMask) * a.R);
+          });
+        }
+        if constexpr (!PF) {  // gathers of this unit (no prefetch: register budget)
           static_for<V>([&](auto lc) {
             constexpr int l = decltype(lc)::value;
             ul[l] = (c[l] & kBndBit) ? T(0) : __ldg(a.u + (int64_t)(c[l] & kIdMask) * a.R + r);
+          });
+        }
+        if (active) {
+          T Y[V];
+          static_for<V>([&](auto lc) {
+            constexpr int l = decltype(lc)::value;
             if constexpr (col_empty<TB>(l)) Y[l] = T(0);
           });
           static_for<W>([&](auto jc) {
@@ -409,7 +470,18 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T, FACT>::THREADS)
             if (!(c[l] & kBndBit)) atomicAdd(a.y + (int64_t)(c[l] & kIdMask) * a.R + r, Y[l]);
           });
         }
+        if constexpr (PF) {
+          static_for<V>([&](auto lc) {
+            constexpr int l = decltype(lc)::value;
+            ul[l] = un[l];
+          });
+        }
       }
+      static_for<V>([&](auto lc) {
+        constexpr int l = decltype(lc)::value;
+        c[l] = cn[l];
+      });
+      active = active_n;
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);  // this warp no longer reads stage s
     }
@@ -440,24 +512,28 @@ struct AhatArgs {
   double* diag;           // [n], accumulated (must be zeroed)
   int* err;
   int64_t E;
+  double* qp64 = nullptr;  // [E][n_sym] processing order: the cell's coefficient (packed
+  float* qp32 = nullptr;   // symmetric part; the scalar for the projection), may be null
+  const uint32_t* connW = nullptr;  // global-W projection: AoSoA [Epad/32][W_T][32] W-node ids
+  double* aw = nullptr;             // global-W projection: A_diag [n_W], accumulated (zeroed)
 };
 
-template <int D>
-__device__ __forceinline__ double det_inv(const double (&R)[D][D], double (&Ri)[D][D]) {
+template <int D, typename F = double>
+__device__ __forceinline__ F det_inv(const F (&R)[D][D], F (&Ri)[D][D]) {
   if constexpr (D == 2) {
-    const double det = R[0][0] * R[1][1] - R[0][1] * R[1][0];
-    const double id = 1.0 / det;
+    const F det = R[0][0] * R[1][1] - R[0][1] * R[1][0];
+    const F id = F(1) / det;
     Ri[0][0] = R[1][1] * id;
     Ri[0][1] = -R[0][1] * id;
     Ri[1][0] = -R[1][0] * id;
     Ri[1][1] = R[0][0] * id;
     return det;
   } else {
-    const double c00 = R[1][1] * R[2][2] - R[1][2] * R[2][1];
-    const double c01 = R[1][2] * R[2][0] - R[1][0] * R[2][2];
-    const double c02 = R[1][0] * R[2][1] - R[1][1] * R[2][0];
-    const double det = R[0][0] * c00 + R[0][1] * c01 + R[0][2] * c02;
-    const double id = 1.0 / det;
+    const F c00 = R[1][1] * R[2][2] - R[1][2] * R[2][1];
+    const F c01 = R[1][2] * R[2][0] - R[1][0] * R[2][2];
+    const F c02 = R[1][0] * R[2][1] - R[1][1] * R[2][0];
+    const F det = R[0][0] * c00 + R[0][1] * c01 + R[0][2] * c02;
+    const F id = F(1) / det;
     Ri[0][0] = c00 * id;
     Ri[1][0] = c01 * id;
     Ri[2][0] = c02 * id;
@@ -471,15 +547,15 @@ __device__ __forceinline__ double det_inv(const double (&R)[D][D], double (&Ri)[
   }
 }
 
-// Step a8: A_T,j = |det R_T| w_j R_T^-1 M_T R_T^-T (elliptic) or m_T |det R_T| w_j
-// (projection), written in FP64 (and FP32), plus the element geometry and the
-// Jacobi diagonal sum_j B_{.jl}^T A_T,j B_{.jl} scattered into diag.
-template <int D, int P, int FORM>
-__global__ void __launch_bounds__(128) k_ahat(AhatArgs a) {
-  using TB = dogip_tab::Tab<D, P, FORM>;
-  constexpr int V = TB::V, W = TB::W, NB = TB::NB, NS = NSym<D, FORM>::value;
-  const int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (pos >= a.E) return;
+// Per-cell factor of Theorems 4 and 8: geometry (R_T^-1, |det R_T|), the validated
+// coefficient and K_T = |det R_T| R_T^-1 M_T R_T^-T (packed) or m_T |det R_T|; also
+// writes the cell's entry of the quadrature-point comparator's coefficient stream.
+// Returns the validation flags.
+template <int D, int FORM>
+__device__ __forceinline__ int cell_factor(const AhatArgs& a, int64_t pos,
+                                           double (&K)[NSym<D, FORM>::value],
+                                           double (&Ri)[D][D], double& vol) {
+  constexpr int NS = NSym<D, FORM>::value;
   double X[D + 1][D];
   static_for<D + 1>([&](auto ic) {
     constexpr int i = decltype(ic)::value;
@@ -489,7 +565,7 @@ __global__ void __launch_bounds__(128) k_ahat(AhatArgs a) {
       X[i][k] = a.coords[v * D + k];
     });
   });
-  double R[D][D], Ri[D][D];
+  double R[D][D];
   static_for<D>([&](auto ic) {
     constexpr int i = decltype(ic)::value;
     static_for<D>([&](auto kc) {
@@ -498,16 +574,19 @@ __global__ void __launch_bounds__(128) k_ahat(AhatArgs a) {
     });
   });
   const double det = det_inv<D>(R, Ri);
-  const double vol = fabs(det);
+  vol = fabs(det);
   int err = 0;
   if (!(vol > 0.0) || !isfinite(det)) err |= kErrGeometry;
   const int64_t user = a.perm[pos];
-  double K[NS];
   if constexpr (FORM == DOGIP_PROJECTION) {
     const double m = a.coef[user];
     if (!isfinite(m)) err |= kErrNonFinite;
     if (!(m > 0.0)) err |= kErrNotPos;
     K[0] = m * vol;
+    if (a.qp64 != nullptr) {
+      a.qp64[pos] = m;
+      if (a.qp32) a.qp32[pos] = (float)m;
+    }
   } else {
     double M[D][D];
     if (a.coef_kind == DOGIP_COEF_ELEM_SCALAR) {
@@ -551,6 +630,19 @@ __global__ void __launch_bounds__(128) k_ahat(AhatArgs a) {
         if (!(m3 > 0.0)) err |= kErrNotPos;
       }
     }
+    if (a.qp64 != nullptr) {  // coefficient stream of the quadrature-point comparator
+      static_for<D>([&](auto rc) {
+        constexpr int r = decltype(rc)::value;
+        static_for<D>([&](auto sc) {
+          constexpr int s = decltype(sc)::value;
+          if constexpr (r <= s) {
+            const double v = 0.5 * (M[r][s] + M[s][r]);
+            a.qp64[pos * NS + sym_idx(D, r, s)] = v;
+            if (a.qp32) a.qp32[pos * NS + sym_idx(D, r, s)] = (float)v;
+          }
+        });
+      });
+    }
     // K = vol * R^-1 M R^-T, symmetric part, packed
     static_for<D>([&](auto rc) {
       constexpr int r = decltype(rc)::value;
@@ -570,10 +662,32 @@ __global__ void __launch_bounds__(128) k_ahat(AhatArgs a) {
       });
     });
   }
+  return err;
+}
+
+// Step a8: A_T,j = |det R_T| w_j R_T^-1 M_T R_T^-T (elliptic) or m_T |det R_T| w_j
+// (projection), written in FP64 (and FP32), plus the element geometry and the
+// Jacobi diagonal sum_j B_{.jl}^T A_T,j B_{.jl} scattered into diag.
+template <int D, int P, int FORM>
+__global__ void __launch_bounds__(128) k_ahat(AhatArgs a) {
+  using TB = dogip_tab::Tab<D, P, FORM>;
+  constexpr int V = TB::V, W = TB::W, NB = TB::NB, NS = NSym<D, FORM>::value;
+  const int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (pos >= a.E) return;
+  double K[NS], Ri[D][D], vol;
+  const int err = cell_factor<D, FORM>(a, pos, K, Ri, vol);
   if (err) atomicOr(a.err, err);
   const int64_t tile = pos >> 5;
   const int lane = (int)(pos & 31);
-  if (a.fact) {
+  if (a.aw != nullptr) {
+    // global double grid: A_diag,i = sum over the cells containing W node i of K_T w_j
+    const uint32_t* cw = a.connW + tile * ((int64_t)W * kTile) + lane;
+    static_for<W>([&](auto jc) {
+      constexpr int j = decltype(jc)::value;
+      constexpr double wj = TB::w[j];
+      atomicAdd(a.aw + (cw[j * kTile] & kIdMask), wj * K[0]);
+    });
+  } else if (a.fact) {
     double* Kt = a.A64 + tile * ((int64_t)NS * kTile) + lane;
     float* Kt32 = a.A32 ? a.A32 + tile * ((int64_t)NS * kTile) + lane : nullptr;
     static_for<NS>([&](auto kc) {
@@ -941,5 +1055,207 @@ __global__ void k_export_fact(const double* K, const int64_t* perm, double* out,
 // A_T (AoSoA, processing order) -> [E][W][NS] caller order; nsw = W * NS.
 __global__ void k_export_ahat(const double* A, const int64_t* perm, double* out, int64_t E,
                               int nsw);
+
+// ------------------------------------ quadrature-point matrix-free apply
+//
+// The conventional matrix-free operator that the paper sets DoGIP against (§1,
+// §3.3), on the same GPU as a comparator: per (cell, right-hand side) one thread
+// recomputes the geometry R_T, |det R_T|, R_T^-1 from the vertex coordinates at every
+// apply, reads the cell's coefficient, and integrates with the collapsed
+// Gauss-Jacobi rule of TabQ (exact for element-constant coefficients):
+//   Y_T = sum_q B_q^T (w_q K_T) B_q u_T,   K_T = |det R_T| R_T^-1 M_T R_T^-T  (or m_T |det R_T|).
+// The edge vectors are formed in FP64 from the FP64 coordinates; everything after
+// that runs in T.  Atomic scatter; the Dirichlet rows are written by the caller.
+
+template <typename T>
+struct QpArgs {
+  const double* coords;  // [nv x D]
+  const int32_t* cells;  // [E x (D+1)] processing order
+  const T* coef;         // [E][n_sym] processing order
+  const uint32_t* conn;  // AoSoA [Epad/32][V][32]
+  const T* u;            // [n x R]
+  T* y;                  // [n x R]
+  int64_t E;
+  int R;
+};
+
+template <int D, int P, int FORM, typename T, bool MULTI>
+__global__ void __launch_bounds__(256) k_apply_qp(QpArgs<T> a) {
+  using TQ = dogip_tab::TabQ<D, P, FORM>;
+  constexpr int V = TQ::V, Q = TQ::W, NB = TQ::NB, NS = NSym<D, FORM>::value;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t e;
+  int r = 0;
+  if constexpr (MULTI) {
+    const int64_t q = t / a.R;
+    e = q;
+    r = (int)(t - q * a.R);
+  } else {
+    e = t;
+  }
+  if (e >= a.E) return;
+  const int R = MULTI ? a.R : 1;
+  // geometry of the cell
+  double X0[D];
+  T Rm[D][D], Ri[D][D];
+  const int32_t v0 = __ldg(a.cells + e * (D + 1));
+  static_for<D>([&](auto kc) {
+    constexpr int k = decltype(kc)::value;
+    X0[k] = __ldg(a.coords + (int64_t)v0 * D + k);
+  });
+  static_for<D>([&](auto ic) {
+    constexpr int i = decltype(ic)::value;  // column i = v_{i+1} - v_0
+    const int32_t vi = __ldg(a.cells + e * (D + 1) + i + 1);
+    static_for<D>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      Rm[k][i] = (T)(__ldg(a.coords + (int64_t)vi * D + k) - X0[k]);
+    });
+  });
+  const T vol = fabs(det_inv<D, T>(Rm, Ri));
+  T K[NS];
+  if constexpr (FORM == DOGIP_PROJECTION) {
+    K[0] = __ldg(a.coef + e) * vol;
+  } else {
+    T M[NS];
+    static_for<NS>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      M[k] = __ldg(a.coef + e * NS + k);
+    });
+    static_for<D>([&](auto rc) {
+      constexpr int rr = decltype(rc)::value;
+      static_for<D>([&](auto sc) {
+        constexpr int ss = decltype(sc)::value;
+        if constexpr (rr <= ss) {
+          T acc = T(0);
+          static_for<D>([&](auto pc) {
+            constexpr int pp = decltype(pc)::value;
+            static_for<D>([&](auto qc) {
+              constexpr int qq = decltype(qc)::value;
+              acc = fma(Ri[rr][pp] * M[sym_idx(D, pp, qq)], Ri[ss][qq], acc);
+            });
+          });
+          K[sym_idx(D, rr, ss)] = vol * acc;
+        }
+      });
+    });
+  }
+  // gather, quadrature loop, scatter
+  const int64_t tile = e >> 5;
+  const int lane = (int)(e & 31);
+  const uint32_t* ct = a.conn + tile * (V * kTile) + lane;
+  uint32_t c[V];
+  T ul[V], Y[V];
+  static_for<V>([&](auto lc) {
+    constexpr int l = decltype(lc)::value;
+    c[l] = __ldg(ct + l * kTile);
+  });
+  static_for<V>([&](auto lc) {
+    constexpr int l = decltype(lc)::value;
+    ul[l] = (c[l] & kBndBit) ? T(0) : __ldg(a.u + (int64_t)(c[l] & kIdMask) * R + r);
+    if constexpr (col_empty<TQ>(l)) Y[l] = T(0);
+  });
+  static_for<Q>([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    constexpr double wq = TQ::w[q];
+    T g[NB], h[NB], aq[NS];
+    static_for<NS>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      aq[k] = T(wq) * K[k];
+    });
+    interp<TQ, q>(ul, g);
+    block_mul<D, FORM>(aq, g, h);
+    project<TQ, q>(h, Y);
+  });
+  static_for<V>([&](auto lc) {
+    constexpr int l = decltype(lc)::value;
+    if (!(c[l] & kBndBit)) atomicAdd(a.y + (int64_t)(c[l] & kIdMask) * R + r, Y[l]);
+  });
+}
+
+// ------------------------- global double grid for the weighted projection
+//
+// §2.2, Theorem "DoGIP for weighted projection": K = B^* A_diag B with the continuous
+// W = C_{N,2p}, B_ij = phi_V^j(x_W^i) and A_diag,ii = int m phi_W^i.  Every W node is
+// owned by the first cell containing it (bit 31 of its connW entry), so
+//   k_gw_interp:  w_i = A_diag,ii (B u)_i, written once by the owner (no atomics),
+//   k_gw_project: y  += sum over owned nodes j of the cell of B^_j^T w_i (atomics),
+// which counts every pair (i, l) of B exactly once (phi_V^l vanishes at the W nodes of
+// a cell that does not contain dof l).  Rows of B are the element-wise tables.
+
+template <typename T>
+struct GwArgs {
+  const uint32_t* conn;   // AoSoA [Epad/32][V][32]
+  const uint32_t* connW;  // AoSoA [Epad/32][W][32], bit 31 = owned by this cell
+  const T* A;             // A_diag [n_W]
+  const T* u;             // [n x R]
+  T* w;                   // [n_W x R] scratch
+  T* y;                   // [n x R]
+  int64_t E;
+  int R;
+  const int* skip;        // device flag: return at once when set (may be null)
+};
+
+template <int D, int P, typename T, bool MULTI>
+__global__ void __launch_bounds__(256) k_gw_interp(GwArgs<T> a) {
+  using TB = dogip_tab::Tab<D, P, DOGIP_PROJECTION>;
+  constexpr int V = TB::V, W = TB::W;
+  if (a.skip != nullptr && *a.skip) return;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t e = MULTI ? t / a.R : t;
+  const int r = MULTI ? (int)(t - e * a.R) : 0;
+  if (e >= a.E) return;
+  const int R = MULTI ? a.R : 1;
+  const int64_t tile = e >> 5;
+  const int lane = (int)(e & 31);
+  const uint32_t* ct = a.conn + tile * (V * kTile) + lane;
+  const uint32_t* cw = a.connW + tile * ((int64_t)W * kTile) + lane;
+  T ul[V];
+  static_for<V>([&](auto lc) {
+    constexpr int l = decltype(lc)::value;
+    ul[l] = __ldg(a.u + (int64_t)(__ldg(ct + l * kTile) & kIdMask) * R + r);
+  });
+  static_for<W>([&](auto jc) {
+    constexpr int j = decltype(jc)::value;
+    const uint32_t cj = __ldg(cw + j * kTile);
+    if (cj & kBndBit) {
+      T g[1];
+      interp<TB, j>(ul, g);
+      const int64_t i = (int64_t)(cj & kIdMask);
+      a.w[i * R + r] = __ldg(a.A + i) * g[0];
+    }
+  });
+}
+
+template <int D, int P, typename T, bool MULTI>
+__global__ void __launch_bounds__(256) k_gw_project(GwArgs<T> a) {
+  using TB = dogip_tab::Tab<D, P, DOGIP_PROJECTION>;
+  constexpr int V = TB::V, W = TB::W;
+  if (a.skip != nullptr && *a.skip) return;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t e = MULTI ? t / a.R : t;
+  const int r = MULTI ? (int)(t - e * a.R) : 0;
+  if (e >= a.E) return;
+  const int R = MULTI ? a.R : 1;
+  const int64_t tile = e >> 5;
+  const int lane = (int)(e & 31);
+  const uint32_t* ct = a.conn + tile * (V * kTile) + lane;
+  const uint32_t* cw = a.connW + tile * ((int64_t)W * kTile) + lane;
+  T Y[V];
+  static_for<V>([&](auto lc) {
+    constexpr int l = decltype(lc)::value;
+    if constexpr (col_empty<TB>(l)) Y[l] = T(0);
+  });
+  static_for<W>([&](auto jc) {
+    constexpr int j = decltype(jc)::value;
+    const uint32_t cj = __ldg(cw + j * kTile);
+    T h[1];
+    h[0] = (cj & kBndBit) ? __ldg(a.w + (int64_t)(cj & kIdMask) * R + r) : T(0);
+    project<TB, j>(h, Y);
+  });
+  static_for<V>([&](auto lc) {
+    constexpr int l = decltype(lc)::value;
+    atomicAdd(a.y + (int64_t)(__ldg(ct + l * kTile) & kIdMask) * R + r, Y[l]);
+  });
+}
 
 }  // namespace dogip

@@ -28,6 +28,12 @@ void setup_run(Ctx& c, const SetupCall& k, cudaStream_t s) {
     case kSetupAhat: {
       AhatArgs a{c.d_coords, c.factorized ? 1 : 0, c.d_cells, c.d_perm, k.coef, k.coef_kind,
                  c.d_conn, c.d_A64, c.keep32 ? c.d_A32 : nullptr, c.d_geo, c.d_diag, c.d_err, c.E};
+      a.qp64 = c.d_qp64;
+      a.qp32 = c.keep32 ? c.d_qp32 : nullptr;
+      if (c.global_w) {
+        a.connW = c.d_connW;
+        a.aw = c.d_Aw64;
+      }
       k_ahat<D, P, FORM><<<nb, 128, 0, s>>>(a);
       break;
     }

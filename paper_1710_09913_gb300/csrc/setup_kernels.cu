@@ -11,6 +11,20 @@ bool setup_d3(Ctx& c, const SetupCall& k, cudaStream_t s);
 
 namespace {
 void setup_dispatch(Ctx& c, const SetupCall& k, cudaStream_t s, const char* what) {
+  if (c.hi) {  // run-time tables: the precompute and the load are built, nothing else
+    bool ok = false;
+    if (k.op == kSetupAhat) {
+      AhatArgs a{c.d_coords, 0, c.d_cells, c.d_perm, k.coef, k.coef_kind, c.d_conn, c.d_A64,
+                 c.keep32 ? c.d_A32 : nullptr, c.d_geo, c.d_diag, c.d_err, c.E};
+      ok = ahat_hi(c, a, s);
+    } else if (k.op == kSetupLoad) {
+      LoadArgs a{c.d_geo, c.d_perm, k.f, c.d_conn, k.b, c.E};
+      ok = load_hi(c, a, s);
+    }
+    if (!ok) fail(DOGIP_EUNSUPPORTED, "not built for orders above the compiled tables");
+    cuda_check(cudaGetLastError(), what);
+    return;
+  }
   const bool ok = c.d == 2 ? setup_d2(c, k, s) : setup_d3(c, k, s);
   if (!ok) fail(DOGIP_EUNSUPPORTED, "no compiled instance for this (dim, p, form)");
   cuda_check(cudaGetLastError(), what);
@@ -29,6 +43,7 @@ int apply_d3b(const Ctx&, const void*, void*, int, int, bool, int64_t, int64_t, 
 namespace {
 int apply_dispatch(const Ctx& c, const void* u, void* y, int R, int prec, bool atomic, int64_t e0,
                    int64_t e1, cudaStream_t s, const int* skip) {
+  if (c.hi) return apply_hi(c, u, y, R, prec, atomic, e0, e1, s, skip);
   if (c.d == 2) return apply_d2(c, u, y, R, prec, atomic, e0, e1, s, skip);
   if (c.p <= 2) return apply_d3a(c, u, y, R, prec, atomic, e0, e1, s, skip);
   if (c.p == 3) return apply_d3b(c, u, y, R, prec, atomic, e0, e1, s, skip);
@@ -116,11 +131,13 @@ void copy_one(double* B, double* w, double* iv) {
 
 void launch_ahat(Ctx& c, const double* coef, int coef_kind, cudaStream_t s) {
   cuda_check(cudaMemsetAsync(c.d_diag, 0, sizeof(double) * c.n, s), "memset diag");
+  if (c.global_w) cuda_check(cudaMemsetAsync(c.d_Aw64, 0, sizeof(double) * c.nW, s), "memset A_diag");
   SetupCall k;
   k.op = kSetupAhat;
   k.coef = coef;
   k.coef_kind = coef_kind;
   setup_dispatch(c, k, s, "ahat kernel launch");
+  if (c.global_w && c.keep32) narrow_copy(c.d_Aw64, c.d_Aw32, c.nW, s);
   c.launches += 1;
   launch_diag_finish(c, s);
 }
@@ -200,6 +217,14 @@ void prepare_apply(Ctx& c) {
 
 void launch_apply_cg(Ctx& c, const void* p, void* q, int R, int prec, int scatter, cudaStream_t s,
                      SolveWork& w) {
+  if (c.global_w) {  // q was cleared by the previous p update (atomic scatter)
+    if (R > c.w_cap) fail(DOGIP_EINVAL, "global double-grid scratch too small for nrhs");
+    if (!apply_gw(c, p, q, R, prec, s, w.flags))
+      fail(DOGIP_EUNSUPPORTED, "no compiled global double-grid instance for this (dim, p)");
+    cuda_check(cudaGetLastError(), "global double-grid apply launch");
+    c.launches += 2;
+    return;
+  }
   if (scatter == DOGIP_SCATTER_ATOMIC) {
     const int k = apply_dispatch(c, p, q, R, prec, true, 0, c.E, s, w.flags);
     if (!k) fail(DOGIP_EUNSUPPORTED, "no compiled apply instance for this (dim, p, form)");
@@ -218,6 +243,14 @@ void launch_apply(Ctx& c, const void* u, void* y, int R, int prec, int scatter, 
                   const int* skip) {
   const size_t es = prec == DOGIP_FP64 ? sizeof(double) : sizeof(float);
   cuda_check(cudaMemsetAsync(y, 0, es * c.n * R, s), "memset y");
+  if (c.global_w) {
+    if (R > c.w_cap) fail(DOGIP_EINVAL, "global double-grid scratch too small for nrhs");
+    if (!apply_gw(c, u, y, R, prec, s, skip))
+      fail(DOGIP_EUNSUPPORTED, "no compiled global double-grid instance for this (dim, p)");
+    c.launches += 2;
+    cuda_check(cudaGetLastError(), "global double-grid apply launch");
+    return;
+  }
   bool staged = false;
   auto run = [&](bool atomic, int64_t e0, int64_t e1) {
     const int k = apply_dispatch(c, u, y, R, prec, atomic, e0, e1, s, skip);
@@ -238,17 +271,50 @@ void launch_apply(Ctx& c, const void* u, void* y, int R, int prec, int scatter, 
   cuda_check(cudaGetLastError(), "apply kernel launch");
 }
 
+bool apply_qp_d2(const Ctx& c, const void* u, void* y, int R, int prec, cudaStream_t s);
+bool apply_qp_d3(const Ctx& c, const void* u, void* y, int R, int prec, cudaStream_t s);
+
+void launch_apply_qp(Ctx& c, const void* u, void* y, int R, int prec, cudaStream_t s) {
+  const size_t es = prec == DOGIP_FP64 ? sizeof(double) : sizeof(float);
+  cuda_check(cudaMemsetAsync(y, 0, es * c.n * R, s), "memset y");
+  const bool ok = c.d == 2 ? apply_qp_d2(c, u, y, R, prec, s) : apply_qp_d3(c, u, y, R, prec, s);
+  if (!ok) fail(DOGIP_EUNSUPPORTED, "no compiled quadrature-point instance for this (dim, p, form)");
+  c.launches += 1;
+  if (c.dirichlet && c.nbnd > 0) {
+    launch_dirichlet_copy(c, u, y, R, prec, s, nullptr);
+    c.launches += 1;
+  }
+  cuda_check(cudaGetLastError(), "quadrature-point apply launch");
+}
+
 bool table_info(int d, int p, int form, int* NB, int* W, int* V, long long* nnz, long long* nnz1) {
   bool ok_ = true;
 #define CALL(D, P, F) info_one<D, P, F>(NB, W, V, nnz, nnz1)
   DOGIP_DISPATCH(d, p, form, CALL);
 #undef CALL
+  if (!ok_) return hi_table(d, p, form, NB, W, V, nnz, nnz1, nullptr, nullptr, nullptr);
   return ok_;
 }
 
 bool table_copy(int d, int p, int form, double* B, double* w, double* iv) {
   bool ok_ = true;
 #define CALL(D, P, F) copy_one<D, P, F>(B, w, iv)
+  DOGIP_DISPATCH(d, p, form, CALL);
+#undef CALL
+  if (!ok_) {
+    int NB, W, V;
+    const double *hB, *hw, *hiv;
+    if (!hi_table(d, p, form, &NB, &W, &V, nullptr, nullptr, &hB, &hw, &hiv)) return false;
+    if (B) std::memcpy(B, hB, sizeof(double) * NB * W * V);
+    if (w) std::memcpy(w, hw, sizeof(double) * W);
+    if (iv) std::memcpy(iv, hiv, sizeof(double) * V);
+  }
+  return true;
+}
+
+bool table_is_compiled(int d, int p, int form) {
+  bool ok_ = true;
+#define CALL(D, P, F) (void)0
   DOGIP_DISPATCH(d, p, form, CALL);
 #undef CALL
   return ok_;

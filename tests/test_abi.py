@@ -42,10 +42,11 @@ def test_version_and_error_string(lib):
     assert isinstance(lib.lib.dogip_last_error(), bytes)
 
 
-@pytest.mark.parametrize("d,p,form", [(2, p, f) for p in (1, 2, 3, 4) for f in ("projection", "elliptic")]
-                         + [(3, p, f) for p in (1, 2, 3) for f in ("projection", "elliptic")])
+@pytest.mark.parametrize("d,p,form", [(2, p, f) for p in range(1, 9) for f in ("projection", "elliptic")]
+                         + [(3, p, f) for p in (1, 2, 3, 4) for f in ("projection", "elliptic")])
 def test_tables_equal_oracle(lib, d, p, form):
-    """B and w compiled into the kernels == the oracle's exact rationals rounded once."""
+    """B and w of the library (compiled into the kernels for p <= 4 (3D: 3), run-time
+    tables above) == the oracle's exact rationals rounded once, bit for bit."""
     from oracle import refelem
     B, w = lib.get_tables(d, p, form)
     ref = refelem.bhat(form, d, p)
@@ -58,7 +59,7 @@ def test_tables_equal_oracle(lib, d, p, form):
 
 def test_unsupported_order(lib):
     sizes = (C.c_int * 3)()
-    assert lib.lib.dogip_get_tables(3, 4, 1, None, None, sizes) == lib.EUNSUPPORTED
+    assert lib.lib.dogip_get_tables(3, 5, 1, None, None, sizes) == lib.EUNSUPPORTED
     assert lib.lib.dogip_get_tables(2, 9, 1, None, None, sizes) == lib.EUNSUPPORTED
 
 
