@@ -59,8 +59,10 @@ void run_apply_tma(const T* A, const Ctx& c, const void* u, void* y, int R, cuda
   const int64_t nchunks = (ntiles + Cfg::TPC - 1) / Cfg::TPC;
   if (nchunks == 0) return;
   const int64_t grid = std::min<int64_t>(nchunks, (int64_t)num_sms * blocks_per_sm);
+  const bool r4 = sizeof(T) == 4 && R % 4 == 0 && ((uintptr_t)u & 15u) == 0 &&
+                  ((uintptr_t)y & 15u) == 0;
   TmaArgs<T> a{A, c.d_conn, (const T*)u, (T*)y, c.E, ntiles, nchunks, R, skip, c.d_kerr,
-                c.d_bnd, c.dirichlet ? c.nbnd : 0, c.wait_budget, c.test_skip_chunk};
+                c.d_bnd, c.dirichlet ? c.nbnd : 0, c.wait_budget, c.test_skip_chunk, r4 ? 1 : 0};
   k_apply_tma<D, P, FORM, T, FACT><<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
 }
 
@@ -87,7 +89,11 @@ int run_apply(const Ctx& c, const void* u, void* y, int R, int prec, bool atomic
   }
   // variant: 1 staged, 0 one thread per cell
   const int var = c.apply_variant_prec[prec] >= 0 ? c.apply_variant_prec[prec] : c.apply_variant;
-  const bool whole = atomic && e0 == 0 && e1 == c.E && var == 1;
+  // several right-hand sides in FP32 reuse A_T from shared memory 4 at a time in the
+  // staged kernel (the autotuner times one rhs only)
+  constexpr bool small_v = dogip_tab::Tab<D, P, FORM>::V <= 10;
+  const bool multi4 = small_v && prec == DOGIP_FP32 && R % 4 == 0;
+  const bool whole = atomic && e0 == 0 && e1 == c.E && (var == 1 || multi4);
   if (prec == DOGIP_FP64) {
     if constexpr (ok64) {
       if (whole) {

@@ -299,6 +299,7 @@ struct TmaArgs {
   int64_t nbnd;
   long long wait_budget;  // clock cycles per bounded mbarrier wait
   int64_t test_skip_chunk;  // test hook: this chunk's copy is never issued (-1: none)
+  int r4;                   // 1: FP32, R % 4 == 0, u and y 16-byte aligned
 };
 
 template <int D, int P, int FORM, typename T, bool FACT>
@@ -310,6 +311,8 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T, FACT>::THREADS)
   constexpr int V = C::V, W = C::W, NB = TB::NB, NS = C::NS;
   // prefetch the next unit's gathers where the extra V live values fit the registers
   constexpr bool PF = sizeof(T) * V <= 64;
+  // 4-wide right-hand-side units (FP32, small V)
+  constexpr bool Q4 = std::is_same<T, float>::value && V <= 10;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base =
       (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
@@ -378,114 +381,143 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T, FACT>::THREADS)
     }
   } else {
     // ---- consumer warps: warp w computes tile w of every chunk.  A unit of work
-    // is (chunk, rhs); the u gathers of the next unit are issued before the
-    // arithmetic of the current one, so their latency hides behind it.
-    int failed = 0;
-    uint32_t c[V], cn[V];
-    T ul[V];
-    bool active = false;
-    if (k0 < a.nchunks) {
-      failed = __any_sync(0xffffffffu, mbar_wait_bounded(pro, 0u, a.wait_budget) ? 0 : 1);
-      if (!failed) {
-        const int64_t tile = k0 * C::TPC + warp;
-        active = tile < a.ntiles && tile * kTile + lane < a.E;
-        const uint32_t* sC = (const uint32_t*)(pro_buf + warp * C::C_TILE) + lane;
+    // is (chunk, RW right-hand sides); the u gathers of the next unit are issued
+    // before the arithmetic of the current one, so their latency hides behind it.
+    // FP32 with nrhs a multiple of 4 (r4) takes RW = 4: one 16-byte gather and one
+    // 16-byte atomic per dof and unit, A_T read from shared memory once per 4 rhs.
+    auto consume = [&](auto rw_tag) {
+      constexpr int RW = decltype(rw_tag)::value;
+      constexpr bool PFW = PF && RW == 1;
+      int failed = 0;
+      uint32_t c[V], cn[V];
+      T ul[RW][V];
+      bool active = false;
+      auto gather = [&](const uint32_t(&cc)[V], int r, T(&dst)[RW][V]) {
         static_for<V>([&](auto lc) {
           constexpr int l = decltype(lc)::value;
-          c[l] = active ? sC[l * kTile] : kBndBit;
-          if constexpr (PF)
-            ul[l] = (c[l] & kBndBit) ? T(0) : __ldg(a.u + (int64_t)(c[l] & kIdMask) * a.R);
+          if constexpr (RW == 4) {
+            float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (!(cc[l] & kBndBit))
+              v = __ldg((const float4*)(a.u + (int64_t)(cc[l] & kIdMask) * a.R + r));
+            dst[0][l] = v.x;
+            dst[1][l] = v.y;
+            dst[2][l] = v.z;
+            dst[3][l] = v.w;
+          } else {
+            dst[0][l] =
+                (cc[l] & kBndBit) ? T(0) : __ldg(a.u + (int64_t)(cc[l] & kIdMask) * a.R + r);
+          }
         });
+      };
+      if (k0 < a.nchunks) {
+        failed = __any_sync(0xffffffffu, mbar_wait_bounded(pro, 0u, a.wait_budget) ? 0 : 1);
+        if (!failed) {
+          const int64_t tile = k0 * C::TPC + warp;
+          active = tile < a.ntiles && tile * kTile + lane < a.E;
+          const uint32_t* sC = (const uint32_t*)(pro_buf + warp * C::C_TILE) + lane;
+          static_for<V>([&](auto lc) {
+            constexpr int l = decltype(lc)::value;
+            c[l] = active ? sC[l * kTile] : kBndBit;
+          });
+          if constexpr (PFW) gather(c, 0, ul);
+        }
       }
-    }
-    for (int64_t i = 0; !failed; ++i) {
-      const int64_t k = k0 + i * G;
-      if (k >= a.nchunks) break;
-      const int s = (int)(i % C::S);
-      const uint32_t parity = (uint32_t)((i / C::S) & 1);
-      failed = __any_sync(0xffffffffu, mbar_wait_bounded(&full[s], parity, a.wait_budget) ? 0 : 1);
-      if (failed) break;
-      const T* sA = (const T*)(base + (size_t)s * C::CHUNK + warp * C::A_TILE) + lane;
-      const uint32_t* sCn =
-          (const uint32_t*)(base + (size_t)s * C::CHUNK + C::TPC * C::A_TILE + warp * C::C_TILE) +
-          lane;
-      const int64_t kn = k + G, tile_n = kn * C::TPC + warp;
-      const bool active_n = kn < a.nchunks && tile_n < a.ntiles && tile_n * kTile + lane < a.E;
-      T kf[NS];  // factorised K_T (FACT only)
-      if constexpr (FACT) {
-        static_for<NS>([&](auto kc) {
-          constexpr int kk = decltype(kc)::value;
-          kf[kk] = active ? sA[kk * kTile] : T(0);
-        });
-      }
-      for (int r = 0; r < a.R; ++r) {
-        // next unit: (this chunk, r + 1) or (next chunk, rhs 0)
-        T un[V];
-        if (r + 1 < a.R) {
-          if constexpr (PF) {
+      for (int64_t i = 0; !failed; ++i) {
+        const int64_t k = k0 + i * G;
+        if (k >= a.nchunks) break;
+        const int s = (int)(i % C::S);
+        const uint32_t parity = (uint32_t)((i / C::S) & 1);
+        failed = __any_sync(0xffffffffu, mbar_wait_bounded(&full[s], parity, a.wait_budget) ? 0 : 1);
+        if (failed) break;
+        const T* sA = (const T*)(base + (size_t)s * C::CHUNK + warp * C::A_TILE) + lane;
+        const uint32_t* sCn =
+            (const uint32_t*)(base + (size_t)s * C::CHUNK + C::TPC * C::A_TILE + warp * C::C_TILE) +
+            lane;
+        const int64_t kn = k + G, tile_n = kn * C::TPC + warp;
+        const bool active_n = kn < a.nchunks && tile_n < a.ntiles && tile_n * kTile + lane < a.E;
+        T kf[NS];  // factorised K_T (FACT only)
+        if constexpr (FACT) {
+          static_for<NS>([&](auto kc) {
+            constexpr int kk = decltype(kc)::value;
+            kf[kk] = active ? sA[kk * kTile] : T(0);
+          });
+        }
+        for (int r = 0; r < a.R; r += RW) {
+          // next unit: (this chunk, r + RW) or (next chunk, rhs 0)
+          T un[RW][V];
+          if (r + RW < a.R) {
+            if constexpr (PFW) gather(c, r + RW, un);
+          } else {
             static_for<V>([&](auto lc) {
               constexpr int l = decltype(lc)::value;
-              un[l] = (c[l] & kBndBit) ? T(0)
-                                       : __ldg(a.u + (int64_t)(c[l] & kIdMask) * a.R + (r + 1));
+              cn[l] = active_n ? sCn[l * kTile] : kBndBit;
             });
+            if constexpr (PFW) gather(cn, 0, un);
           }
-        } else {
-          static_for<V>([&](auto lc) {
-            constexpr int l = decltype(lc)::value;
-            cn[l] = active_n ? sCn[l * kTile] : kBndBit;
-            if constexpr (PF)
-              un[l] = (cn[l] & kBndBit) ? T(0) : __ldg(a.u + (int64_t)(cn[l] & kIdMask) * a.R);
-          });
-        }
-        if constexpr (!PF) {  // gathers of this unit (no prefetch: register budget)
-          static_for<V>([&](auto lc) {
-            constexpr int l = decltype(lc)::value;
-            ul[l] = (c[l] & kBndBit) ? T(0) : __ldg(a.u + (int64_t)(c[l] & kIdMask) * a.R + r);
-          });
-        }
-        if (active) {
-          T Y[V];
-          static_for<V>([&](auto lc) {
-            constexpr int l = decltype(lc)::value;
-            if constexpr (col_empty<TB>(l)) Y[l] = T(0);
-          });
-          static_for<W>([&](auto jc) {
-            constexpr int j = decltype(jc)::value;
-            T g[NB], h[NB], aj[NS];
-            static_for<NS>([&](auto kc) {
-              constexpr int kk = decltype(kc)::value;
-              if constexpr (FACT) {
-                constexpr double wj = TB::w[j];
-                aj[kk] = T(wj) * kf[kk];
-              } else {
-                aj[kk] = sA[(j * NS + kk) * kTile];
+          if constexpr (!PFW) gather(c, r, ul);  // this unit (no prefetch: register budget)
+          if (active) {
+            T Y[RW][V];
+            static_for<RW>([&](auto qc) {
+              constexpr int q = decltype(qc)::value;
+              static_for<V>([&](auto lc) {
+                constexpr int l = decltype(lc)::value;
+                if constexpr (col_empty<TB>(l)) Y[q][l] = T(0);
+              });
+            });
+            static_for<W>([&](auto jc) {
+              constexpr int j = decltype(jc)::value;
+              T aj[NS];
+              static_for<NS>([&](auto kc) {
+                constexpr int kk = decltype(kc)::value;
+                if constexpr (FACT) {
+                  constexpr double wj = TB::w[j];
+                  aj[kk] = T(wj) * kf[kk];
+                } else {
+                  aj[kk] = sA[(j * NS + kk) * kTile];
+                }
+              });
+              static_for<RW>([&](auto qc) {
+                constexpr int q = decltype(qc)::value;
+                T g[NB], h[NB];
+                interp<TB, j>(ul[q], g);
+                block_mul<D, FORM>(aj, g, h);
+                project<TB, j>(h, Y[q]);
+              });
+            });
+            static_for<V>([&](auto lc) {
+              constexpr int l = decltype(lc)::value;
+              if (!(c[l] & kBndBit)) {
+                T* dst = a.y + (int64_t)(c[l] & kIdMask) * a.R + r;
+                if constexpr (RW == 4)
+                  atomicAdd((float4*)dst, make_float4(Y[0][l], Y[1][l], Y[2][l], Y[3][l]));
+                else
+                  atomicAdd(dst, Y[0][l]);
               }
             });
-            interp<TB, j>(ul, g);
-            block_mul<D, FORM>(aj, g, h);
-            project<TB, j>(h, Y);
-          });
-          static_for<V>([&](auto lc) {
-            constexpr int l = decltype(lc)::value;
-            if (!(c[l] & kBndBit)) atomicAdd(a.y + (int64_t)(c[l] & kIdMask) * a.R + r, Y[l]);
-          });
+          }
+          if constexpr (PFW) {
+            static_for<V>([&](auto lc) {
+              constexpr int l = decltype(lc)::value;
+              ul[0][l] = un[0][l];
+            });
+          }
         }
-        if constexpr (PF) {
-          static_for<V>([&](auto lc) {
-            constexpr int l = decltype(lc)::value;
-            ul[l] = un[l];
-          });
-        }
+        static_for<V>([&](auto lc) {
+          constexpr int l = decltype(lc)::value;
+          c[l] = cn[l];
+        });
+        active = active_n;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);  // this warp no longer reads stage s
       }
-      static_for<V>([&](auto lc) {
-        constexpr int l = decltype(lc)::value;
-        c[l] = cn[l];
-      });
-      active = active_n;
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[s]);  // this warp no longer reads stage s
+      if (failed && lane == 0) atomicOr(a.err, 1);
+    };
+    if constexpr (Q4) {
+      if (a.r4) consume(std::integral_constant<int, 4>{});
+      else consume(std::integral_constant<int, 1>{});
+    } else {
+      consume(std::integral_constant<int, 1>{});
     }
-    if (failed && lane == 0) atomicOr(a.err, 1);
   }
   __syncthreads();
   // Dirichlet rows: y_b = u_b (the scatter skipped them)

@@ -231,8 +231,8 @@ def test_invalid_inputs_rejected(B):
     with pytest.raises(B.DogipError) as e:  # colour scatter needs colour-sorted storage
         ctx.apply(b, scatter="colour")
     assert e.value.code == B.EINVAL
-    with pytest.raises(B.DogipError) as e:
-        B.Context(*inputs.lattice_mesh(3, 1), 4, "elliptic", np.ones(6))
+    with pytest.raises(B.DogipError) as e:  # above the orders of Tables 2 and 4
+        B.Context(*inputs.lattice_mesh(3, 1), 5, "elliptic", np.ones(6))
     assert e.value.code == B.EUNSUPPORTED
 
 
