@@ -38,6 +38,10 @@ WORKLOAD = ("2D scalar elliptic, unit square, 512x512 grid x 2 triangles (524,28
             "eigenvalues, uniform rotation), f = 1, zero Dirichlet; P1-P4 sweep; "
             "mixed FP32 PCG + FP64 refinement to 1e-8")
 L2_FLUSH_BYTES = 512 << 20
+# DRAM bytes (read + write) of one launch of the staged P4 FP32 apply on this workload,
+# from the ncu capture summarised in profiles/k_apply_tma_2d_p4_fp32.md; to be taken
+# again whenever that kernel changes.
+TRAFFIC_P4_FP32 = 252637696  # 241,421,824 read + 11,215,872 written
 
 
 def mesh_and_coef():
@@ -315,6 +319,17 @@ def only_apply(args):
     return 0
 
 
+_T0 = [None, None]
+
+
+def _section(name):
+    """Progress line on stderr with the wall time of the previous section."""
+    now = time.time()
+    if _T0[0] is not None:
+        print(f"[bench] {_T0[1]}: {now - _T0[0]:.1f} s", file=sys.stderr, flush=True)
+    _T0[0], _T0[1] = now, name
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -403,6 +418,7 @@ def main():
     value = work_all / (total_ms * 1e-3) / 1e9
     clocks = clk.summary()
 
+    _section("time_to_tol")
     # time-to-tolerance per p: mixed (from the timed steps' last solve) and FP64 PCG
     t2t = {"mixed_ms": {}, "fp64_ms": {}, "mixed_iters": {}, "fp64_iters": {}, "mixed_outer": {}}
     for p in P_LIST:
@@ -422,6 +438,7 @@ def main():
                 t2t["mixed_outer"][f"P{p}"] = info["outer"]
             t2t.setdefault(f"{mode}_rel_residual", {})[f"P{p}"] = info["rel_residual"]
 
+    _section("apply")
     # apply throughput and roofline of the dominant kernel (FP32 apply)
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
@@ -452,6 +469,7 @@ def main():
                                        "GBps": round(bytes_alg / ms / 1e6, 1),
                                        "TFLOPs": round(flops_alg / ms / 1e9, 3),
                                        "alg_bytes": int(bytes_alg), "alg_flops": int(flops_alg)}
+    _section("csr")
     # assembled CSR on the same GPU: SpMV bandwidth and FP64 PCG time-to-tolerance
     csr = {}
     if not args.no_csr:
@@ -496,6 +514,7 @@ def main():
             del K64
             torch.cuda.empty_cache()
 
+    _section("batch")
     # batched uneven problems (256 independent 2D problems, one graph launch per phase)
     batch = None
     if not args.no_batch:
@@ -533,6 +552,7 @@ def main():
                  "gpu_launches": int(sum(c.launches() for c in bctx) - l0)}
         del bctx, bb, bu
 
+    _section("cube3d")
     # 3D, 64^3 cube x 6 tetrahedra, P2, inclusions, 16 right-hand sides in one launch
     multi = None
     if not args.no_3d:
@@ -599,6 +619,7 @@ def main():
             del c, b3, u3
             torch.cuda.empty_cache()
 
+    _section("factorized")
     # factorised element factors (A_T,j = w_j K_T, K_T per cell): a different memory
     # trade-off, reported beside the per-node storage of the headline
     fact = {}
@@ -635,6 +656,7 @@ def main():
         fact[f"P{p}"] = out
         del cf
 
+    _section("qp")
     # the conventional quadrature-point matrix-free apply on the same GPU (comparator):
     # geometry from the vertex coordinates at every apply, the cell's coefficient, and
     # a collapsed Gauss-Jacobi rule of p^2 points (stiffness, element-constant M_T)
@@ -667,6 +689,7 @@ def main():
             out[f"dogip_apply_{prec}_ms"] = applies[f"P{p}_{prec}"]["ms"]
         qp[f"P{p}"] = out
 
+    _section("global_w")
     # global double grid of the weighted projection (one A_diag value per global W node)
     # against the element-wise projection on the same mesh (scalar lognormal m)
     gw = {}
@@ -709,6 +732,7 @@ def main():
             del c
         gw[f"P{p}"] = out
 
+    _section("high_order")
     # higher orders of Tables 3-4 (run-time-table kernels), same mesh and tensors
     hi_ord = {}
     for p in (5, 6, 7, 8):
@@ -739,14 +763,19 @@ def main():
         del c
         torch.cuda.empty_cache()
 
+    _section("roofline")
     dom = applies["P4_fp32"]
     roofline = {"bound": "hbm", "achieved": dom["GBps"], "peak": hbm, "unit": "GB/s",
-                "frac": round(dom["GBps"] / hbm, 4), "traffic": None,
-                "kernel": "k_apply<2,4,ELLIPTIC,float,atomic> (dogip_apply call: memset + kernel "
-                          "+ boundary copy), 2D P4, 524,288 cells",
+                "frac": round(dom["GBps"] / hbm, 4),
+                "traffic": TRAFFIC_P4_FP32 if tuned["P4"]["fp32"][0] == 1 else None,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch "
+                                  "(profiles/k_apply_tma_2d_p4_fp32.md)",
+                "kernel": "k_apply_tma<2,4,ELLIPTIC,float> (staged apply), 2D P4, 524,288 cells; "
+                          "timed as 30 back-to-back dogip_apply calls (y memset + kernel)",
                 "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
                 "alg_bytes_per_launch": dom["alg_bytes"]}
 
+    _section("e2e")
     # end to end through the public API with host buffers
     A_host = torch.tensor(A).pin_memory()
     u_host = {p: torch.empty(ctxs[p].n, dtype=torch.float64).pin_memory() for p in P_LIST}
@@ -774,11 +803,13 @@ def main():
     e2e = {"value": e2e_work * ws / (e2e_ms * 1e-3) / 1e9, "unit": "GDoF/s",
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
+    _section("cpu_baseline")
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         w, s, desc = oracle_sample(coords, cells, A, P_LIST, 1)
         cpu = {"value": w / s / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle", "sample": desc}
 
+    _section("done")
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
