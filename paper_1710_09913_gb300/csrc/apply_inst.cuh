@@ -66,7 +66,41 @@ void run_apply_tma(const T* A, const Ctx& c, const void* u, void* y, int R, cuda
   k_apply_tma<D, P, FORM, T, FACT><<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
 }
 
-// Returns 2 when the staged kernel ran (it also wrote the Dirichlet rows), 1 for the
+// Self-feeding warps variant (one right-hand side, atomic scatter, whole range).
+template <int D, int P, int FORM, typename T>
+const TmaLaunch& sfw_launch() {
+  static const TmaLaunch info = [] {
+    using Cfg = SfwCfg<D, P, FORM, T>;
+    auto kern = k_apply_sfw<D, P, FORM, T>;
+    TmaLaunch t;
+    cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM),
+               "apply smem attribute");
+    int dev = 0, nb = 0;
+    cuda_check(cudaGetDevice(&dev), "get device");
+    cuda_check(cudaDeviceGetAttribute(&t.num_sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, Cfg::THREADS, Cfg::SMEM),
+               "occupancy");
+    t.blocks_per_sm = nb < 1 ? 1 : nb;
+    return t;
+  }();
+  return info;
+}
+
+template <int D, int P, int FORM, typename T>
+void run_apply_sfw(const T* A, const Ctx& c, const void* u, void* y, cudaStream_t s,
+                   const int* skip) {
+  using Cfg = SfwCfg<D, P, FORM, T>;
+  const TmaLaunch& L = sfw_launch<D, P, FORM, T>();
+  const int64_t ntiles = (c.E + kTile - 1) / kTile;
+  if (ntiles == 0) return;
+  const int64_t grid = std::min<int64_t>((ntiles + Cfg::NW - 1) / Cfg::NW,
+                                         (int64_t)L.num_sms * L.blocks_per_sm);
+  TmaArgs<T> a{A, c.d_conn, (const T*)u, (T*)y, c.E, ntiles, 0, 1, skip, c.d_kerr,
+                c.d_bnd, c.dirichlet ? c.nbnd : 0, c.wait_budget, c.test_skip_chunk, 0};
+  k_apply_sfw<D, P, FORM, T><<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
+}
+
+// Returns 2 when a staged kernel ran (it also wrote the Dirichlet rows), 1 for the
 // one-thread-per-cell kernel.
 template <int D, int P, int FORM>
 int run_apply(const Ctx& c, const void* u, void* y, int R, int prec, bool atomic, int64_t e0,
@@ -79,6 +113,8 @@ int run_apply(const Ctx& c, const void* u, void* y, int R, int prec, bool atomic
     } else {
       if constexpr (ok64) tma_launch<D, P, FORM, double, false>();
       if constexpr (ok32) tma_launch<D, P, FORM, float, false>();
+      if constexpr (SfwCfg<D, P, FORM, double>::OK) sfw_launch<D, P, FORM, double>();
+      if constexpr (SfwCfg<D, P, FORM, float>::OK) sfw_launch<D, P, FORM, float>();
     }
     return 1;
   }
@@ -87,13 +123,26 @@ int run_apply(const Ctx& c, const void* u, void* y, int R, int prec, bool atomic
     else run_apply_tma<D, P, FORM, float, true>(c.d_A32, c, u, y, R, s, skip);
     return 2;
   }
-  // variant: 1 staged, 0 one thread per cell
+  // variant: 2 self-feeding warps, 1 staged, 0 one thread per cell
   const int var = c.apply_variant_prec[prec] >= 0 ? c.apply_variant_prec[prec] : c.apply_variant;
+  if (var == 2 && R == 1 && atomic && e0 == 0 && e1 == c.E) {
+    if (prec == DOGIP_FP64) {
+      if constexpr (SfwCfg<D, P, FORM, double>::OK) {
+        run_apply_sfw<D, P, FORM, double>(c.d_A64, c, u, y, s, skip);
+        return 2;
+      }
+    } else {
+      if constexpr (SfwCfg<D, P, FORM, float>::OK) {
+        run_apply_sfw<D, P, FORM, float>(c.d_A32, c, u, y, s, skip);
+        return 2;
+      }
+    }
+  }
   // several right-hand sides in FP32 reuse A_T from shared memory 4 at a time in the
   // staged kernel (the autotuner times one rhs only)
   constexpr bool small_v = dogip_tab::Tab<D, P, FORM>::V <= 10;
   const bool multi4 = small_v && prec == DOGIP_FP32 && R % 4 == 0;
-  const bool whole = atomic && e0 == 0 && e1 == c.E && (var == 1 || multi4);
+  const bool whole = atomic && e0 == 0 && e1 == c.E && (var >= 1 || multi4);
   if (prec == DOGIP_FP64) {
     if constexpr (ok64) {
       if (whole) {

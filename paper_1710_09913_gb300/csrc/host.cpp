@@ -622,16 +622,11 @@ void run_chunk(Ctx& c, int prec, int scatter, double* x64, int k, double delta) 
     const int64_t launches_before = c.launches;  // captured launches run only on replay
     cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
     try {
+      const void* dinv = prec == DOGIP_FP64 ? (const void*)c.d_dinv64 : (const void*)c.d_dinv32;
       for (int it = 0; it < k; ++it) {
-        if (prec == DOGIP_FP64) {
-          launch_apply_cg(c, w.p64, w.q64, w.R, DOGIP_FP64, scatter, s, w);
-          c.launches += vec_cg_step(w, DOGIP_FP64, x64, c.d_dinv64, delta, s,
-                                    scatter == DOGIP_SCATTER_ATOMIC);
-        } else {
-          launch_apply_cg(c, w.p32, w.q32, w.R, DOGIP_FP32, scatter, s, w);
-          c.launches += vec_cg_step(w, DOGIP_FP32, nullptr, c.d_dinv32, delta, s,
-                                    scatter == DOGIP_SCATTER_ATOMIC);
-        }
+        if (prec == DOGIP_FP64) launch_apply_cg(c, w.p64, w.q64, w.R, DOGIP_FP64, scatter, s, w);
+        else launch_apply_cg(c, w.p32, w.q32, w.R, DOGIP_FP32, scatter, s, w);
+        c.launches += vec_cg_step(w, prec, x64, dinv, delta, s, scatter == DOGIP_SCATTER_ATOMIC);
       }
       cuda_check(cudaMemcpyAsync(w.h_flags, w.flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, s),
                  "flags copy");
@@ -671,7 +666,7 @@ void run_chunk(Ctx& c, int prec, int scatter, double* x64, int k, double delta) 
   cuda_check(cudaGraphLaunch(w.graph, s), "graph launch");
   c.launches += w.graph_kernels;
   cuda_check(cudaStreamSynchronize(s), "cg chunk");
-  if (w.h_flags[4]) fail(DOGIP_ETIMEOUT, "a bounded wait inside the apply kernel expired");
+  if (w.h_flags[4]) fail(DOGIP_ETIMEOUT, "a bounded wait inside a kernel expired");
 }
 
 void read_scal(Ctx& c) {
@@ -1148,8 +1143,8 @@ int autotune(Ctx& c, int force, cudaStream_t s) {
       cuda_check(cudaMemsetAsync(u, 0, es * c.n, s), "tuning input");
       cuda_check(cudaEventCreate(&e0), "event");
       cuda_check(cudaEventCreate(&e1), "event");
-      // staged, one thread per cell with 64 / 128 / 256 cells per CTA
-      const std::pair<int, int> cands[] = {{1, 256}, {0, 64}, {0, 128}, {0, 256}};
+      // self-feeding warps, staged, one thread per cell with 64 / 128 / 256 cells per CTA
+      const std::pair<int, int> cands[] = {{2, 256}, {1, 256}, {0, 64}, {0, 128}, {0, 256}};
       for (auto [var, blk] : cands) {
         c.apply_variant_prec[prec] = var;
         c.apply_block[prec] = blk;
@@ -1364,7 +1359,7 @@ int dogip_check(dogip_ctx* c, void* stream) {
     dogip::cuda_check(cudaStreamSynchronize(s), "stream sync");
     if (kerr) {
       dogip::cuda_check(cudaMemset(c->d_kerr, 0, sizeof(int)), "kernel flag reset");
-      fail(DOGIP_ETIMEOUT, "a bounded wait inside the apply kernel expired");
+      fail(DOGIP_ETIMEOUT, "a bounded wait inside a kernel expired");
     }
     return DOGIP_OK;
   });

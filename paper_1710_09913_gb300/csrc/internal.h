@@ -110,7 +110,7 @@ struct dogip_ctx {
   int w_cap = 0;
   int* d_err = nullptr;        // validation flags
   int* d_kerr = nullptr;       // kernel wait timeouts (bounded mbarrier waits)
-  int apply_variant = 1;       // 1: bulk-async staged apply; 0: one thread per cell
+  int apply_variant = 1;       // 2: self-feeding warps; 1: bulk-async staged; 0: one thread per cell
   bool factorized = false;     // store K_T per cell; A_T,j = w_j K_T formed in the kernel
   int apply_variant_prec[2] = {-1, -1};  // per precision (autotuner), -1: apply_variant
   int apply_block[2] = {256, 256};       // cells per CTA of the per-cell kernel

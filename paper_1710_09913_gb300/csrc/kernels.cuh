@@ -528,6 +528,173 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T, FACT>::THREADS)
   }
 }
 
+// ------------------------------------------------- self-feeding warps apply
+//
+// The same Algorithm 1 with the data movement done by each consumer warp for itself:
+// a warp processes the tiles w, w + stride, ... and streams, in order, the items of
+// each tile -- its conn tile, then its A_T in pieces of JP W nodes -- into a private
+// ring of NSLOT shared-memory slots with cp.async.bulk, LA = NSLOT - 1 items ahead.
+// A slot is rewritten only after the same warp has consumed it, so no producer warp
+// and no cross-warp barrier is needed, and a warp holds only NSLOT small pieces
+// instead of whole double-buffered tiles: 12-16 computing warps per SM instead of 8.
+// One right-hand side per launch.  Every wait is bounded by the clock budget; on
+// expiry the warp raises the error word, drains its copies in flight and stops.
+
+template <int D, int P, int FORM, typename T>
+struct SfwCfg {
+  using TB = dogip_tab::Tab<D, P, FORM>;
+  static constexpr int V = TB::V, W = TB::W, NS = NSym<D, FORM>::value;
+  static constexpr uint32_t A_TILE = W * NS * kTile * sizeof(T);
+  static constexpr uint32_t C_TILE = V * kTile * 4;
+  static constexpr uint32_t PIECE_TARGET = 3072;  // bytes of A_T per item
+  static constexpr int JP0 = (int)(PIECE_TARGET / (NS * kTile * sizeof(T)));
+  static constexpr int JP = JP0 < 1 ? 1 : (JP0 > W ? W : JP0);  // W nodes per piece
+  static constexpr int NPC = (W + JP - 1) / JP;                  // pieces per tile
+  static constexpr uint32_t PIECE = JP * NS * kTile * sizeof(T);
+  static constexpr uint32_t SLOT0 = PIECE > C_TILE ? PIECE : C_TILE;
+  static constexpr uint32_t SLOT = (SLOT0 + 127) / 128 * 128;
+  static constexpr int NSLOT = 4, LA = NSLOT - 1;
+  static constexpr uint32_t kBudget = 224 * 1024;
+  static constexpr uint32_t per_warp() { return NSLOT * (SLOT + 8); }
+  static constexpr int NW = 16 * per_warp() + 128 <= kBudget ? 16
+                            : (12 * per_warp() + 128 <= kBudget ? 12 : 8);
+  static constexpr uint32_t SMEM = NW * NSLOT * SLOT + NW * NSLOT * 8 + 128;
+  static constexpr int THREADS = NW * 32;
+  static constexpr bool OK = 8 * per_warp() + 128 <= kBudget;
+};
+
+template <int D, int P, int FORM, typename T>
+__global__ void __launch_bounds__(SfwCfg<D, P, FORM, T>::THREADS)
+    k_apply_sfw(TmaArgs<T> a) {
+  using C = SfwCfg<D, P, FORM, T>;
+  using TB = typename C::TB;
+  constexpr int V = C::V, W = C::W, NB = TB::NB, NS = C::NS, JP = C::JP, NPC = C::NPC;
+  constexpr int NSLOT = C::NSLOT, LA = C::LA, ITEMS = NPC + 1;  // items per tile
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base =
+      (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  if (a.skip != nullptr && *a.skip) return;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  unsigned char* ring = base + (size_t)warp * NSLOT * C::SLOT;
+  uint64_t* bar = (uint64_t*)(base + (size_t)C::NW * NSLOT * C::SLOT) + warp * NSLOT;
+  if (lane == 0) {
+    for (int s = 0; s < NSLOT; ++s) mbar_init(&bar[s], 1);
+    mbar_fence_init();
+  }
+  __syncwarp();
+  const int64_t w0 = (int64_t)blockIdx.x * C::NW + warp;
+  const int64_t wstride = (int64_t)gridDim.x * C::NW;
+  // item it of this warp: tile w0 + (it / ITEMS) * wstride, part it % ITEMS
+  // (0: conn tile, m >= 1: A_T piece m - 1); returns false past the last tile
+  auto issue = [&](int64_t it) -> bool {
+    const int64_t t = w0 + (it / ITEMS) * wstride;
+    if (t >= a.ntiles) return false;
+    const int m = (int)(it % ITEMS);
+    const int s = (int)(it % NSLOT);
+    if (m == 0 && t == a.test_skip_chunk) return true;  // test hook: never lands
+    const unsigned char* src;
+    uint32_t bytes;
+    if (m == 0) {
+      src = (const unsigned char*)a.conn + t * C::C_TILE;
+      bytes = C::C_TILE;
+    } else {
+      const int j0 = (m - 1) * JP;
+      const int nj = min(JP, W - j0);
+      src = (const unsigned char*)a.A + t * C::A_TILE + (size_t)j0 * NS * kTile * sizeof(T);
+      bytes = (uint32_t)nj * NS * kTile * sizeof(T);
+    }
+    fence_proxy_async_smem();
+    mbar_expect_tx(&bar[s], bytes);
+    bulk_copy_g2s(ring + (size_t)s * C::SLOT, src, bytes, &bar[s]);
+    return true;
+  };
+  int64_t issued = 0;  // items issued (or skipped by the test hook)
+  if (lane == 0)
+    for (int64_t it = 0; it < LA; ++it)
+      if (issue(it)) issued = it + 1;
+  issued = __shfl_sync(0xffffffffu, issued, 0);
+  int failed = 0;
+  int64_t it = 0;  // next item to consume
+  auto wait_item = [&](int64_t i) -> bool {
+    const int s = (int)(i % NSLOT);
+    const uint32_t parity = (uint32_t)((i / NSLOT) & 1);
+    return __any_sync(0xffffffffu, mbar_wait_bounded(&bar[s], parity, a.wait_budget) ? 0 : 1) == 0;
+  };
+  auto advance = [&]() {  // item it consumed: reuse its slot for item it + LA
+    __syncwarp();
+    int64_t n = issued;
+    if (lane == 0 && it + LA == issued && issue(it + LA)) n = issued + 1;
+    issued = __shfl_sync(0xffffffffu, n, 0);
+    ++it;
+  };
+  for (int64_t k = 0;; ++k) {
+    const int64_t t = w0 + k * wstride;
+    if (t >= a.ntiles) break;
+    const int64_t e = t * kTile + lane;
+    const bool active = e < a.E;
+    // conn tile
+    if (!wait_item(it)) { failed = 1; break; }
+    uint32_t c[V];
+    {
+      const uint32_t* sC = (const uint32_t*)(ring + (size_t)(it % NSLOT) * C::SLOT) + lane;
+      static_for<V>([&](auto lc) {
+        constexpr int l = decltype(lc)::value;
+        c[l] = active ? sC[l * kTile] : kBndBit;
+      });
+    }
+    advance();
+    T ul[V], Y[V];
+    static_for<V>([&](auto lc) {
+      constexpr int l = decltype(lc)::value;
+      ul[l] = (c[l] & kBndBit) ? T(0) : __ldg(a.u + (int64_t)(c[l] & kIdMask));
+      if constexpr (col_empty<TB>(l)) Y[l] = T(0);
+    });
+    static_for<NPC>([&](auto pc) {
+      constexpr int pcv = decltype(pc)::value;
+      if (failed) return;
+      if (!wait_item(it)) {
+        failed = 1;
+        return;
+      }
+      const T* sA = (const T*)(ring + (size_t)(it % NSLOT) * C::SLOT) + lane;
+      static_for<JP>([&](auto jc) {
+        constexpr int jj = decltype(jc)::value;
+        constexpr int j = pcv * JP + jj;
+        if constexpr (j < W) {
+          T g[NB], h[NB], aj[NS];
+          static_for<NS>([&](auto kc) {
+            constexpr int kk = decltype(kc)::value;
+            aj[kk] = sA[(jj * NS + kk) * kTile];
+          });
+          interp<TB, j>(ul, g);
+          block_mul<D, FORM>(aj, g, h);
+          project<TB, j>(h, Y);
+        }
+      });
+      advance();
+    });
+    if (failed) break;
+    if (active) {
+      static_for<V>([&](auto lc) {
+        constexpr int l = decltype(lc)::value;
+        if (!(c[l] & kBndBit)) atomicAdd(a.y + (int64_t)(c[l] & kIdMask), Y[l]);
+      });
+    }
+  }
+  // drain (bounded): copies issued and not consumed
+  for (int64_t i = it; i < issued; ++i) {
+    const int s = (int)(i % NSLOT);
+    if (lane == 0) mbar_wait_bounded(&bar[s], (uint32_t)((i / NSLOT) & 1), a.wait_budget);
+  }
+  if (failed && lane == 0) atomicOr(a.err, 1);
+  __syncthreads();
+  // Dirichlet rows: y_b = u_b (the scatter skipped them)
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + tid; q < a.nbnd; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t idx = a.bnd[q];
+    a.y[idx] = a.u[idx];
+  }
+}
+
 // ------------------------------------------------------------------ setup
 
 struct AhatArgs {
