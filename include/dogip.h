@@ -35,6 +35,14 @@
  *  - Local node order of P_q on the reference simplex: multi-indices alpha,
  *    |alpha| <= q, in lexicographic order with the last coordinate fastest;
  *    node alpha sits at sum_i (alpha_i / q) (v_i - v_0) + v_0.
+ *
+ * Environment variables read by dogip_setup (none is required):
+ *  - DOGIP_APPLY_VARIANT: apply kernel until dogip_autotune decides (2 self-feeding
+ *    warps, 1 staged kernel (default), 0 one thread per cell).
+ *  - DOGIP_TUNE_CACHE: file of autotuner choices (see dogip_autotune).
+ *  - DOGIP_TEST_WAIT_CYCLES, DOGIP_TEST_SKIP_CHUNK: test hooks of the device-side
+ *    failure path (a shorter bound on the kernels' waits, and one chunk of the
+ *    staged apply whose copy is never issued, so that its bounded wait expires).
  */
 #ifndef DOGIP_H
 #define DOGIP_H
@@ -313,16 +321,19 @@ DOGIP_API int dogip_solve_host(dogip_ctx* ctx, const double* b_host, double* u_h
 
 /* --------------------------------------------------------------- autotuner */
 typedef struct {
-  int variant[2]; /* per precision (index DOGIP_FP64 / DOGIP_FP32): 1 staged kernel,
-                     0 one thread per cell                                    */
+  int variant[2]; /* per precision (index DOGIP_FP64 / DOGIP_FP32): 2 self-feeding
+                     warps, 1 staged producer/consumer kernel, 0 one thread per
+                     cell                                                      */
   int block[2];   /* cells per CTA of the one-thread-per-cell kernel          */
 } dogip_tune_info;
 
 /*
  * Choose the apply kernel of this context per precision by timing the candidates
- * on its own data: the bulk-async staged kernel, and the one-thread-per-cell kernel
- * with 64, 128 or 256 cells per CTA (median of 5 CUDA-event timings after 2 warm-up
- * applies, atomic scatter, one right-hand side).  Choices are cached for the process
+ * on its own data: the self-feeding-warps kernel, the bulk-async staged kernel, and
+ * the one-thread-per-cell kernel with 64, 128 or 256 cells per CTA (median of 5
+ * CUDA-event timings after 2 warm-up applies, atomic scatter, one right-hand side).
+ * Applies with several right-hand sides use the staged kernel where it exists
+ * (FP32 with nrhs a multiple of 4 and V_T <= 10 always), and the choice otherwise.  Choices are cached for the process
  * per (dim, p, form, precision, log2 cells) and reused without timing unless
  * force != 0; the environment variable DOGIP_TUNE_CACHE names a text file the cache
  * is read from and appended to.  Allocates two temporary vectors (stream-ordered)
