@@ -152,6 +152,33 @@ def measured_peaks():
 _ORACLE_CACHE = {}
 
 
+def host_info():
+    """CPU model and logical core count of this host, as measured."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "processor name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        try:  # aarch64 /proc/cpuinfo carries no model name; lscpu decodes the part ids
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    if model is None:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"cpu_model": model, "host_cores": os.cpu_count()}
+
+
 def oracle_sample(coords, cells, A, p_list, inner_iters):
     """The FP64 CPU oracle, as it stands, on a bounded sample of the workload: for
     every p, one refinement step with `inner_iters` emulated-FP32 PCG iterations.
@@ -207,7 +234,7 @@ def run_reference(args):
             "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64/f32 (numpy)", "data": "synthetic",
             "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": value, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {**host_info(), "value": value, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": value, "unit": "GDoF/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -807,7 +834,8 @@ def main():
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         w, s, desc = oracle_sample(coords, cells, A, P_LIST, 1)
-        cpu = {"value": w / s / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle", "sample": desc}
+        cpu = {"value": w / s / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle", "sample": desc,
+               **host_info()}
 
     _section("done")
     if rank == 0:
