@@ -206,6 +206,27 @@ DOGIP_API int dogip_get_ahat(const dogip_ctx* ctx, double* dev_out, void* cuda_s
 /* Jacobi diagonal of the operator (1 on Dirichlet rows): device [n_dofs]. Async. */
 DOGIP_API int dogip_get_diag(const dogip_ctx* ctx, double* dev_out, void* cuda_stream);
 
+/*
+ * Host-only mesh preprocessing (no CUDA call, no context; the routines dogip_setup
+ * uses).  cells: host int32 [n_cells x (dim+1)] vertex ids >= 0.
+ *  dogip_mesh_dofmap : ids [n_cells x V_T] (may be NULL) and the dof count of the
+ *                      continuous P_p space, numbered by first appearance (§2.1).
+ *  dogip_mesh_boundary: mask [n_dofs], 1 on the dofs of facets of one cell.
+ *  dogip_mesh_colouring: greedy cell colouring, cells in order, smallest colour not
+ *                      used by an earlier cell sharing a vertex; colour [n_cells].
+ *  dogip_mesh_wdofmap: the W nodes of order 2p (global double grid): ids
+ *                      [n_cells x W_T], owner flags [n_cells x W_T], count.
+ * Errors: DOGIP_EINVAL (dim, p outside 1..16, empty or negative ids).
+ */
+DOGIP_API int dogip_mesh_dofmap(int dim, int p, int64_t n_cells, const int32_t* cells,
+                                int32_t* ids, int64_t* n_dofs);
+DOGIP_API int dogip_mesh_boundary(int dim, int p, int64_t n_cells, const int32_t* cells,
+                                  uint8_t* mask);
+DOGIP_API int dogip_mesh_colouring(int dim, int64_t n_cells, const int32_t* cells,
+                                   int32_t* colour, int* n_colours);
+DOGIP_API int dogip_mesh_wdofmap(int dim, int p, int64_t n_cells, const int32_t* cells,
+                                 int32_t* ids, uint8_t* owner, int64_t* n_w);
+
 /* Global double grid only (global_w = 1):
  * A_diag: device double [n_W] (n_W = info.n_wglobal).  Async.
  * W-node map: host int32 [n_cells x W_T] global W-node ids (first appearance,

@@ -96,6 +96,10 @@ _SIGS = {
     "dogip_get_ahat": (C.c_int, [_vp, _vp, _vp]),
     "dogip_get_diag": (C.c_int, [_vp, _vp, _vp]),
     "dogip_get_ahat_global": (C.c_int, [_vp, _vp, _vp]),
+    "dogip_mesh_dofmap": (C.c_int, [C.c_int, C.c_int, C.c_int64, _vp, _vp, _vp]),
+    "dogip_mesh_boundary": (C.c_int, [C.c_int, C.c_int, C.c_int64, _vp, _vp]),
+    "dogip_mesh_colouring": (C.c_int, [C.c_int, C.c_int64, _vp, _vp, _vp]),
+    "dogip_mesh_wdofmap": (C.c_int, [C.c_int, C.c_int, C.c_int64, _vp, _vp, _vp, _vp]),
     "dogip_get_wdofmap": (C.c_int, [_vp, _vp, _vp]),
     "dogip_get_tables": (C.c_int, [C.c_int, C.c_int, C.c_int, _vp, _vp, _vp]),
     "dogip_apply": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp]),
@@ -180,6 +184,59 @@ def batch_solve(ctxs, bs, us, *, mode="mixed", tol=1e-8, check_every=None, inner
     _check(code, allow=(ENOTCONV,))
     return [dict(status=i.status, iterations=i.iterations, outer=i.outer,
                  rel_residual=i.rel_residual, seconds=i.seconds) for i in infos]
+
+
+def _cells(cells):
+    cells = np.ascontiguousarray(cells, dtype=np.int32)
+    return cells, cells.shape[1] - 1, cells.shape[0]
+
+
+def mesh_dofmap(cells, p):
+    """(ids [E, V_T] int32, n_dofs): first-appearance numbering (host, no GPU)."""
+    cells, d, E = _cells(cells)
+    n = C.c_int64()
+    _check(lib.dogip_mesh_dofmap(d, int(p), E, cells.ctypes.data_as(_vp), None, C.byref(n)))
+    V = len(_multi(d, p))
+    ids = np.zeros((E, V), dtype=np.int32)
+    _check(lib.dogip_mesh_dofmap(d, int(p), E, cells.ctypes.data_as(_vp), ids.ctypes.data_as(_vp),
+                                 C.byref(n)))
+    return ids, n.value
+
+
+def mesh_boundary(cells, p):
+    """Dirichlet boundary mask [n_dofs] bool (host, no GPU)."""
+    cells, d, E = _cells(cells)
+    _, n = mesh_dofmap(cells, p)
+    mask = np.zeros(n, dtype=np.uint8)
+    _check(lib.dogip_mesh_boundary(d, int(p), E, cells.ctypes.data_as(_vp), mask.ctypes.data_as(_vp)))
+    return mask.astype(bool)
+
+
+def mesh_colouring(cells):
+    """(colour [E] int32, n_colours) of the greedy cell colouring (host, no GPU)."""
+    cells, d, E = _cells(cells)
+    col = np.zeros(E, dtype=np.int32)
+    nc = C.c_int()
+    _check(lib.dogip_mesh_colouring(d, E, cells.ctypes.data_as(_vp), col.ctypes.data_as(_vp),
+                                    C.byref(nc)))
+    return col, nc.value
+
+
+def mesh_wdofmap(cells, p):
+    """(W ids [E, W_T], owner flags [E, W_T] bool, n_W) of order 2p (host, no GPU)."""
+    cells, d, E = _cells(cells)
+    WT = len(_multi(d, 2 * p))
+    ids = np.zeros((E, WT), dtype=np.int32)
+    own = np.zeros((E, WT), dtype=np.uint8)
+    n = C.c_int64()
+    _check(lib.dogip_mesh_wdofmap(d, int(p), E, cells.ctypes.data_as(_vp), ids.ctypes.data_as(_vp),
+                                  own.ctypes.data_as(_vp), C.byref(n)))
+    return ids, own.astype(bool), n.value
+
+
+def _multi(d, q):
+    from math import comb
+    return range(comb(q + d, d))
 
 
 def get_tables(dim, p, form):

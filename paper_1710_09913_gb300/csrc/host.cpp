@@ -1291,6 +1291,75 @@ int dogip_get_info(const dogip_ctx* c, dogip_info* i) {
 
 int64_t dogip_ndofs(const dogip_ctx* c) { return c ? c->n : -1; }
 
+// Host-only mesh preprocessing (no CUDA call): the same routines the set-up uses.
+namespace {
+dogip::Ctx host_ctx(int dim, int p, int64_t n_cells, const int32_t* cells) {
+  if (dim != 2 && dim != 3) dogip::fail(DOGIP_EINVAL, "dim must be 2 or 3");
+  if (p < 1 || p > 16) dogip::fail(DOGIP_EINVAL, "p must be in 1..16");
+  if (n_cells <= 0 || !cells) dogip::fail(DOGIP_EINVAL, "cells are required");
+  int64_t nv = 0;
+  for (int64_t k = 0; k < n_cells * (dim + 1); ++k) {
+    if (cells[k] < 0) dogip::fail(DOGIP_EINVAL, "negative vertex id");
+    nv = std::max<int64_t>(nv, (int64_t)cells[k] + 1);
+  }
+  dogip::Ctx c;
+  c.d = dim;
+  c.p = p;
+  c.E = n_cells;
+  c.nv = nv;
+  c.VT = (int)dogip::local_betas(dim, p).size();
+  c.dirichlet = true;
+  return c;
+}
+}  // namespace
+
+int dogip_mesh_dofmap(int dim, int p, int64_t n_cells, const int32_t* cells, int32_t* ids,
+                      int64_t* n_dofs) {
+  return guarded([&] {
+    dogip::Ctx c = host_ctx(dim, p, n_cells, cells);
+    dogip::build_dofmap(c, cells);
+    if (ids) std::memcpy(ids, c.dofmap.data(), sizeof(int32_t) * c.dofmap.size());
+    if (n_dofs) *n_dofs = c.n;
+    return DOGIP_OK;
+  });
+}
+
+int dogip_mesh_boundary(int dim, int p, int64_t n_cells, const int32_t* cells, uint8_t* mask) {
+  return guarded([&] {
+    if (!mask) dogip::fail(DOGIP_EINVAL, "mask is required");
+    dogip::Ctx c = host_ctx(dim, p, n_cells, cells);
+    dogip::build_dofmap(c, cells);
+    dogip::build_boundary(c, cells);
+    std::memcpy(mask, c.bmask.data(), c.bmask.size());
+    return DOGIP_OK;
+  });
+}
+
+int dogip_mesh_colouring(int dim, int64_t n_cells, const int32_t* cells, int32_t* colour,
+                         int* n_colours) {
+  return guarded([&] {
+    dogip::Ctx c = host_ctx(dim, 1, n_cells, cells);
+    dogip::build_colouring(c, cells);
+    if (colour) std::memcpy(colour, c.colour.data(), sizeof(int32_t) * c.colour.size());
+    if (n_colours) *n_colours = c.ncolours;
+    return DOGIP_OK;
+  });
+}
+
+int dogip_mesh_wdofmap(int dim, int p, int64_t n_cells, const int32_t* cells, int32_t* ids,
+                       uint8_t* owner, int64_t* n_w) {
+  return guarded([&] {
+    dogip::Ctx c = host_ctx(dim, p, n_cells, cells);
+    std::vector<int32_t> w;
+    std::vector<uint8_t> first;
+    const int64_t n = dogip::number_nodes(dim, 2 * p, n_cells, cells, w, &first);
+    if (ids) std::memcpy(ids, w.data(), sizeof(int32_t) * w.size());
+    if (owner) std::memcpy(owner, first.data(), first.size());
+    if (n_w) *n_w = n;
+    return DOGIP_OK;
+  });
+}
+
 int dogip_get_dofmap(const dogip_ctx* c, int32_t* out) {
   return guarded([&] {
     if (!c || !out) fail(DOGIP_EINVAL, "ctx and output are required");
