@@ -111,10 +111,13 @@ __device__ __forceinline__ void set_all_done(const Red& rd, int R) {
   *rd.counter = 0u;
 }
 
-// Two CTAs of 256 threads per SM (152 SMs), at least 8 elements per thread.
+// CTAs of 256 threads with at least 8 elements per thread: two per SM (152 SMs) for
+// vectors that stay in L2 between the kernels of an iteration, four per SM (more
+// bytes in flight) from 2^21 entries on, where they stream from HBM.
 unsigned red_blocks(int64_t N) {
   int64_t b = (N + 8 * kRedThreads - 1) / (8 * kRedThreads);
-  if (b > 2 * 152) b = 2 * 152;
+  const int64_t cap = N >= (int64_t(1) << 21) ? 4 * 152 : 2 * 152;
+  if (b > cap) b = cap;
   if (b < 1) b = 1;
   return (unsigned)b;
 }
