@@ -64,7 +64,11 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # raw samples: a directory named by DOGIP_BENCH_CLOCKS_DIR, else a temporary one
+        # (the JSON line carries their summary)
+        import tempfile
+        d = os.environ.get("DOGIP_BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"dogip_clocks_rank{index}.csv")
 
     def __enter__(self):
         try:
