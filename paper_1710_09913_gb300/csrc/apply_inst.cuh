@@ -115,6 +115,7 @@ int run_apply(const Ctx& c, const void* u, void* y, int R, int prec, bool atomic
       if constexpr (ok32) tma_launch<D, P, FORM, float, false>();
       if constexpr (SfwCfg<D, P, FORM, double>::OK) sfw_launch<D, P, FORM, double>();
       if constexpr (SfwCfg<D, P, FORM, float>::OK) sfw_launch<D, P, FORM, float>();
+      if (c.keep32) apply_tc(c, nullptr, nullptr, nullptr, nullptr);
     }
     return 1;
   }
@@ -123,8 +124,11 @@ int run_apply(const Ctx& c, const void* u, void* y, int R, int prec, bool atomic
     else run_apply_tma<D, P, FORM, float, true>(c.d_A32, c, u, y, R, s, skip);
     return 2;
   }
-  // variant: 2 self-feeding warps, 1 staged, 0 one thread per cell
+  // variant: 3 tensor cores (FP32), 2 self-feeding warps, 1 staged, 0 one thread per cell
   const int var = c.apply_variant_prec[prec] >= 0 ? c.apply_variant_prec[prec] : c.apply_variant;
+  if (var == 3 && prec == DOGIP_FP32 && R == 1 && atomic && e0 == 0 && e1 == c.E &&
+      apply_tc(c, u, y, s, skip))
+    return 2;
   if (var == 2 && R == 1 && atomic && e0 == 0 && e1 == c.E) {
     if (prec == DOGIP_FP64) {
       if constexpr (SfwCfg<D, P, FORM, double>::OK) {

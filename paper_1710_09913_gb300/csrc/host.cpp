@@ -1143,9 +1143,12 @@ int autotune(Ctx& c, int force, cudaStream_t s) {
       cuda_check(cudaMemsetAsync(u, 0, es * c.n, s), "tuning input");
       cuda_check(cudaEventCreate(&e0), "event");
       cuda_check(cudaEventCreate(&e1), "event");
-      // self-feeding warps, staged, one thread per cell with 64 / 128 / 256 cells per CTA
-      const std::pair<int, int> cands[] = {{2, 256}, {1, 256}, {0, 64}, {0, 128}, {0, 256}};
+      // tensor cores (FP32), self-feeding warps, staged, one thread per cell with
+      // 64 / 128 / 256 cells per CTA
+      const std::pair<int, int> cands[] = {{3, 256}, {2, 256}, {1, 256},
+                                           {0, 64},  {0, 128}, {0, 256}};
       for (auto [var, blk] : cands) {
+        if (var == 3 && (prec != DOGIP_FP32 || !apply_tc_available(c.d, c.p, c.form))) continue;
         c.apply_variant_prec[prec] = var;
         c.apply_block[prec] = blk;
         for (int w = 0; w < 2; ++w) launch_apply(c, u, y, 1, prec, DOGIP_SCATTER_ATOMIC, s, nullptr);

@@ -110,7 +110,7 @@ struct dogip_ctx {
   int w_cap = 0;
   int* d_err = nullptr;        // validation flags
   int* d_kerr = nullptr;       // kernel wait timeouts (bounded mbarrier waits)
-  int apply_variant = 1;       // 2: self-feeding warps; 1: bulk-async staged; 0: one thread per cell
+  int apply_variant = 1;       // 3: tensor cores (FP32); 2: self-feeding warps; 1: bulk-async staged; 0: one thread per cell
   bool factorized = false;     // store K_T per cell; A_T,j = w_j K_T formed in the kernel
   int apply_variant_prec[2] = {-1, -1};  // per precision (autotuner), -1: apply_variant
   int apply_block[2] = {256, 256};       // cells per CTA of the per-cell kernel
@@ -172,6 +172,11 @@ bool load_hi(const Ctx& c, LoadArgs& a, cudaStream_t s);
 bool hi_table(int d, int p, int form, int* NB, int* W, int* V, long long* nnz, long long* nnz1,
               const double** B, const double** w, const double** iv);
 bool table_is_compiled(int d, int p, int form);
+// Tensor-core FP32 apply (apply_tc.cu): one right-hand side, atomic scatter over the
+// whole cell range.  false when no instance exists for (d, p, form); u == nullptr
+// only sets the kernel attributes (context set-up).
+bool apply_tc(const Ctx& c, const void* u, void* y, cudaStream_t s, const int* skip);
+bool apply_tc_available(int d, int p, int form);
 // Global double-grid apply of the weighted projection (two kernels); false when no
 // instance exists.  The scratch must hold R right-hand sides (ensure_w_scratch).
 bool apply_gw(const Ctx& c, const void* u, void* y, int R, int prec, cudaStream_t s,

@@ -1,0 +1,117 @@
+// tcgen05 (5th-generation tensor core) helpers for sm_100-family GPUs: tensor-memory
+// allocation, shared-memory matrix descriptors, single-CTA MMA issue with an mbarrier
+// commit, tensor-memory loads, and the TF32 hi/lo operand split.
+//
+// Operand layout used throughout ("K-major, no swizzle"): a matrix of R rows (M or N,
+// a multiple of 8) and K columns (a multiple of 8, 32-bit elements) is stored as core
+// matrices of 8 rows x 16 bytes (8 x 4 elements, 128 contiguous bytes).  Core matrices
+// adjacent along the rows are 128 bytes apart (stride byte offset), those adjacent
+// along K are R/8 * 128 bytes apart (leading byte offset):
+//   byte(row, k) = ((k / 4) * (R / 8) + row / 8) * 128 + (row % 8) * 16 + (k % 4) * 4.
+// One kind::tf32 MMA consumes K = 8, i.e. two core-matrix columns; its operand starts
+// at 2 * (R / 8) * 128 bytes per k-step.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace dogip {
+namespace tc {
+
+__host__ __device__ constexpr uint32_t op_off(int R, int row, int k) {
+  return (uint32_t)((((k >> 2) * (R >> 3) + (row >> 3)) << 7) + ((row & 7) << 4) + ((k & 3) << 2));
+}
+__host__ __device__ constexpr uint32_t op_lbo(int R) { return (uint32_t)((R >> 3) << 7); }
+__host__ __device__ constexpr uint32_t op_kstep(int R) { return 2u * op_lbo(R); }
+
+// Shared-memory matrix descriptor (tcgen05 format): start address, leading and
+// stride byte offsets (all >> 4), descriptor version 1, base offset 0, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::tf32 with FP32 accumulation, both operands
+// K-major: D format F32 (bits 4-5 = 1), A and B format TF32 (bits 7-9, 10-12 = 2),
+// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+// Tensor-memory allocation of `ncols` columns (a power of two >= 32) by one whole
+// warp; the base address is written to shared memory at `slot`.
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void fence_before_sync() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after_sync() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, issued by one thread.
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Arrive once on the mbarrier when every MMA issued so far by this thread completed.
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          (uint32_t)__cvta_generic_to_shared(bar))
+      : "memory");
+}
+
+// 16 consecutive 32-bit columns of this thread's tensor-memory lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// x = hi + lo with hi rounded to TF32 (nearest, ties away from zero: the 13 low
+// mantissa bits cleared after adding half of their range) and lo = x - hi exact in
+// FP32.  The tensor core reads lo truncated to TF32, so hi + lo carries about 21 bits.
+__device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
+  hi = __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+  lo = x - hi;
+}
+
+// Bar.sync on a named barrier among `n` threads, OR-reducing a predicate.
+__device__ __forceinline__ int bar_or(int id, int n, int pred) {
+  int out;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.s32 q, %1, 0;\n bar.red.or.pred p, %2, %3, q;\n"
+      " selp.s32 %0, 1, 0, p;\n}\n"
+      : "=r"(out)
+      : "r"(pred), "r"(id), "r"(n)
+      : "memory");
+  return out;
+}
+
+}  // namespace tc
+}  // namespace dogip

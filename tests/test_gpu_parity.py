@@ -444,13 +444,14 @@ def test_subelement_constant_field_equals_elementwise(B):
     np.testing.assert_allclose(a.diag().cpu().numpy(), b.diag().cpu().numpy(), rtol=1e-13)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 @pytest.mark.parametrize("d,p,form", [(2, 1, "elliptic"), (2, 4, "elliptic"), (2, 3, "projection"),
                                       (3, 2, "elliptic"), (3, 3, "projection")])
 def test_apply_variants_parity(B, d, p, form, variant, monkeypatch):
     """Each apply kernel the autotuner can choose — one thread per cell (0), the staged
-    producer/consumer ring (1), self-feeding warps (2) — matches the oracle on its own,
-    FP64 and FP32, one right-hand side."""
+    producer/consumer ring (1), self-feeding warps (2), tensor cores (3, FP32; the
+    staged kernel serves FP64 and instances without a tensor-core kernel) — matches
+    the oracle on its own, FP64 and FP32, one right-hand side."""
     monkeypatch.setenv("DOGIP_APPLY_VARIANT", str(variant))
     ctx, P = make(B, d, p, form, NSMALL[d])
     u = inputs.rhs_normal(P.n, 1, seed=31)[:, 0]
