@@ -687,6 +687,47 @@ def main():
         fact[f"P{p}"] = out
         del cf
 
+    _section("tensor_core")
+    # the tcgen05 kernel (3xTF32 contractions in tensor memory), forced for FP32 applies
+    # on contexts of its own: the autotuner times it beside the CUDA-core kernels
+    tcore = {}
+    os.environ["DOGIP_APPLY_VARIANT"] = "3"
+    try:
+        for p in P_LIST:
+            ct = B.Context(coords, cells, p, "elliptic", A)
+            u = torch.randn(ct.n, dtype=torch.float32, device="cuda")
+            y = torch.empty_like(u)
+            for _ in range(3):
+                ct.apply(u, y, prec="fp32")
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(20):
+                ct.apply(u, y, prec="fp32")
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1) / 20
+            inf = ct.info
+            byt = E * inf.w_loc * inf.n_sym * 4 + E * inf.v_loc * 4 + 2 * ct.n * 4
+            out = {"apply_fp32_ms": round(ms, 4), "apply_fp32_GBps": round(byt / ms / 1e6, 1),
+                   "vs_autotuned_fp32": round(applies[f"P{p}_fp32"]["ms"] / ms, 3)}
+            if p == max(P_LIST):
+                b = ct.load()
+                ux = torch.zeros_like(b)
+                torch.cuda.synchronize()
+                ev0.record(stream)
+                _, info = ct.solve(b, ux, mode="mixed", tol=TOL, check_every=args.check_every)
+                ev1.record(stream)
+                torch.cuda.synchronize()
+                out["mixed_ms"] = round(ev0.elapsed_time(ev1), 2)
+                out["mixed_iters"] = info["iterations"]
+            ct.check()
+            tcore[f"P{p}"] = out
+            del ct
+    finally:
+        del os.environ["DOGIP_APPLY_VARIANT"]
+
     _section("qp")
     # the conventional quadrature-point matrix-free apply on the same GPU (comparator):
     # geometry from the vertex coordinates at every apply, the cell's coefficient, and
@@ -857,6 +898,7 @@ def main():
                 "time_to_tol": t2t, "apply": applies, "csr_baseline": csr, "batch_uneven": batch,
                 "cube_p2_16rhs": multi, "factorized": fact, "quadrature_point_comparator": qp,
                 "global_double_grid_projection": gw, "high_order": hi_ord,
+                "tensor_core_apply": tcore,
                 "roofline": roofline,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks}
         print(json.dumps(line), flush=True)

@@ -28,25 +28,32 @@ struct TcCfg {
   using TB = dogip_tab::Tab<D, P, FORM>;
   static constexpr int V = TB::V, W = TB::W, NB = TB::NB, NS = NSym<D, FORM>::value;
   static constexpr int NC = NB * W;
-  static constexpr int M = 128, TPC = 4;  // cells per MMA tile; consumer warps (one tile each)
+  static constexpr int M = 128;  // cells per MMA tile (one per thread of a warpgroup)
   static constexpr int K1 = (V + 7) / 8 * 8, N1 = (NC + 15) / 16 * 16;
   static constexpr int K2 = (NC + 7) / 8 * 8, N2 = (V + 15) / 16 * 16;
-  static constexpr uint32_t TMC = (N1 + N2) <= 32 ? 32u
-                                  : (N1 + N2) <= 64 ? 64u
-                                  : (N1 + N2) <= 128 ? 128u
-                                  : (N1 + N2) <= 256 ? 256u
-                                                     : 512u;
-  // operand buffers, hi and lo halves of each
-  static constexpr uint32_t A1B = M * K1 * 4, A2B = M * K2 * 4, B1B = N1 * K1 * 4, B2B = N2 * K2 * 4;
-  static constexpr uint32_t OPS = 2 * (A1B + A2B + B1B + B2B);
-  static constexpr uint32_t A_TILE = W * NS * kTile * 4, C_TILE = V * kTile * 4;
-  static constexpr uint32_t CHUNK = TPC * (A_TILE + C_TILE), PRO = TPC * C_TILE;
+  // shared memory: the split tables (per CTA); per warpgroup the A1 operand (hi, lo)
+  // and one stage of A^_T for its 128 cells (four AoSoA tiles, one bulk copy)
+  static constexpr uint32_t BTAB = 2 * (N1 * K1 + N2 * K2) * 4;
+  static constexpr uint32_t A_TILE = W * NS * kTile * 4;
+  static constexpr uint32_t WGB = 2 * M * K1 * 4 + 4 * A_TILE;
   static constexpr uint32_t kBudget = 224 * 1024;
-  static constexpr int S0 = (int)(((long)kBudget - OPS - PRO - 256) / CHUNK);
-  static constexpr int S = S0 > 4 ? 4 : S0;
-  static constexpr bool OK = S >= 2 && N1 <= 256 && N1 + N2 <= 512;
-  static constexpr uint32_t SMEM = OPS + (S < 2 ? 2 : S) * CHUNK + PRO + 256 + 1024;
-  static constexpr int THREADS = (TPC + 1) * 32;
+  // tensor memory per warpgroup: D1 = G (its columns then hold the hi part of H, the
+  // A operand of GEMM 2), the lo part of H, and D2 = Y
+  static constexpr int TMW = 2 * N1 + N2;
+  static constexpr int NWG0 = (int)(((long)kBudget - BTAB - 256) / WGB);
+  static constexpr int NWG1 = NWG0 > 4 ? 4 : NWG0;
+  static constexpr int NWG = NWG1 * TMW > 512 ? 512 / TMW : NWG1;  // warpgroups per CTA
+  static constexpr uint32_t TMC = NWG * TMW <= 32 ? 32u
+                                  : NWG * TMW <= 64 ? 64u
+                                  : NWG * TMW <= 128 ? 128u
+                                  : NWG * TMW <= 256 ? 256u
+                                                     : 512u;
+  // D1 columns are read 16 at a time, and a W node's NB values may not straddle two
+  // reads: NB = 3 (3D elliptic) reads all N1 <= 32 columns at once
+  static constexpr int CH = NB == 3 ? N1 : 16;
+  static constexpr bool OK = NWG >= 1 && N1 <= 256 && (NB != 3 || N1 <= 32);
+  static constexpr uint32_t SMEM = BTAB + (NWG < 1 ? 1 : NWG) * WGB + 256 + 1024;
+  static constexpr int THREADS = (NWG < 1 ? 1 : NWG) * M;
 };
 
 // B1 and B2 in the operand layout of tc.cuh (FP32; split into hi + lo in the kernel):
@@ -79,37 +86,26 @@ template <int D, int P, int FORM>
 __global__ void __launch_bounds__(TcCfg<D, P, FORM>::THREADS, 1) k_apply_tc(TmaArgs<float> a) {
   using C = TcCfg<D, P, FORM>;
   static_assert(C::OK, "tensor-core apply does not fit in shared / tensor memory");
-  constexpr int V = C::V, W = C::W, NB = C::NB, NS = C::NS, NC = C::NC, M = C::M;
-  constexpr int K1 = C::K1, N1 = C::N1, K2 = C::K2, N2 = C::N2, S = C::S, TPC = C::TPC;
+  constexpr int V = C::V, W = C::W, NB = C::NB, NS = C::NS, M = C::M;
+  constexpr int K1 = C::K1, N1 = C::N1, K2 = C::K2, N2 = C::N2, NWG = C::NWG, CH = C::CH;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  float* a1h = (float*)base;
-  float* a1l = a1h + M * K1;
-  float* a2h = a1l + M * K1;
-  float* a2l = a2h + M * K2;
-  float* b1h = a2l + M * K2;
+  float* b1h = (float*)base;
   float* b1l = b1h + N1 * K1;
   float* b2h = b1l + N1 * K1;
   float* b2l = b2h + N2 * K2;
-  unsigned char* ring = base + C::OPS;
-  unsigned char* pro_buf = ring + S * C::CHUNK;  // conn of the first chunk
-  uint64_t* full = (uint64_t*)(pro_buf + C::PRO);
-  uint64_t* empty = full + S;
-  uint64_t* pro = empty + S;
-  uint64_t* mma1 = pro + 1;
-  uint64_t* mma2 = mma1 + 1;
-  uint32_t* tslot = (uint32_t*)(mma2 + 1);
+  uint64_t* bars = (uint64_t*)(base + C::BTAB + NWG * C::WGB);  // [NWG][3]
+  uint32_t* tslot = (uint32_t*)(bars + 3 * NWG);
   if (a.skip != nullptr && *a.skip) return;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t G = gridDim.x, k0 = blockIdx.x;
+  const int tid = threadIdx.x, wg = tid / M, m = tid % M, warp = m >> 5, lane = tid & 31;
+  float* a1h = (float*)(base + C::BTAB + wg * C::WGB);
+  float* a1l = a1h + M * K1;
+  unsigned char* stA = (unsigned char*)(a1l + M * K1);  // A^_T of the warpgroup's tile
+  uint64_t* mma1 = bars + 3 * wg;
+  uint64_t* mma2 = mma1 + 1;
+  uint64_t* abar = mma1 + 2;
   if (tid == 0) {
-    for (int s = 0; s < S; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], TPC);
-    }
-    mbar_init(pro, 1);
-    mbar_init(mma1, 1);
-    mbar_init(mma2, 1);
+    for (int g = 0; g < 3 * NWG; ++g) mbar_init(&bars[g], 1);
     mbar_fence_init();
   }
   {  // reference tables -> shared memory, split into TF32 hi + lo
@@ -118,239 +114,198 @@ __global__ void __launch_bounds__(TcCfg<D, P, FORM>::THREADS, 1) k_apply_tc(TmaA
     for (int i = tid; i < N2 * K2; i += C::THREADS) tc::split_tf32(tab.b2[i], b2h[i], b2l[i]);
   }
   __syncwarp();
-  if (warp == 0) tc::tmem_alloc(tslot, C::TMC);
+  if (tid < 32) tc::tmem_alloc(tslot, C::TMC);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tslot;
+  // this warpgroup's tensor-memory columns and this warp's lanes
+  const uint32_t d1 = tmem + (uint32_t)(wg * C::TMW);  // G, then the hi part of H
+  const uint32_t hlo = d1 + (uint32_t)N1;              // lo part of H
+  const uint32_t d2 = d1 + (uint32_t)(2 * N1);         // Y
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const uint32_t s_a1h = smem_addr(a1h), s_a1l = smem_addr(a1l);
+  const uint32_t s_b1h = smem_addr(b1h), s_b1l = smem_addr(b1l);
+  const uint32_t s_b2h = smem_addr(b2h), s_b2l = smem_addr(b2l);
 
-  if (warp == TPC) {
-    // ---- producer warp: stage s of chunk k receives the A^ tiles of k and the conn
-    // tiles of k + G (this CTA's next chunk).
-    if (lane == 0) {
-      int failed = 0;
-      int64_t issued = 0;
-      const bool pro_issued = k0 < a.nchunks;
-      if (pro_issued) {
-        const int nt0 = (int)min((int64_t)TPC, a.ntiles - k0 * TPC);
-        mbar_expect_tx(pro, (uint32_t)nt0 * C::C_TILE);
-        bulk_copy_g2s(pro_buf, (const unsigned char*)a.conn + k0 * TPC * C::C_TILE,
-                      (uint32_t)nt0 * C::C_TILE, pro);
-      }
-      for (int64_t i = 0;; ++i) {
-        const int64_t k = k0 + i * G;
-        if (k >= a.nchunks) break;
-        const int s = (int)(i % S);
-        if (i >= S && !mbar_wait_bounded(&empty[s], (uint32_t)(((i / S) - 1) & 1), a.wait_budget)) {
-          failed = 1;
-          break;
-        }
-        fence_proxy_async_smem();
-        issued = i + 1;
-        const int64_t t0 = k * TPC, kn = k + G;
-        const int nt = (int)min((int64_t)TPC, a.ntiles - t0);
-        const int ntn = kn < a.nchunks ? (int)min((int64_t)TPC, a.ntiles - kn * TPC) : 0;
-        unsigned char* sa = ring + (size_t)s * C::CHUNK;
-        unsigned char* sc = sa + TPC * C::A_TILE;
-        mbar_expect_tx(&full[s], (uint32_t)nt * C::A_TILE + (uint32_t)ntn * C::C_TILE);
-        bulk_copy_g2s(sa, (const unsigned char*)a.A + t0 * C::A_TILE, (uint32_t)nt * C::A_TILE,
-                      &full[s]);
-        if (ntn > 0)
-          bulk_copy_g2s(sc, (const unsigned char*)a.conn + kn * TPC * C::C_TILE,
-                        (uint32_t)ntn * C::C_TILE, &full[s]);
-      }
-      // drain: wait (bounded) until the last copies issued have landed
-      if (pro_issued) mbar_wait_bounded(pro, 0u, a.wait_budget);
-      for (int64_t q = issued - S; q < issued; ++q) {
-        if (q < 0) continue;
-        mbar_wait_bounded(&full[q % S], (uint32_t)((q / S) & 1), a.wait_budget);
-      }
-      if (failed) atomicOr(a.err, 1);
-    }
-  } else {
-    // ---- consumer warpgroup: thread m = 32 warp + lane owns cell m of the tile,
-    // i.e. row m of U, G, H, Y and lane m of tensor memory.
-    const int m = tid;
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-    const uint32_t d1 = tmem, d2 = tmem + (uint32_t)N1;
-    int failed = 0;
-    uint32_t c[V], cn[V];
-    float ul[V], un[V];
-    bool active = false;
-    auto gather = [&](const uint32_t(&cc)[V], float(&dst)[V]) {
-      static_for<V>([&](auto lc) {
-        constexpr int l = decltype(lc)::value;
-        dst[l] = (cc[l] & kBndBit) ? 0.0f : __ldg(a.u + (cc[l] & kIdMask));
+  // Warpgroup wg takes the 128-cell tiles wg + NWG * blockIdx.x, stepping by NWG *
+  // gridDim.x: tile t holds the AoSoA tiles 4t .. 4t+3, warp w the cells of 4t + w.
+  const int64_t ntiles32 = (a.E + kTile - 1) / kTile;
+  const int64_t ntiles128 = (a.E + M - 1) / M, step = (int64_t)NWG * gridDim.x;
+  int64_t a_issued = 0, a_waited = 0;  // bulk copies of A^_T (thread m == 0 issues)
+  auto issue_a = [&](int64_t tt) {
+    const int nt = (int)min((int64_t)4, ntiles32 - 4 * tt);
+    fence_proxy_async_smem();
+    mbar_expect_tx(abar, (uint32_t)nt * C::A_TILE);
+    bulk_copy_g2s(stA, (const unsigned char*)a.A + 4 * tt * C::A_TILE, (uint32_t)nt * C::A_TILE,
+                  abar);
+    ++a_issued;
+  };
+  auto load_conn = [&](int64_t tt, uint32_t(&cc)[V], bool& act) {
+    const int64_t at = 4 * tt + warp;
+    act = tt < ntiles128 && at * kTile + lane < a.E;
+    const uint32_t* src = a.conn + at * (V * kTile) + lane;
+    static_for<V>([&](auto lc) {
+      constexpr int l = decltype(lc)::value;
+      cc[l] = act ? __ldg(src + l * kTile) : kBndBit;
+    });
+  };
+  auto gather = [&](const uint32_t(&cc)[V], float(&dst)[V]) {
+    static_for<V>([&](auto lc) {
+      constexpr int l = decltype(lc)::value;
+      dst[l] = (cc[l] & kBndBit) ? 0.0f : __ldg(a.u + (cc[l] & kIdMask));
+    });
+  };
+  int failed = 0;
+  uint32_t phase = 0;
+  uint32_t c[V], cn[V];
+  float ul[V], un[V];
+  bool active, active_n;
+  int64_t t = (int64_t)blockIdx.x * NWG + wg;
+  if (m == 0 && t < ntiles128) issue_a(t);
+  load_conn(t, c, active);
+  gather(c, ul);
+  for (; t < ntiles128; t += step) {  // the same trip count in the whole warpgroup
+    // U -> A1 (hi, lo); columns V..K1-1 are zero
+    static_for<K1 / 4>([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      float h[4], l[4];
+      static_for<4>([&](auto ec) {
+        constexpr int e = decltype(ec)::value;
+        constexpr int col = 4 * q + e;
+        if constexpr (col < V) tc::split_tf32(ul[col], h[e], l[e]);
+        else h[e] = l[e] = 0.0f;
       });
-    };
-    if (k0 < a.nchunks) {
-      failed = mbar_wait_bounded(pro, 0u, a.wait_budget) ? 0 : 1;
-      const int64_t tile = k0 * TPC + warp;
-      active = !failed && tile < a.ntiles && tile * kTile + lane < a.E;
-      const uint32_t* sC = (const uint32_t*)(pro_buf + warp * C::C_TILE) + lane;
-      static_for<V>([&](auto lc) {
-        constexpr int l = decltype(lc)::value;
-        c[l] = active ? sC[l * kTile] : kBndBit;
-      });
-      gather(c, ul);
+      const uint32_t off = tc::op_off(M, m, 4 * q) / 4;
+      *(float4*)(a1h + off) = make_float4(h[0], h[1], h[2], h[3]);
+      *(float4*)(a1l + off) = make_float4(l[0], l[1], l[2], l[3]);
+    });
+    load_conn(t + step, cn, active_n);  // next tile's conn: in flight during this tile
+    fence_proxy_async_smem();
+    tc::fence_before_sync();
+    if (tc::bar_or(1 + wg, M, failed)) {
+      failed = 1;
+      break;
     }
-    uint32_t phase = 0;
-    const uint32_t s_a1h = smem_addr(a1h), s_a1l = smem_addr(a1l);
-    const uint32_t s_a2h = smem_addr(a2h), s_a2l = smem_addr(a2l);
-    const uint32_t s_b1h = smem_addr(b1h), s_b1l = smem_addr(b1l);
-    const uint32_t s_b2h = smem_addr(b2h), s_b2l = smem_addr(b2l);
-    for (int64_t i = 0;; ++i) {
-      const int64_t k = k0 + i * G;
-      if (k >= a.nchunks) break;  // the same trip count in every consumer warp
-      const int s = (int)(i % S);
-      const uint32_t parity = (uint32_t)((i / S) & 1);
-      int f = failed ? 1 : (mbar_wait_bounded(&full[s], parity, a.wait_budget) ? 0 : 1);
-      // U -> A1 (hi, lo); columns V..K1-1 are zero
-      static_for<K1 / 4>([&](auto qc) {
-        constexpr int q = decltype(qc)::value;
-        float h[4], l[4];
-        static_for<4>([&](auto ec) {
+    if (m == 0) {  // GEMM 1: G = U B1 (three TF32 products per k-step)
+      tc::fence_after_sync();
+      constexpr uint32_t idesc = tc::idesc_tf32(M, N1);
+      static_for<K1 / 8>([&](auto sc) {
+        constexpr int ks = decltype(sc)::value;
+        const uint32_t oa = ks * tc::op_kstep(M), ob = ks * tc::op_kstep(N1);
+        const uint64_t ah = tc::smem_desc(s_a1h + oa, tc::op_lbo(M), 128);
+        const uint64_t al = tc::smem_desc(s_a1l + oa, tc::op_lbo(M), 128);
+        const uint64_t bh = tc::smem_desc(s_b1h + ob, tc::op_lbo(N1), 128);
+        const uint64_t bl = tc::smem_desc(s_b1l + ob, tc::op_lbo(N1), 128);
+        tc::mma_tf32(d1, ah, bh, idesc, ks > 0 ? 1u : 0u);
+        tc::mma_tf32(d1, ah, bl, idesc, 1u);
+        tc::mma_tf32(d1, al, bh, idesc, 1u);
+      });
+      tc::mma_commit(mma1);
+    }
+    int f = __any_sync(0xffffffffu, mbar_wait_bounded(mma1, phase, a.wait_budget) ? 0 : 1);
+    f |= __any_sync(0xffffffffu,
+                    mbar_wait_bounded(abar, (uint32_t)(a_waited & 1), a.wait_budget) ? 0 : 1);
+    ++a_waited;
+    tc::fence_after_sync();
+    // G (tensor memory) -> H_j = A^_T,j G_j -> H hi over the G columns, H lo beside
+    const float* sA = (const float*)(stA + warp * C::A_TILE) + lane;
+    static_for<N1 / CH>([&](auto bc) {
+      constexpr int b = decltype(bc)::value;
+      constexpr int j0 = b * CH / NB, j1 = (b + 1) * CH / NB < W ? (b + 1) * CH / NB : W;
+      float g[CH];
+      static_for<CH / 16>([&](auto hc) {
+        constexpr int hb = decltype(hc)::value;
+        float v[16];
+        tc::tmem_ld16(d1 + lane_base + (uint32_t)(b * CH + 16 * hb), v);
+        static_for<16>([&](auto ec) { g[16 * hb + decltype(ec)::value] = v[decltype(ec)::value]; });
+      });
+      float hh[CH];
+      static_for<CH>([&](auto ec) { hh[decltype(ec)::value] = 0.0f; });
+      static_for<j1 - j0>([&](auto jc) {
+        constexpr int jj = decltype(jc)::value;
+        constexpr int o = (j0 + jj) * NB - b * CH;  // first column of node j0 + jj in the chunk
+        float aj[NS];
+        static_for<NS>([&](auto kc) {
+          constexpr int kk = decltype(kc)::value;
+          aj[kk] = active ? sA[((j0 + jj) * NS + kk) * kTile] : 0.0f;
+        });
+        block_mul<D, FORM>(aj, g + o, hh + o);
+      });
+      static_for<CH / 16>([&](auto hc) {
+        constexpr int hb = decltype(hc)::value;
+        float hi[16], lo[16];
+        static_for<16>([&](auto ec) {
           constexpr int e = decltype(ec)::value;
-          constexpr int col = 4 * q + e;
-          if constexpr (col < V) tc::split_tf32(ul[col], h[e], l[e]);
-          else h[e] = l[e] = 0.0f;
+          tc::split_tf32(hh[16 * hb + e], hi[e], lo[e]);
         });
-        const uint32_t off = tc::op_off(M, m, 4 * q) / 4;
-        *(float4*)(a1h + off) = make_float4(h[0], h[1], h[2], h[3]);
-        *(float4*)(a1l + off) = make_float4(l[0], l[1], l[2], l[3]);
+        tc::tmem_st16(d1 + lane_base + (uint32_t)(b * CH + 16 * hb), hi);
+        tc::tmem_st16(hlo + lane_base + (uint32_t)(b * CH + 16 * hb), lo);
       });
-      // conn of the CTA's next chunk, and its gathers (in flight during this tile)
-      const unsigned char* st = ring + (size_t)s * C::CHUNK;
-      const float* sA = (const float*)(st + warp * C::A_TILE) + lane;
-      const uint32_t* sCn = (const uint32_t*)(st + TPC * C::A_TILE + warp * C::C_TILE) + lane;
-      const int64_t kn = k + G, tile_n = kn * TPC + warp;
-      const bool active_n =
-          !f && kn < a.nchunks && tile_n < a.ntiles && tile_n * kTile + lane < a.E;
-      static_for<V>([&](auto lc) {
-        constexpr int l = decltype(lc)::value;
-        cn[l] = active_n ? sCn[l * kTile] : kBndBit;
-      });
-      gather(cn, un);
-      fence_proxy_async_smem();
-      tc::fence_before_sync();
-      if (tc::bar_or(1, M, f)) {
-        failed = 1;
-        break;
-      }
-      if (tid == 0) {  // GEMM 1: G = U B1 (three TF32 products per k-step)
-        tc::fence_after_sync();
-        constexpr uint32_t idesc = tc::idesc_tf32(M, N1);
-        static_for<K1 / 8>([&](auto sc) {
-          constexpr int ks = decltype(sc)::value;
-          const uint32_t oa = ks * tc::op_kstep(M), ob = ks * tc::op_kstep(N1);
-          const uint64_t ah = tc::smem_desc(s_a1h + oa, tc::op_lbo(M), 128);
-          const uint64_t al = tc::smem_desc(s_a1l + oa, tc::op_lbo(M), 128);
-          const uint64_t bh = tc::smem_desc(s_b1h + ob, tc::op_lbo(N1), 128);
-          const uint64_t bl = tc::smem_desc(s_b1l + ob, tc::op_lbo(N1), 128);
-          tc::mma_tf32(d1, ah, bh, idesc, ks > 0 ? 1u : 0u);
-          tc::mma_tf32(d1, ah, bl, idesc, 1u);
-          tc::mma_tf32(d1, al, bh, idesc, 1u);
-        });
-        tc::mma_commit(mma1);
-      }
-      f = __any_sync(0xffffffffu, mbar_wait_bounded(mma1, phase, a.wait_budget) ? 0 : 1);
-      tc::fence_after_sync();
-      // G (tensor memory) -> H_j = A^_T,j G_j -> A2 (hi, lo); columns NC..K2-1 zero
-      {
-        float g[N1];
-        static_for<N1 / 16>([&](auto bc) {
-          constexpr int b = decltype(bc)::value;
-          float v[16];
-          tc::tmem_ld16(d1 + lane_base + (uint32_t)(16 * b), v);
-          static_for<16>([&](auto ec) {
-            constexpr int e = decltype(ec)::value;
-            g[16 * b + e] = v[e];
-          });
-        });
-        float hh[K2];
-        static_for<W>([&](auto jc) {
-          constexpr int j = decltype(jc)::value;
-          float aj[NS];
-          static_for<NS>([&](auto kc) {
-            constexpr int kk = decltype(kc)::value;
-            aj[kk] = active ? sA[(j * NS + kk) * kTile] : 0.0f;
-          });
-          block_mul<D, FORM>(aj, g + j * NB, hh + j * NB);
-        });
-        static_for<K2 - NC>([&](auto ec) { hh[NC + decltype(ec)::value] = 0.0f; });
-        static_for<K2 / 4>([&](auto qc) {
-          constexpr int q = decltype(qc)::value;
-          float h[4], l[4];
-          static_for<4>([&](auto ec) {
-            constexpr int e = decltype(ec)::value;
-            tc::split_tf32(hh[4 * q + e], h[e], l[e]);
-          });
-          const uint32_t off = tc::op_off(M, m, 4 * q) / 4;
-          *(float4*)(a2h + off) = make_float4(h[0], h[1], h[2], h[3]);
-          *(float4*)(a2l + off) = make_float4(l[0], l[1], l[2], l[3]);
-        });
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[s]);  // this warp no longer reads stage s
-      fence_proxy_async_smem();
-      tc::fence_before_sync();
-      if (tc::bar_or(1, M, f)) {
-        failed = 1;
-        break;
-      }
-      if (tid == 0) {  // GEMM 2: Y = H B2
-        tc::fence_after_sync();
-        constexpr uint32_t idesc = tc::idesc_tf32(M, N2);
-        static_for<K2 / 8>([&](auto sc) {
-          constexpr int ks = decltype(sc)::value;
-          const uint32_t oa = ks * tc::op_kstep(M), ob = ks * tc::op_kstep(N2);
-          const uint64_t ah = tc::smem_desc(s_a2h + oa, tc::op_lbo(M), 128);
-          const uint64_t al = tc::smem_desc(s_a2l + oa, tc::op_lbo(M), 128);
-          const uint64_t bh = tc::smem_desc(s_b2h + ob, tc::op_lbo(N2), 128);
-          const uint64_t bl = tc::smem_desc(s_b2l + ob, tc::op_lbo(N2), 128);
-          tc::mma_tf32(d2, ah, bh, idesc, ks > 0 ? 1u : 0u);
-          tc::mma_tf32(d2, ah, bl, idesc, 1u);
-          tc::mma_tf32(d2, al, bh, idesc, 1u);
-        });
-        tc::mma_commit(mma2);
-      }
-      f = __any_sync(0xffffffffu, mbar_wait_bounded(mma2, phase, a.wait_budget) ? 0 : 1);
-      tc::fence_after_sync();
-      phase ^= 1u;
-      if (!f) {  // Y (tensor memory) -> y += P_T^T Y_T
-        static_for<N2 / 16>([&](auto bc) {
-          constexpr int b = decltype(bc)::value;
-          float v[16];
-          tc::tmem_ld16(d2 + lane_base + (uint32_t)(16 * b), v);
-          static_for<16>([&](auto ec) {
-            constexpr int l = 16 * b + decltype(ec)::value;
-            if constexpr (l < V) {
-              if (!(c[l] & kBndBit)) atomicAdd(a.y + (c[l] & kIdMask), v[l - 16 * b]);
-            }
-          });
-        });
-      }
-      tc::fence_before_sync();
-      failed = f;
-      static_for<V>([&](auto lc) {
-        constexpr int l = decltype(lc)::value;
-        c[l] = cn[l];
-        ul[l] = un[l];
-      });
-      active = active_n;
+    });
+    tc::tmem_st_wait();
+    gather(cn, un);  // next tile's u (its conn has arrived by now)
+    tc::fence_before_sync();
+    if (tc::bar_or(1 + wg, M, f)) {  // the warpgroup is done with the A^_T stage and H
+      failed = 1;
+      break;
     }
-    if (failed && lane == 0) atomicOr(a.err, 1);
+    if (m == 0) {
+      if (t + step < ntiles128) issue_a(t + step);  // next tile's A^_T into the free stage
+      tc::fence_after_sync();  // GEMM 2: Y = H B2, H from tensor memory
+      constexpr uint32_t idesc = tc::idesc_tf32(M, N2);
+      static_for<K2 / 8>([&](auto sc) {
+        constexpr int ks = decltype(sc)::value;
+        const uint32_t ob = ks * tc::op_kstep(N2);
+        const uint64_t bh = tc::smem_desc(s_b2h + ob, tc::op_lbo(N2), 128);
+        const uint64_t bl = tc::smem_desc(s_b2l + ob, tc::op_lbo(N2), 128);
+        tc::mma_tf32_ts(d2, d1 + 8u * ks, bh, idesc, ks > 0 ? 1u : 0u);
+        tc::mma_tf32_ts(d2, d1 + 8u * ks, bl, idesc, 1u);
+        tc::mma_tf32_ts(d2, hlo + 8u * ks, bh, idesc, 1u);
+      });
+      tc::mma_commit(mma2);
+    }
+    f = __any_sync(0xffffffffu, mbar_wait_bounded(mma2, phase, a.wait_budget) ? 0 : 1);
+    tc::fence_after_sync();
+    phase ^= 1u;
+    if (!f) {  // Y (tensor memory) -> y += P_T^T Y_T
+      static_for<N2 / 16>([&](auto bc) {
+        constexpr int b = decltype(bc)::value;
+        float v[16];
+        tc::tmem_ld16(d2 + lane_base + (uint32_t)(16 * b), v);
+        static_for<16>([&](auto ec) {
+          constexpr int l = 16 * b + decltype(ec)::value;
+          if constexpr (l < V) {
+            if (!(c[l] & kBndBit)) atomicAdd(a.y + (c[l] & kIdMask), v[l - 16 * b]);
+          }
+        });
+      });
+    }
+    tc::fence_before_sync();
+    failed = f;
+    static_for<V>([&](auto lc) {
+      constexpr int l = decltype(lc)::value;
+      c[l] = cn[l];
+      ul[l] = un[l];
+    });
+    active = active_n;
   }
+  // a copy issued for a tile this warpgroup did not reach (after a failed wait) must
+  // land before the shared memory is released
+  if (m == 0)
+    for (int64_t q = a_waited; q < a_issued; ++q)
+      mbar_wait_bounded(abar, (uint32_t)(q & 1), a.wait_budget);
+  if (failed && lane == 0) atomicOr(a.err, 1);
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) {
+  if (tid < 32) {
     tc::fence_after_sync();
     tc::tmem_dealloc(tmem, C::TMC);
   }
   // Dirichlet rows: y_b = u_b (the scatter skipped them)
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + tid; t < a.nbnd;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t idx = a.bnd[t];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + tid; i < a.nbnd;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t idx = a.bnd[i];
     a.y[idx] = a.u[idx];
   }
 }
@@ -358,6 +313,7 @@ __global__ void __launch_bounds__(TcCfg<D, P, FORM>::THREADS, 1) k_apply_tc(TmaA
 namespace {
 
 struct TcLaunch {
+  int blocks = 1;  // resident CTAs per SM (shared memory, registers, tensor memory)
   int num_sms = 1;
 };
 
@@ -365,13 +321,17 @@ template <int D, int P, int FORM>
 const TcLaunch& tc_launch() {
   static const TcLaunch info = [] {
     using Cfg = TcCfg<D, P, FORM>;
+    auto kern = k_apply_tc<D, P, FORM>;
     TcLaunch t;
-    cuda_check(cudaFuncSetAttribute(k_apply_tc<D, P, FORM>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM),
+    cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM),
                "tensor-core apply smem attribute");
-    int dev = 0;
+    int dev = 0, nb = 0;
     cuda_check(cudaGetDevice(&dev), "get device");
     cuda_check(cudaDeviceGetAttribute(&t.num_sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, Cfg::THREADS, Cfg::SMEM),
+               "occupancy");
+    // every resident CTA holds TMC of the SM's 512 tensor-memory columns
+    t.blocks = std::max(1, std::min(nb, (int)(512 / Cfg::TMC)));
     return t;
   }();
   return info;
@@ -383,13 +343,13 @@ bool run_tc(const Ctx& c, const void* u, void* y, cudaStream_t s, const int* ski
     return false;
   } else {
     using Cfg = TcCfg<D, P, FORM>;
-    const TcLaunch& L = tc_launch<D, P, FORM>();  // one CTA per SM (shared memory)
-    if (u == nullptr) return true;               // preparation call from context set-up
-    const int64_t ntiles = (c.E + kTile - 1) / kTile;
-    const int64_t nchunks = (ntiles + Cfg::TPC - 1) / Cfg::TPC;
-    if (nchunks == 0) return true;
-    const int64_t grid = std::min<int64_t>(nchunks, (int64_t)L.num_sms);
-    TmaArgs<float> a{c.d_A32, c.d_conn, (const float*)u, (float*)y, c.E, ntiles, nchunks, 1,
+    const TcLaunch& L = tc_launch<D, P, FORM>();
+    if (u == nullptr) return true;  // preparation call from context set-up
+    const int64_t ntiles128 = (c.E + Cfg::M - 1) / Cfg::M;
+    if (ntiles128 == 0) return true;
+    const int64_t grid = std::min<int64_t>((ntiles128 + Cfg::NWG - 1) / Cfg::NWG,
+                                           (int64_t)L.num_sms * L.blocks);
+    TmaArgs<float> a{c.d_A32, c.d_conn, (const float*)u, (float*)y, c.E, 0, 0, 1,
                      skip, c.d_kerr, c.d_bnd, c.dirichlet ? c.nbnd : 0, c.wait_budget, -1, 0};
     k_apply_tc<D, P, FORM><<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
     return true;

@@ -53,6 +53,19 @@ def test_tc_apply_parity(B, d, p, form, N2, N3, monkeypatch):
     ctx.check()
 
 
+# 165,888 triangles = 1,296 tiles of 128 cells: more tiles than warpgroups on a GB300,
+# so every warpgroup loops (next-tile conn and gathers in flight across iterations)
+@pytest.mark.parametrize("p,form", [(2, "elliptic"), (3, "projection"), (4, "elliptic")])
+def test_tc_apply_parity_looping(B, p, form, monkeypatch):
+    monkeypatch.setenv("DOGIP_APPLY_VARIANT", "3")
+    ctx, P = make(B, 2, p, form, 288)
+    u = inputs.rhs_normal(P.n, 1, seed=43)[:, 0].astype(np.float32)
+    u64 = u.astype(np.float64)
+    y = ctx.apply(torch.tensor(u, device="cuda"), prec="fp32").cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(y - P.apply(u64)) <= TOL32 * P.apply_abs(u64))
+    ctx.check()
+
+
 def test_tc_empty_like_inputs(B, monkeypatch):
     """Zero input gives exactly zero (no stale tensor memory or shared-memory tables
     leak into the result); Dirichlet rows copy u."""
