@@ -41,7 +41,14 @@ L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) of one launch of the staged P4 FP32 apply on this workload,
 # from the ncu capture summarised in profiles/k_apply_tma_2d_p4_fp32.md; to be taken
 # again whenever that kernel changes.
-TRAFFIC_P4_FP32 = 252637696  # 241,421,824 read + 11,215,872 written
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one P4 FP32 launch, per kernel variant
+TRAFFIC_P4_FP32 = {1: 252637696,   # staged apply: 241,421,824 read + 11,215,872 written
+                   3: 252793344}   # tensor cores: 241,417,472 read + 11,375,872 written
+KERNEL_P4_FP32 = {0: "k_apply<2,4,ELLIPTIC,float> (one thread per cell)",
+                  1: "k_apply_tma<2,4,ELLIPTIC,float> (staged apply)",
+                  2: "k_apply_sfw<2,4,ELLIPTIC,float> (self-feeding warps)",
+                  3: "k_apply_tc<2,4,ELLIPTIC> (tensor cores, tcgen05)"}
+PROFILE_P4_FP32 = {1: "profiles/k_apply_tma_2d_p4_fp32.md", 3: "profiles/k_apply_tc_2d_p4_fp32.md"}
 
 
 def mesh_and_coef():
@@ -837,12 +844,13 @@ def main():
 
     _section("roofline")
     dom = applies["P4_fp32"]
+    var4 = tuned["P4"]["fp32"][0]
     roofline = {"bound": "hbm", "achieved": dom["GBps"], "peak": hbm, "unit": "GB/s",
                 "frac": round(dom["GBps"] / hbm, 4),
-                "traffic": TRAFFIC_P4_FP32 if tuned["P4"]["fp32"][0] == 1 else None,
+                "traffic": TRAFFIC_P4_FP32.get(var4),
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch "
-                                  "(profiles/k_apply_tma_2d_p4_fp32.md)",
-                "kernel": "k_apply_tma<2,4,ELLIPTIC,float> (staged apply), 2D P4, 524,288 cells; "
+                                  f"({PROFILE_P4_FP32.get(var4, 'not captured for this kernel')})",
+                "kernel": f"{KERNEL_P4_FP32.get(var4, var4)}, 2D P4, 524,288 cells; "
                           "timed as 30 back-to-back dogip_apply calls (y memset + kernel)",
                 "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
                 "alg_bytes_per_launch": dom["alg_bytes"]}
