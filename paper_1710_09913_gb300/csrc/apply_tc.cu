@@ -11,8 +11,11 @@
 // The operands are FP32 values split as hi + lo with hi rounded to TF32; each GEMM
 // is three kind::tf32 MMAs (hi.hi + hi.lo + lo.hi) accumulating in FP32 in tensor
 // memory, about 21 bits per product (the dropped lo.lo term and the TF32 truncation
-// of lo are 2^-21 relative).  The A^_T and conn streams reach shared memory through
-// the same producer-warp ring of cp.async.bulk copies as the staged apply.  Every
+// of lo are 2^-21 relative).  The A operands U and H live in tensor memory next to
+// the accumulators, the split tables B1, B2 in shared memory.  Each warpgroup (four
+// warps, one 128-cell tile at a time) has its own tensor-memory columns, MMA
+// mbarriers and one shared-memory stage of A^_T, refilled by cp.async.bulk for its
+// next tile; conn and the u gathers of the next tile are in flight meanwhile.  Every
 // wait is bounded: on expiry the warpgroup leaves the loop together (the named
 // barriers OR-reduce the failure), the kernel raises the error word, frees its
 // tensor memory and returns.
@@ -31,15 +34,19 @@ struct TcCfg {
   static constexpr int M = 128;  // cells per MMA tile (one per thread of a warpgroup)
   static constexpr int K1 = (V + 7) / 8 * 8, N1 = (NC + 15) / 16 * 16;
   static constexpr int K2 = (NC + 7) / 8 * 8, N2 = (V + 15) / 16 * 16;
-  // shared memory: the split tables (per CTA); per warpgroup the A1 operand (hi, lo)
-  // and one stage of A^_T for its 128 cells (four AoSoA tiles, one bulk copy)
+  // shared memory: the split tables (per CTA) and, per warpgroup, one stage of A^_T
+  // for its 128 cells (four AoSoA tiles, one bulk copy)
   static constexpr uint32_t BTAB = 2 * (N1 * K1 + N2 * K2) * 4;
   static constexpr uint32_t A_TILE = W * NS * kTile * 4;
-  static constexpr uint32_t WGB = 2 * M * K1 * 4 + 4 * A_TILE;
+  static constexpr uint32_t WGB = 4 * A_TILE;
   static constexpr uint32_t kBudget = 224 * 1024;
-  // tensor memory per warpgroup: D1 = G (its columns then hold the hi part of H, the
-  // A operand of GEMM 2), the lo part of H, and D2 = Y
-  static constexpr int TMW = 2 * N1 + N2;
+  // tensor-memory columns of a warpgroup: [0, N1) G = D1, whose first K2 columns then
+  // hold the TF32 hi part of H (the A operand of GEMM 2); [K2, 2 K2) the lo part of H;
+  // [D2O, D2O + N2) Y = D2; and U (hi, lo), the A operand of GEMM 1, at [N1, N1 + 2 K1)
+  // while GEMM 1 runs (columns of the previous tile's H lo and Y, dead by then)
+  static constexpr int D2O = (2 * K2 + 15) / 16 * 16;
+  static constexpr int TMW0 = D2O + N2 > N1 + 2 * K1 ? D2O + N2 : N1 + 2 * K1;
+  static constexpr int TMW = (TMW0 + 15) / 16 * 16;
   static constexpr int NWG0 = (int)(((long)kBudget - BTAB - 256) / WGB);
   static constexpr int NWG1 = NWG0 > 4 ? 4 : NWG0;
   static constexpr int NWG = NWG1 * TMW > 512 ? 512 / TMW : NWG1;  // warpgroups per CTA
@@ -98,9 +105,7 @@ __global__ void __launch_bounds__(TcCfg<D, P, FORM>::THREADS, 1) k_apply_tc(TmaA
   uint32_t* tslot = (uint32_t*)(bars + 3 * NWG);
   if (a.skip != nullptr && *a.skip) return;
   const int tid = threadIdx.x, wg = tid / M, m = tid % M, warp = m >> 5, lane = tid & 31;
-  float* a1h = (float*)(base + C::BTAB + wg * C::WGB);
-  float* a1l = a1h + M * K1;
-  unsigned char* stA = (unsigned char*)(a1l + M * K1);  // A^_T of the warpgroup's tile
+  unsigned char* stA = base + C::BTAB + wg * C::WGB;  // A^_T of the warpgroup's tile
   uint64_t* mma1 = bars + 3 * wg;
   uint64_t* mma2 = mma1 + 1;
   uint64_t* abar = mma1 + 2;
@@ -121,10 +126,10 @@ __global__ void __launch_bounds__(TcCfg<D, P, FORM>::THREADS, 1) k_apply_tc(TmaA
   const uint32_t tmem = *tslot;
   // this warpgroup's tensor-memory columns and this warp's lanes
   const uint32_t d1 = tmem + (uint32_t)(wg * C::TMW);  // G, then the hi part of H
-  const uint32_t hlo = d1 + (uint32_t)N1;              // lo part of H
-  const uint32_t d2 = d1 + (uint32_t)(2 * N1);         // Y
+  const uint32_t hlo = d1 + (uint32_t)K2;              // lo part of H
+  const uint32_t d2 = d1 + (uint32_t)C::D2O;           // Y
+  const uint32_t uhi = d1 + (uint32_t)N1, ulo = uhi + (uint32_t)K1;  // U during GEMM 1
   const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-  const uint32_t s_a1h = smem_addr(a1h), s_a1l = smem_addr(a1l);
   const uint32_t s_b1h = smem_addr(b1h), s_b1l = smem_addr(b1l);
   const uint32_t s_b2h = smem_addr(b2h), s_b2l = smem_addr(b2l);
 
@@ -166,40 +171,37 @@ __global__ void __launch_bounds__(TcCfg<D, P, FORM>::THREADS, 1) k_apply_tc(TmaA
   load_conn(t, c, active);
   gather(c, ul);
   for (; t < ntiles128; t += step) {  // the same trip count in the whole warpgroup
-    // U -> A1 (hi, lo); columns V..K1-1 are zero
-    static_for<K1 / 4>([&](auto qc) {
+    // U -> tensor memory (hi, lo); columns V..K1-1 are zero
+    static_for<K1 / 8>([&](auto qc) {
       constexpr int q = decltype(qc)::value;
-      float h[4], l[4];
-      static_for<4>([&](auto ec) {
+      float h[8], l[8];
+      static_for<8>([&](auto ec) {
         constexpr int e = decltype(ec)::value;
-        constexpr int col = 4 * q + e;
+        constexpr int col = 8 * q + e;
         if constexpr (col < V) tc::split_tf32(ul[col], h[e], l[e]);
         else h[e] = l[e] = 0.0f;
       });
-      const uint32_t off = tc::op_off(M, m, 4 * q) / 4;
-      *(float4*)(a1h + off) = make_float4(h[0], h[1], h[2], h[3]);
-      *(float4*)(a1l + off) = make_float4(l[0], l[1], l[2], l[3]);
+      tc::tmem_st8(uhi + lane_base + (uint32_t)(8 * q), h);
+      tc::tmem_st8(ulo + lane_base + (uint32_t)(8 * q), l);
     });
     load_conn(t + step, cn, active_n);  // next tile's conn: in flight during this tile
-    fence_proxy_async_smem();
+    tc::tmem_st_wait();
     tc::fence_before_sync();
     if (tc::bar_or(1 + wg, M, failed)) {
       failed = 1;
       break;
     }
-    if (m == 0) {  // GEMM 1: G = U B1 (three TF32 products per k-step)
+    if (m == 0) {  // GEMM 1: G = U B1 (three TF32 products per k-step), U from tensor memory
       tc::fence_after_sync();
       constexpr uint32_t idesc = tc::idesc_tf32(M, N1);
       static_for<K1 / 8>([&](auto sc) {
         constexpr int ks = decltype(sc)::value;
-        const uint32_t oa = ks * tc::op_kstep(M), ob = ks * tc::op_kstep(N1);
-        const uint64_t ah = tc::smem_desc(s_a1h + oa, tc::op_lbo(M), 128);
-        const uint64_t al = tc::smem_desc(s_a1l + oa, tc::op_lbo(M), 128);
+        const uint32_t ob = ks * tc::op_kstep(N1);
         const uint64_t bh = tc::smem_desc(s_b1h + ob, tc::op_lbo(N1), 128);
         const uint64_t bl = tc::smem_desc(s_b1l + ob, tc::op_lbo(N1), 128);
-        tc::mma_tf32(d1, ah, bh, idesc, ks > 0 ? 1u : 0u);
-        tc::mma_tf32(d1, ah, bl, idesc, 1u);
-        tc::mma_tf32(d1, al, bh, idesc, 1u);
+        tc::mma_tf32_ts(d1, uhi + 8u * ks, bh, idesc, ks > 0 ? 1u : 0u);
+        tc::mma_tf32_ts(d1, uhi + 8u * ks, bl, idesc, 1u);
+        tc::mma_tf32_ts(d1, ulo + 8u * ks, bh, idesc, 1u);
       });
       tc::mma_commit(mma1);
     }
@@ -208,7 +210,9 @@ __global__ void __launch_bounds__(TcCfg<D, P, FORM>::THREADS, 1) k_apply_tc(TmaA
                     mbar_wait_bounded(abar, (uint32_t)(a_waited & 1), a.wait_budget) ? 0 : 1);
     ++a_waited;
     tc::fence_after_sync();
-    // G (tensor memory) -> H_j = A^_T,j G_j -> H hi over the G columns, H lo beside
+    // G (tensor memory) -> H_j = A^_T,j G_j -> H hi over the G columns, H lo at K2.
+    // Only the K2 columns GEMM 2 reads are stored: the G columns from K2 on are the
+    // zero rows of B1, never used, and may be overwritten by H lo before they are read.
     const float* sA = (const float*)(stA + warp * C::A_TILE) + lane;
     static_for<N1 / CH>([&](auto bc) {
       constexpr int b = decltype(bc)::value;
@@ -232,15 +236,18 @@ __global__ void __launch_bounds__(TcCfg<D, P, FORM>::THREADS, 1) k_apply_tc(TmaA
         });
         block_mul<D, FORM>(aj, g + o, hh + o);
       });
-      static_for<CH / 16>([&](auto hc) {
+      static_for<CH / 8>([&](auto hc) {
         constexpr int hb = decltype(hc)::value;
-        float hi[16], lo[16];
-        static_for<16>([&](auto ec) {
-          constexpr int e = decltype(ec)::value;
-          tc::split_tf32(hh[16 * hb + e], hi[e], lo[e]);
-        });
-        tc::tmem_st16(d1 + lane_base + (uint32_t)(b * CH + 16 * hb), hi);
-        tc::tmem_st16(hlo + lane_base + (uint32_t)(b * CH + 16 * hb), lo);
+        constexpr int col = b * CH + 8 * hb;
+        if constexpr (col < K2) {
+          float hi[8], lo[8];
+          static_for<8>([&](auto ec) {
+            constexpr int e = decltype(ec)::value;
+            tc::split_tf32(hh[8 * hb + e], hi[e], lo[e]);
+          });
+          tc::tmem_st8(d1 + lane_base + (uint32_t)col, hi);
+          tc::tmem_st8(hlo + lane_base + (uint32_t)col, lo);
+        }
       });
     });
     tc::tmem_st_wait();
