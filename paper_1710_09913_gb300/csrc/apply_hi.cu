@@ -186,8 +186,14 @@ int hi_run(const Ctx& c, int op, const void* u, void* y, int R, int prec, bool a
     if (u == nullptr) {  // preparation call (context set-up, outside capture)
       hi_attr<D, P, FORM, double>();
       hi_attr<D, P, FORM, float>();
+      apply_tc(c, nullptr, nullptr, nullptr, nullptr);
       return 1;
     }
+    // variant 3: the tensor-core kernel (FP32, one right-hand side, whole range)
+    const int var = c.apply_variant_prec[prec] >= 0 ? c.apply_variant_prec[prec] : c.apply_variant;
+    if (var == 3 && prec == DOGIP_FP32 && R == 1 && atomic && e0 == 0 && e1 == c.E &&
+        apply_tc(c, u, y, s, skip))
+      return 2;
     const int64_t nth = (e1 - e0) * (int64_t)R;
     if (nth <= 0) return 1;
     const unsigned nb = (unsigned)((nth + C::THREADS - 1) / C::THREADS);

@@ -26,10 +26,36 @@
 
 namespace dogip {
 
+constexpr int tc_binom(int n, int k) {
+  long long r = 1;
+  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+  return (int)r;
+}
+
+// Kernel arguments; B is the run-time reference table [NB][W][V] of the orders above
+// the compiled tables (null otherwise).
+struct TcArgs {
+  const float* A;
+  const uint32_t* conn;
+  const float* u;
+  float* y;
+  int64_t E;
+  const int* skip;
+  int* err;
+  const int32_t* bnd;
+  int64_t nbnd;
+  long long wait_budget;
+  const float* B;
+};
+
 template <int D, int P, int FORM>
 struct TcCfg {
-  using TB = dogip_tab::Tab<D, P, FORM>;
-  static constexpr int V = TB::V, W = TB::W, NB = TB::NB, NS = NSym<D, FORM>::value;
+  // RT: B^ comes from the context's run-time table (2D p > 4, 3D p > 3)
+  static constexpr bool RT = P > (D == 2 ? 4 : 3);
+  static constexpr int V = tc_binom(P + D, D);
+  static constexpr int W = tc_binom((FORM == DOGIP_PROJECTION ? 2 * P : 2 * P - 2) + D, D);
+  static constexpr int NB = FORM == DOGIP_PROJECTION ? 1 : D;
+  static constexpr int NS = NSym<D, FORM>::value;
   static constexpr int NC = NB * W;
   static constexpr int M = 128;  // cells per MMA tile (one per thread of a warpgroup)
   static constexpr int K1 = (V + 7) / 8 * 8, N1 = (NC + 15) / 16 * 16;
@@ -58,7 +84,8 @@ struct TcCfg {
   // D1 columns are read 16 at a time, and a W node's NB values may not straddle two
   // reads: NB = 3 (3D elliptic) reads all N1 <= 32 columns at once
   static constexpr int CH = NB == 3 ? N1 : 16;
-  static constexpr bool OK = NWG >= 1 && N1 <= 256 && (NB != 3 || N1 <= 32);
+  // V <= 36: the cell's conn, u_T and the next tile's must stay in registers
+  static constexpr bool OK = NWG >= 1 && N1 <= 256 && (NB != 3 || N1 <= 32) && V <= 36;
   static constexpr uint32_t SMEM = BTAB + (NWG < 1 ? 1 : NWG) * WGB + 256 + 1024;
   static constexpr int THREADS = (NWG < 1 ? 1 : NWG) * M;
 };
@@ -74,7 +101,7 @@ struct TcTab {
 template <int D, int P, int FORM>
 constexpr TcTab<D, P, FORM> make_tc_tab() {
   using C = TcCfg<D, P, FORM>;
-  using TB = typename C::TB;
+  using TB = dogip_tab::Tab<D, P, FORM>;
   TcTab<D, P, FORM> t{};
   for (int r = 0; r < C::NB; ++r)
     for (int j = 0; j < C::W; ++j)
@@ -90,7 +117,7 @@ template <int D, int P, int FORM>
 __device__ const TcTab<D, P, FORM> kTcTab = make_tc_tab<D, P, FORM>();
 
 template <int D, int P, int FORM>
-__global__ void __launch_bounds__(TcCfg<D, P, FORM>::THREADS, 1) k_apply_tc(TmaArgs<float> a) {
+__global__ void __launch_bounds__(TcCfg<D, P, FORM>::THREADS, 1) k_apply_tc(TcArgs a) {
   using C = TcCfg<D, P, FORM>;
   static_assert(C::OK, "tensor-core apply does not fit in shared / tensor memory");
   constexpr int V = C::V, W = C::W, NB = C::NB, NS = C::NS, M = C::M;
@@ -113,10 +140,23 @@ __global__ void __launch_bounds__(TcCfg<D, P, FORM>::THREADS, 1) k_apply_tc(TmaA
     for (int g = 0; g < 3 * NWG; ++g) mbar_init(&bars[g], 1);
     mbar_fence_init();
   }
-  {  // reference tables -> shared memory, split into TF32 hi + lo
+  if constexpr (!C::RT) {  // reference tables -> shared memory, split into TF32 hi + lo
     const TcTab<D, P, FORM>& tab = kTcTab<D, P, FORM>;
     for (int i = tid; i < N1 * K1; i += C::THREADS) tc::split_tf32(tab.b1[i], b1h[i], b1l[i]);
     for (int i = tid; i < N2 * K2; i += C::THREADS) tc::split_tf32(tab.b2[i], b2h[i], b2l[i]);
+  } else {  // the same from the run-time table B[r][j][l]
+    for (int i = tid; i < N1 * K1; i += C::THREADS) {
+      const int row = i / K1, k = i % K1;  // B1 row c = j NB + r, column l = k
+      const float b = row < NB * W && k < V ? a.B[((row % NB) * W + row / NB) * V + k] : 0.0f;
+      const uint32_t o = tc::op_off(N1, row, k) / 4;
+      tc::split_tf32(b, b1h[o], b1l[o]);
+    }
+    for (int i = tid; i < N2 * K2; i += C::THREADS) {
+      const int l = i / K2, col = i % K2;  // B2 row l, column c = j NB + r
+      const float b = l < V && col < NB * W ? a.B[((col % NB) * W + col / NB) * V + l] : 0.0f;
+      const uint32_t o = tc::op_off(N2, l, col) / 4;
+      tc::split_tf32(b, b2h[o], b2l[o]);
+    }
   }
   __syncwarp();
   if (tid < 32) tc::tmem_alloc(tslot, C::TMC);
@@ -356,8 +396,8 @@ bool run_tc(const Ctx& c, const void* u, void* y, cudaStream_t s, const int* ski
     if (ntiles128 == 0) return true;
     const int64_t grid = std::min<int64_t>((ntiles128 + Cfg::NWG - 1) / Cfg::NWG,
                                            (int64_t)L.num_sms * L.blocks);
-    TmaArgs<float> a{c.d_A32, c.d_conn, (const float*)u, (float*)y, c.E, 0, 0, 1,
-                     skip, c.d_kerr, c.d_bnd, c.dirichlet ? c.nbnd : 0, c.wait_budget, -1, 0};
+    TcArgs a{c.d_A32, c.d_conn, (const float*)u, (float*)y, c.E, skip, c.d_kerr, c.d_bnd,
+             c.dirichlet ? c.nbnd : 0, c.wait_budget, Cfg::RT ? c.d_hiB32 : nullptr};
     k_apply_tc<D, P, FORM><<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
     return true;
   }
@@ -366,24 +406,13 @@ bool run_tc(const Ctx& c, const void* u, void* y, cudaStream_t s, const int* ski
 }  // namespace
 
 bool apply_tc_available(int d, int p, int form) {
-  auto ok = [&](auto dc, auto pc) {
-    constexpr int D = decltype(dc)::value, P = decltype(pc)::value;
-    return form == DOGIP_ELLIPTIC ? TcCfg<D, P, DOGIP_ELLIPTIC>::OK
-                                  : TcCfg<D, P, DOGIP_PROJECTION>::OK;
-  };
-  if (d == 2) {
-    switch (p) {
-      case 1: return ok(std::integral_constant<int, 2>{}, std::integral_constant<int, 1>{});
-      case 2: return ok(std::integral_constant<int, 2>{}, std::integral_constant<int, 2>{});
-      case 3: return ok(std::integral_constant<int, 2>{}, std::integral_constant<int, 3>{});
-      case 4: return ok(std::integral_constant<int, 2>{}, std::integral_constant<int, 4>{});
-    }
-  } else if (d == 3) {
-    switch (p) {
-      case 1: return ok(std::integral_constant<int, 3>{}, std::integral_constant<int, 1>{});
-      case 2: return ok(std::integral_constant<int, 3>{}, std::integral_constant<int, 2>{});
-    }
-  }
+  const bool ell = form == DOGIP_ELLIPTIC;
+#define DOGIP_TC_OK(D, P)                                                                  \
+  if (d == D && p == P) return ell ? TcCfg<D, P, DOGIP_ELLIPTIC>::OK : TcCfg<D, P, DOGIP_PROJECTION>::OK;
+  DOGIP_TC_OK(2, 1) DOGIP_TC_OK(2, 2) DOGIP_TC_OK(2, 3) DOGIP_TC_OK(2, 4)
+  DOGIP_TC_OK(2, 5) DOGIP_TC_OK(2, 6) DOGIP_TC_OK(2, 7)
+  DOGIP_TC_OK(3, 1) DOGIP_TC_OK(3, 2)
+#undef DOGIP_TC_OK
   return false;
 }
 
@@ -391,7 +420,9 @@ bool apply_tc_available(int d, int p, int form) {
 // false when no tensor-core instance exists for (d, p, form).  u == nullptr only sets
 // the kernel attributes (context set-up, outside any stream capture).
 bool apply_tc(const Ctx& c, const void* u, void* y, cudaStream_t s, const int* skip) {
-  if (c.hi || c.global_w || c.factorized || !apply_tc_available(c.d, c.p, c.form)) return false;
+  if (c.global_w || c.factorized || !c.keep32 || !apply_tc_available(c.d, c.p, c.form))
+    return false;
+  if (c.hi && c.d_hiB32 == nullptr) return false;
   const bool ell = c.form == DOGIP_ELLIPTIC;
 #define DOGIP_TC_CASE(D, P)                                                          \
   if (c.d == D && c.p == P)                                                          \
@@ -401,6 +432,9 @@ bool apply_tc(const Ctx& c, const void* u, void* y, cudaStream_t s, const int* s
   DOGIP_TC_CASE(2, 2)
   DOGIP_TC_CASE(2, 3)
   DOGIP_TC_CASE(2, 4)
+  DOGIP_TC_CASE(2, 5)
+  DOGIP_TC_CASE(2, 6)
+  DOGIP_TC_CASE(2, 7)
   DOGIP_TC_CASE(3, 1)
   DOGIP_TC_CASE(3, 2)
 #undef DOGIP_TC_CASE

@@ -1112,12 +1112,15 @@ void tune_store_locked(const TuneKey& k, const TuneChoice& ch) {
 
 int autotune(Ctx& c, int force, cudaStream_t s) {
   DeviceGuard guard(c.device);
-  if (c.factorized || c.global_w || c.hi) return 0;  // one kernel only
+  if (c.factorized || c.global_w) return 0;  // one kernel only
+  // higher orders: the run-time-table kernel, or the tensor cores (FP32) where built
+  if (c.hi && !apply_tc_available(c.d, c.p, c.form)) return 0;
   int logE = 0;
   while ((int64_t(1) << logE) < c.E) ++logE;
   int tuned = 0;
   for (int prec : {DOGIP_FP32, DOGIP_FP64}) {
     if (prec == DOGIP_FP32 && !c.keep32) continue;
+    if (prec == DOGIP_FP64 && c.hi) continue;  // one FP64 kernel
     const TuneKey key{c.d, c.p, c.form, prec, logE};
     {
       std::lock_guard<std::mutex> lock(g_tune_mutex);
@@ -1149,6 +1152,7 @@ int autotune(Ctx& c, int force, cudaStream_t s) {
                                            {0, 64},  {0, 128}, {0, 256}};
       for (auto [var, blk] : cands) {
         if (var == 3 && (prec != DOGIP_FP32 || !apply_tc_available(c.d, c.p, c.form))) continue;
+        if (c.hi && var != 3 && var != 1) continue;  // 1: the run-time-table kernel
         c.apply_variant_prec[prec] = var;
         c.apply_block[prec] = blk;
         for (int w = 0; w < 2; ++w) launch_apply(c, u, y, 1, prec, DOGIP_SCATTER_ATOMIC, s, nullptr);

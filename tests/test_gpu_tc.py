@@ -55,6 +55,38 @@ def test_tc_apply_parity(B, d, p, form, N2, N3, monkeypatch):
 
 # 165,888 triangles = 1,296 tiles of 128 cells: more tiles than warpgroups on a GB300,
 # so every warpgroup loops (next-tile conn and gathers in flight across iterations)
+# orders above the compiled tables: B^ from the context's run-time table, split in the
+# kernel; 2D N = 7 (98 triangles, one ragged tile) and N = 20 (800 triangles)
+HI = [(5, "elliptic"), (5, "projection"), (6, "elliptic"), (6, "projection"), (7, "projection")]
+
+
+@pytest.mark.parametrize("N", [7, 20])
+@pytest.mark.parametrize("p,form", HI, ids=[f"P{p}-{f}" for p, f in HI])
+def test_tc_high_order_parity(B, p, form, N, monkeypatch):
+    monkeypatch.setenv("DOGIP_APPLY_VARIANT", "3")
+    ctx, P = make(B, 2, p, form, N)
+    u = inputs.rhs_normal(P.n, 1, seed=47)[:, 0].astype(np.float32)
+    u64 = u.astype(np.float64)
+    for _ in range(2):
+        y = ctx.apply(torch.tensor(u, device="cuda"), prec="fp32").cpu().numpy().astype(np.float64)
+        assert np.all(np.abs(y - P.apply(u64)) <= TOL32 * P.apply_abs(u64))
+    ctx.check()
+
+
+def test_tc_high_order_autotune_and_solve(B):
+    """The autotuner chooses between the run-time-table kernel and the tensor cores for
+    a high order; the mixed solve reaches the FP64 tolerance with its choice."""
+    ctx, P = make(B, 2, 5, "elliptic", 8)
+    t = ctx.autotune(force=True)
+    assert t["fp32"][0] in (1, 3)
+    b = ctx.load()
+    x, info = ctx.solve(b, mode="mixed", tol=1e-10)
+    bb = b.cpu().numpy()
+    assert info["status"] == 0
+    assert np.linalg.norm(bb - P.apply(x.cpu().numpy())) <= 1.01e-10 * np.linalg.norm(bb)
+    ctx.check()
+
+
 @pytest.mark.parametrize("p,form", [(2, "elliptic"), (3, "projection"), (4, "elliptic")])
 def test_tc_apply_parity_looping(B, p, form, monkeypatch):
     monkeypatch.setenv("DOGIP_APPLY_VARIANT", "3")
