@@ -812,12 +812,14 @@ def main():
         gw[f"P{p}"] = out
 
     _section("high_order")
-    # higher orders of Tables 3-4 (run-time-table kernels), same mesh and tensors
+    # higher orders of Tables 3-4, same mesh and tensors: the run-time-table kernels, or
+    # the tensor cores (FP32, p 5-6) where the autotuner finds them faster
     hi_ord = {}
     for p in (5, 6, 7, 8):
         c = B.Context(coords, cells, p, "elliptic", A)
         inf = c.info
-        out = {"dofs": c.n, "w_loc": inf.w_loc, "v_loc": inf.v_loc}
+        out = {"dofs": c.n, "w_loc": inf.w_loc, "v_loc": inf.v_loc,
+               "apply_kernel": c.autotune()}
         for prec, dt, s_ in (("fp32", torch.float32, 4), ("fp64", torch.float64, 8)):
             u = torch.randn(c.n, dtype=dt, device="cuda")
             y = torch.empty_like(u)
