@@ -38,9 +38,10 @@
  *
  * Environment variables read by dogip_setup (none is required):
  *  - DOGIP_APPLY_VARIANT: apply kernel until dogip_autotune decides (3 tensor cores
- *    for FP32 single-rhs applies where an instance exists (2D p <= 4, 3D p <= 2),
- *    else as 1; 2 self-feeding warps, 1 staged kernel (default), 0 one thread per
- *    cell).
+ *    for FP32 single-rhs applies where an instance exists (2D p <= 6, 2D p = 7
+ *    projection, 3D p <= 2), else as 1; 2 self-feeding warps, 1 staged kernel
+ *    (default), 0 one thread per cell; the orders above the compiled tables have
+ *    one CUDA-core kernel, taken for every value but 3).
  *  - DOGIP_TUNE_CACHE: file of autotuner choices (see dogip_autotune).
  *  - DOGIP_TEST_WAIT_CYCLES, DOGIP_TEST_SKIP_CHUNK: test hooks of the device-side
  *    failure path (a shorter bound on the kernels' waits, and one chunk of the
@@ -354,7 +355,8 @@ typedef struct {
  * Choose the apply kernel of this context per precision by timing the candidates
  * on its own data: the tensor-core kernel (FP32, where an instance exists), the
  * self-feeding-warps kernel, the bulk-async staged kernel, and the
- * one-thread-per-cell kernel with 64, 128 or 256 cells per CTA (median of 5
+ * one-thread-per-cell kernel with 64, 128 or 256 cells per CTA (orders above the
+ * compiled tables: the run-time-table kernel against the tensor cores, FP32 only) (median of 5
  * CUDA-event timings after 2 warm-up applies, atomic scatter, one right-hand side).
  * Applies with several right-hand sides use the staged kernel where it exists
  * (FP32 with nrhs a multiple of 4 and V_T <= 10 always), and the choice otherwise.  Choices are cached for the process
