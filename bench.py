@@ -43,7 +43,7 @@ L2_FLUSH_BYTES = 512 << 20
 # again whenever that kernel changes.
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one P4 FP32 launch, per kernel variant
 TRAFFIC_P4_FP32 = {1: 252637696,   # staged apply: 241,421,824 read + 11,215,872 written
-                   3: 252793344}   # tensor cores: 241,417,472 read + 11,375,872 written
+                   3: 251405824}   # tensor cores: 241,437,696 read + 9,968,128 written
 KERNEL_P4_FP32 = {0: "k_apply<2,4,ELLIPTIC,float> (one thread per cell)",
                   1: "k_apply_tma<2,4,ELLIPTIC,float> (staged apply)",
                   2: "k_apply_sfw<2,4,ELLIPTIC,float> (self-feeding warps)",
