@@ -1,8 +1,9 @@
 // tcgen05 (5th-generation tensor core) helpers for sm_100-family GPUs: tensor-memory
-// allocation, shared-memory matrix descriptors, single-CTA MMA issue with an mbarrier
-// commit, tensor-memory loads, and the TF32 hi/lo operand split.
+// allocation, loads and stores, shared-memory matrix descriptors, single-CTA MMA issue
+// (A in tensor memory, B in shared memory) with an mbarrier commit, and the TF32 hi/lo
+// operand split.
 //
-// Operand layout used throughout ("K-major, no swizzle"): a matrix of R rows (M or N,
+// Shared-memory operand layout ("K-major, no swizzle"): a matrix of R rows (M or N,
 // a multiple of 8) and K columns (a multiple of 8, 32-bit elements) is stored as core
 // matrices of 8 rows x 16 bytes (8 x 4 elements, 128 contiguous bytes).  Core matrices
 // adjacent along the rows are 128 bytes apart (stride byte offset), those adjacent
@@ -60,15 +61,6 @@ __device__ __forceinline__ void fence_after_sync() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// D[tmem] (+)= A[smem] * B[smem]^T, issued by one thread.
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
 // D[tmem] (+)= A[tmem] * B[smem]^T, issued by one thread: A is M rows (lanes) by K
 // 32-bit columns starting at column a_tmem.
 __device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc,
@@ -103,20 +95,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Store 16 consecutive 32-bit columns of this thread's tensor-memory lane
-// (tmem_st_wait completes this thread's stores).
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-      "%11, %12, %13, %14, %15, %16};" ::"r"(taddr),
-      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
-      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
-      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
-      "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
-      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
-      "r"(__float_as_uint(v[15]))
-      : "memory");
-}
 // Store 8 consecutive 32-bit columns of this thread's tensor-memory lane.
 __device__ __forceinline__ void tmem_st8(uint32_t taddr, const float* v) {
   asm volatile(
