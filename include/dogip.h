@@ -39,7 +39,7 @@
  * Environment variables read by dogip_setup (none is required):
  *  - DOGIP_APPLY_VARIANT: apply kernel until dogip_autotune decides (3 tensor cores
  *    for FP32 single-rhs applies where an instance exists (2D p <= 6, 2D p = 7
- *    projection, 3D p <= 2), else as 1; 2 self-feeding warps, 1 staged kernel
+ *    projection, 3D p <= 2, 3D p = 4 projection), else as 1; 2 self-feeding warps, 1 staged kernel
  *    (default), 0 one thread per cell; the orders above the compiled tables have
  *    one CUDA-core kernel, taken for every value but 3).
  *  - DOGIP_TUNE_CACHE: file of autotuner choices (see dogip_autotune).

@@ -411,7 +411,7 @@ bool apply_tc_available(int d, int p, int form) {
   if (d == D && p == P) return ell ? TcCfg<D, P, DOGIP_ELLIPTIC>::OK : TcCfg<D, P, DOGIP_PROJECTION>::OK;
   DOGIP_TC_OK(2, 1) DOGIP_TC_OK(2, 2) DOGIP_TC_OK(2, 3) DOGIP_TC_OK(2, 4)
   DOGIP_TC_OK(2, 5) DOGIP_TC_OK(2, 6) DOGIP_TC_OK(2, 7)
-  DOGIP_TC_OK(3, 1) DOGIP_TC_OK(3, 2)
+  DOGIP_TC_OK(3, 1) DOGIP_TC_OK(3, 2) DOGIP_TC_OK(3, 4)
 #undef DOGIP_TC_OK
   return false;
 }
@@ -437,6 +437,7 @@ bool apply_tc(const Ctx& c, const void* u, void* y, cudaStream_t s, const int* s
   DOGIP_TC_CASE(2, 7)
   DOGIP_TC_CASE(3, 1)
   DOGIP_TC_CASE(3, 2)
+  DOGIP_TC_CASE(3, 4)
 #undef DOGIP_TC_CASE
   return false;
 }

@@ -63,8 +63,18 @@ HI = [(5, "elliptic"), (5, "projection"), (6, "elliptic"), (6, "projection"), (7
 @pytest.mark.parametrize("N", [7, 20])
 @pytest.mark.parametrize("p,form", HI, ids=[f"P{p}-{f}" for p, f in HI])
 def test_tc_high_order_parity(B, p, form, N, monkeypatch):
+    _hi_parity(B, 2, p, form, N, monkeypatch)
+
+
+# 3D P4 projection (Table 2, k = 4): 48 and 384 tetrahedra
+@pytest.mark.parametrize("N", [2, 4])
+def test_tc_3d_p4_projection_parity(B, N, monkeypatch):
+    _hi_parity(B, 3, 4, "projection", N, monkeypatch)
+
+
+def _hi_parity(B, d, p, form, N, monkeypatch):
     monkeypatch.setenv("DOGIP_APPLY_VARIANT", "3")
-    ctx, P = make(B, 2, p, form, N)
+    ctx, P = make(B, d, p, form, N)
     u = inputs.rhs_normal(P.n, 1, seed=47)[:, 0].astype(np.float32)
     u64 = u.astype(np.float64)
     for _ in range(2):
