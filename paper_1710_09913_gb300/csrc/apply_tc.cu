@@ -1,11 +1,11 @@
 // Tensor-core (tcgen05) variant of the FP32 apply, Algorithm 1 with the two
 // contractions against the reference table B^ on the 5th-generation tensor cores.
 //
-// Per tile of 128 cells (one per thread of the four consumer warps):
+// Per tile of 128 cells (one per thread of a warpgroup):
 //   GEMM 1   G[128 x NC] = U[128 x V] . B1[V x NC]        (interpolation B^ u_T,
 //            NC = NB * W_T values or reference-gradient components per cell)
 //   CUDA     H_j = A^_T,j G_j per W node (scalar or packed symmetric d x d block),
-//            A^_T read from the shared-memory ring
+//            A^_T read from the warpgroup's shared-memory stage
 //   GEMM 2   Y[128 x V] = H[128 x NC] . B2[NC x V]        (projection B^* h)
 //   scatter  y += P_T^T Y_T with FP32 atomics.
 // The operands are FP32 values split as hi + lo with hi rounded to TF32; each GEMM
