@@ -10,7 +10,8 @@ file emulates that arithmetic with numpy on the oracle's B^ and A_T:
   |y - y_oracle| <= 2e-5 (|B^|^T |A_T| |B^| |u|) componentwise (here below 1e-7 of
   the scale), and its norm-wise error is of the order of the FP32 unit roundoff
   (measured on a GB300: 7.3e-7 at 2D P4);
-* a single TF32 product (hi.hi, no split) breaks that bound, which is why the kernel
+* a single TF32 product of the unsplit operands (what the tensor core makes of raw
+  FP32 values: both truncated to TF32) breaks that bound, which is why the kernel
   pays three MMAs per k-step.
 """
 
@@ -41,8 +42,8 @@ def split(x):
 
 def gemm_tc(A, Bm, three=True):
     """A [M, K] . Bm [K, N] as the kernel issues it: per k-step of 8, the TF32
-    products (hi.hi + hi.lo + lo.hi, or hi.hi alone) summed exactly and added to an
-    FP32 accumulator."""
+    products (hi.hi + hi.lo + lo.hi, or one product of the truncated unsplit operands)
+    summed exactly and added to an FP32 accumulator."""
     K = A.shape[1]
     Kp = (K + 7) // 8 * 8
     A = np.pad(A.astype(np.float32), ((0, 0), (0, Kp - K)))
