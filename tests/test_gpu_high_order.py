@@ -91,4 +91,4 @@ def test_high_order_unbuilt_operations(B):
     with pytest.raises(B.DogipError) as e:
         B.Context(coords, cells, 6, "elliptic", np.ones(len(cells)), factorized=True)
     assert e.value.code == B.EUNSUPPORTED
-    ctx.autotune()  # nothing to tune; must not fail
+    ctx.autotune()  # the run-time-table kernel against the tensor cores; must not fail
