@@ -38,17 +38,13 @@ WORKLOAD = ("2D scalar elliptic, unit square, 512x512 grid x 2 triangles (524,28
             "eigenvalues, uniform rotation), f = 1, zero Dirichlet; P1-P4 sweep; "
             "mixed FP32 PCG + FP64 refinement to 1e-8")
 L2_FLUSH_BYTES = 512 << 20
-# DRAM bytes (read + write) of one launch of the staged P4 FP32 apply on this workload,
-# from the ncu capture summarised in profiles/k_apply_tma_2d_p4_fp32.md; to be taken
-# again whenever that kernel changes.
-# ncu dram__bytes_read.sum + dram__bytes_write.sum of one P4 FP32 launch, per kernel variant
-TRAFFIC_P4_FP32 = {1: 252637696,   # staged apply: 241,421,824 read + 11,215,872 written
-                   3: 251405824}   # tensor cores: 241,437,696 read + 9,968,128 written
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one P4 FP32 launch of each apply
+# kernel on this workload (None: not captured since the kernel last changed)
+TRAFFIC_P4_FP32 = {1: None, 3: None}
 KERNEL_P4_FP32 = {0: "k_apply<2,4,ELLIPTIC,float> (one thread per cell)",
                   1: "k_apply_tma<2,4,ELLIPTIC,float> (staged apply)",
                   2: "k_apply_sfw<2,4,ELLIPTIC,float> (self-feeding warps)",
                   3: "k_apply_tc<2,4,ELLIPTIC> (tensor cores, tcgen05)"}
-PROFILE_P4_FP32 = {1: "profiles/k_apply_tma_2d_p4_fp32.md", 3: "profiles/k_apply_tc_2d_p4_fp32.md"}
 
 
 def mesh_and_coef():
@@ -501,11 +497,23 @@ def main():
             ev1.record(stream)
             torch.cuda.synchronize()
             ms = ev0.elapsed_time(ev1) / reps
+            # the kernel alone: dogip_apply_add (y += K u) enqueues exactly the apply
+            # kernel, without the clearing of y that dogip_apply puts before it
+            for _ in range(3):
+                c.apply_add(u, y, prec=prec)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(reps):
+                c.apply_add(u, y, prec=prec)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            kms = ev0.elapsed_time(ev1) / reps
             bytes_alg = E * inf.w_loc * inf.n_sym * s + E * inf.v_loc * 4 + 2 * c.n * s
             flops_alg = E * (2 * inf.nnz_b + 2 * (inf.nnz_b - inf.nnz_pm1_b) + (2 * 4 - 2) * inf.w_loc)
             applies[f"P{p}_{prec}"] = {"ms": round(ms, 4), "gdofs": round(c.n / ms / 1e6, 3),
-                                       "GBps": round(bytes_alg / ms / 1e6, 1),
-                                       "TFLOPs": round(flops_alg / ms / 1e9, 3),
+                                       "kernel_ms": round(kms, 4),
+                                       "GBps": round(bytes_alg / kms / 1e6, 1),
+                                       "TFLOPs": round(flops_alg / kms / 1e9, 3),
                                        "alg_bytes": int(bytes_alg), "alg_flops": int(flops_alg)}
     _section("csr")
     # assembled CSR on the same GPU: SpMV bandwidth and FP64 PCG time-to-tolerance
@@ -695,45 +703,41 @@ def main():
         del cf
 
     _section("tensor_core")
-    # the tcgen05 kernel (3xTF32 contractions in tensor memory), forced for FP32 applies
-    # on contexts of its own: the autotuner times it beside the CUDA-core kernels
+    # the tcgen05 kernel (3xTF32 contractions in tensor memory), selected by prec = TF32 on
+    # the same contexts; kernel-only times (dogip_apply_add) beside the autotuned FP32 kernel
     tcore = {}
-    os.environ["DOGIP_APPLY_VARIANT"] = "3"
-    try:
-        for p in P_LIST:
-            ct = B.Context(coords, cells, p, "elliptic", A)
-            u = torch.randn(ct.n, dtype=torch.float32, device="cuda")
-            y = torch.empty_like(u)
-            for _ in range(3):
-                ct.apply(u, y, prec="fp32")
-            ev0 = torch.cuda.Event(enable_timing=True)
-            ev1 = torch.cuda.Event(enable_timing=True)
+    for p in P_LIST:
+        ct = ctxs[p]
+        u = torch.randn(ct.n, dtype=torch.float32, device="cuda")
+        y = torch.zeros_like(u)
+        for _ in range(3):
+            ct.apply_add(u, y, prec="tf32")
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(20):
+            ct.apply_add(u, y, prec="tf32")
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / 20
+        inf = ct.info
+        byt = E * inf.w_loc * inf.n_sym * 4 + E * inf.v_loc * 4 + 2 * ct.n * 4
+        out = {"kernel_ms": round(ms, 4), "apply_tf32_GBps": round(byt / ms / 1e6, 1),
+               "vs_autotuned_fp32": round(applies[f"P{p}_fp32"]["kernel_ms"] / ms, 3)}
+        if p == max(P_LIST):
+            ux = torch.zeros_like(bs[p])
             torch.cuda.synchronize()
             ev0.record(stream)
-            for _ in range(20):
-                ct.apply(u, y, prec="fp32")
+            _, info = ct.solve(bs[p], ux, mode="mixed", tol=TOL, check_every=args.check_every,
+                               inner_prec="tf32")
             ev1.record(stream)
             torch.cuda.synchronize()
-            ms = ev0.elapsed_time(ev1) / 20
-            inf = ct.info
-            byt = E * inf.w_loc * inf.n_sym * 4 + E * inf.v_loc * 4 + 2 * ct.n * 4
-            out = {"apply_fp32_ms": round(ms, 4), "apply_fp32_GBps": round(byt / ms / 1e6, 1),
-                   "vs_autotuned_fp32": round(applies[f"P{p}_fp32"]["ms"] / ms, 3)}
-            if p == max(P_LIST):
-                b = ct.load()
-                ux = torch.zeros_like(b)
-                torch.cuda.synchronize()
-                ev0.record(stream)
-                _, info = ct.solve(b, ux, mode="mixed", tol=TOL, check_every=args.check_every)
-                ev1.record(stream)
-                torch.cuda.synchronize()
-                out["mixed_ms"] = round(ev0.elapsed_time(ev1), 2)
-                out["mixed_iters"] = info["iterations"]
-            ct.check()
-            tcore[f"P{p}"] = out
-            del ct
-    finally:
-        del os.environ["DOGIP_APPLY_VARIANT"]
+            out["mixed_tf32_ms"] = round(ev0.elapsed_time(ev1), 2)
+            out["mixed_tf32_iters"] = info["iterations"]
+            out["mixed_tf32_rel_residual"] = info["rel_residual"]
+        ct.check()
+        tcore[f"P{p}"] = out
 
     _section("qp")
     # the conventional quadrature-point matrix-free apply on the same GPU (comparator):
@@ -844,16 +848,96 @@ def main():
         del c
         torch.cuda.empty_cache()
 
+    _section("scatter_compare")
+    # the final add of Algorithm 1 by element colouring (one pass per colour, plain
+    # adds, deterministic) against the atomic scatter of the headline kernel; colour
+    # needs colour-sorted element storage, so it runs on contexts set up for it
+    scat = {}
+    for p in P_LIST:
+        cc = B.Context(coords, cells, p, "elliptic", A, scatter="colour")
+        out = {"n_colours": int(cc.info.n_colours)}
+        for prec, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
+            u = torch.randn(cc.n, dtype=dt, device="cuda")
+            y = torch.empty_like(u)
+            y2 = torch.empty_like(u)
+            cc.apply(u, y, prec=prec, scatter="colour")
+            reps = 10
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(reps):
+                cc.apply(u, y2, prec=prec, scatter="colour")
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            out[f"colour_{prec}_ms"] = round(ev0.elapsed_time(ev1) / reps, 4)
+            out[f"atomic_{prec}_ms"] = applies[f"P{p}_{prec}"]["ms"]
+            out[f"colour_{prec}_bitwise_repeatable"] = bool(torch.equal(y, y2))
+            ya = ctxs[p].apply(u, prec=prec)
+            yb = ctxs[p].apply(u, prec=prec)
+            out[f"atomic_{prec}_bitwise_repeatable"] = bool(torch.equal(ya, yb))
+            out[f"colour_vs_atomic_{prec}_max_rel"] = float((y - ya).abs().max() / ya.abs().max())
+            del u, y, y2, ya, yb
+        if p <= 2:
+            ux = torch.zeros_like(bs[p])
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            _, info = cc.solve(bs[p], ux, mode="mixed", tol=TOL, check_every=args.check_every,
+                               scatter="colour")
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            out["mixed_colour_ms"] = round(ev0.elapsed_time(ev1), 2)
+            out["mixed_atomic_ms"] = t2t["mixed_ms"][f"P{p}"]
+        scat[f"P{p}"] = out
+        del cc
+        torch.cuda.empty_cache()
+
+    _section("gradient")
+    # differentiation workload: compliance J = b^T u(A) of FP32 leaf SPD tensors
+    # (log-eigenvalues N(0, 0.5^2)), forward mixed solve and backward (adjoint solve +
+    # W-node outer product) through torch.autograd, at 256^2 x 2 P3 and 32^3 x 6 P1
+    grad = {}
+    from paper_1710_09913_gb300 import autograd as AG
+    from paper_1710_09913_gb300 import inputs as _gi
+    for d, p, N in ((2, 3, 256), (3, 1, 32)):
+        gc, gcl = _gi.lattice_mesh(d, N)
+        A32 = _gi.coef_tensor_lognormal(len(gcl), d, 0.5, 4).astype(np.float32)
+        op = B.Context(gc, gcl, p, "elliptic", A32.astype(np.float64))
+        b = op.load()
+        times = {"forward_ms": [], "backward_ms": []}
+        for it in range(3):
+            leaf = torch.tensor(A32, device="cuda", requires_grad=True)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev2 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            J = AG.compliance(leaf, b, op, mode="mixed", tol=TOL, check_every=args.check_every)
+            ev1.record(stream)
+            J.backward()
+            ev2.record(stream)
+            torch.cuda.synchronize()
+            if it > 0:  # the first pass captures the solver graphs
+                times["forward_ms"].append(ev0.elapsed_time(ev1))
+                times["backward_ms"].append(ev1.elapsed_time(ev2))
+        grad[f"{d}D_P{p}_N{N}"] = {"cells": len(gcl), "dofs": op.n,
+                                   "forward_ms": round(float(np.median(times["forward_ms"])), 2),
+                                   "backward_ms": round(float(np.median(times["backward_ms"])), 2),
+                                   "grad_cells_per_s": round(len(gcl) / (np.median(times["backward_ms"]) * 1e-3))}
+        del op, b, leaf
+        torch.cuda.empty_cache()
+
     _section("roofline")
     dom = applies["P4_fp32"]
     var4 = tuned["P4"]["fp32"][0]
     roofline = {"bound": "hbm", "achieved": dom["GBps"], "peak": hbm, "unit": "GB/s",
                 "frac": round(dom["GBps"] / hbm, 4),
                 "traffic": TRAFFIC_P4_FP32.get(var4),
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch "
-                                  f"({PROFILE_P4_FP32.get(var4, 'not captured for this kernel')})",
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of "
+                                  f"{KERNEL_P4_FP32.get(var4, var4)} on this workload",
                 "kernel": f"{KERNEL_P4_FP32.get(var4, var4)}, 2D P4, 524,288 cells; "
-                          "timed as 30 back-to-back dogip_apply calls (y memset + kernel)",
+                          "30 back-to-back launches through dogip_apply_add (one kernel each), "
+                          "CUDA events on the launching stream",
                 "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
                 "alg_bytes_per_launch": dom["alg_bytes"]}
 
@@ -908,7 +992,7 @@ def main():
                 "time_to_tol": t2t, "apply": applies, "csr_baseline": csr, "batch_uneven": batch,
                 "cube_p2_16rhs": multi, "factorized": fact, "quadrature_point_comparator": qp,
                 "global_double_grid_projection": gw, "high_order": hi_ord,
-                "tensor_core_apply": tcore,
+                "tensor_core_apply": tcore, "scatter_compare": scat, "gradient": grad,
                 "roofline": roofline,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks}
         print(json.dumps(line), flush=True)

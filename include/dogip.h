@@ -69,7 +69,10 @@ extern "C" {
 #define DOGIP_ECUDA 3       /* a CUDA runtime call failed                       */
 #define DOGIP_ENOTCONV 4    /* solver hit its iteration limit (result written)  */
 #define DOGIP_EBREAKDOWN 5  /* CG breakdown: p^T K p <= 0 or not finite         */
-#define DOGIP_ETIMEOUT 6    /* a host-side wait exceeded its time limit         */
+#define DOGIP_ETIMEOUT 6    /* a time limit expired: a solve's host wall-clock
+                               limit (timeout_ms), or a bounded wait inside a
+                               kernel (copy or tensor-core completion), which
+                               then returned without finishing its work      */
 #define DOGIP_EUNSUPPORTED 7 /* valid request outside the compiled instances    */
 
 /* ------------------------------------------------------------ enumerations */
@@ -83,6 +86,14 @@ extern "C" {
 
 #define DOGIP_FP64 0        /* FP64 storage and arithmetic                     */
 #define DOGIP_FP32 1        /* FP32 A_T, vectors and arithmetic                */
+#define DOGIP_TF32 2        /* FP32 A_T and vectors; the two contractions with B
+                               (interpolation B u_T, projection B^* h) on the
+                               tensor cores as three TF32 products each (hi*hi +
+                               hi*lo + lo*hi of a split FP32 operand, FP32
+                               accumulation, about 2^-21 relative per product);
+                               one right-hand side, atomic scatter, element-wise
+                               A_T, instances 2D p <= 6 (p = 7: projection) and
+                               3D p <= 2 (p = 4: projection)                    */
 
 #define DOGIP_SCATTER_ATOMIC 0 /* one pass, atomic adds (order not fixed)      */
 #define DOGIP_SCATTER_COLOUR 1 /* one pass per element colour, plain adds      */
@@ -135,7 +146,10 @@ DOGIP_API int dogip_opts_default(dogip_opts* o);
  * colouring, reference tables B and w (Theorems above), and -- on the device --
  * the element factors A_T (dogip_set_coef) and the Jacobi diagonal.
  *   m       : mesh (host), copied.
- *   p       : polynomial order, 1 <= p <= 4.
+ *   p       : polynomial order: 1..8 on triangles, 1..4 on tetrahedra (2D p <= 4
+ *             and 3D p <= 3 with compile-time tables, the higher orders with the
+ *             run-time-table kernels, which build the apply, precompute, load and
+ *             both solvers only).
  *   form    : DOGIP_PROJECTION or DOGIP_ELLIPTIC.
  *   coef_kind, coef : host coefficients in caller cell order, [n_cells] for
  *             DOGIP_COEF_ELEM_SCALAR or [n_cells x dim x dim] for
@@ -254,7 +268,8 @@ DOGIP_API int dogip_get_tables(int dim, int p, int form, double* bhat, double* w
  *   u, y  : DEVICE [n_dofs x nrhs], double (DOGIP_FP64) or float (DOGIP_FP32);
  *           y is overwritten; u and y must not overlap.
  *   nrhs  : >= 1.
- *   prec  : DOGIP_FP64 or DOGIP_FP32 (the latter needs keep_fp32).
+ *   prec  : DOGIP_FP64, DOGIP_FP32 or DOGIP_TF32 (the latter two need keep_fp32;
+ *           TF32 returns DOGIP_EUNSUPPORTED outside its instances, see above).
  *   scatter: DOGIP_SCATTER_ATOMIC, or DOGIP_SCATTER_COLOUR (needs a context
  *           set up with scatter = COLOUR), or -1 for the context default.
  * Asynchronous on cuda_stream; no host synchronisation.  A global_w context keeps
@@ -264,6 +279,17 @@ DOGIP_API int dogip_get_tables(int dim, int p, int form, double* bhat, double* w
  */
 DOGIP_API int dogip_apply(dogip_ctx* ctx, const void* u, void* y, int nrhs, int prec,
                 int scatter, void* cuda_stream);
+
+/*
+ * y += K u: the same operator as dogip_apply (Algorithm 1 with the Dirichlet rows
+ * y_b += u_b), added into the caller's y instead of overwriting it, so y is not
+ * cleared first.  With the staged, self-feeding or tensor-core kernel (atomic
+ * scatter over the whole mesh) the call enqueues exactly one kernel.  Arguments,
+ * layout, precisions and errors as dogip_apply; y must hold valid numbers.
+ * Asynchronous on cuda_stream.
+ */
+DOGIP_API int dogip_apply_add(dogip_ctx* ctx, const void* u, void* y, int nrhs, int prec,
+                              int scatter, void* cuda_stream);
 
 /*
  * Comparator, not the DoGIP path: the conventional quadrature-point matrix-free
@@ -304,6 +330,9 @@ typedef struct {
   double timeout_ms;  /* host wall-clock limit, <= 0 for none                  */
   double reliable_delta; /* MIXED_RELIABLE: FP64 correction when the FP32
                             residual has dropped by this factor (0.1)         */
+  int inner_prec;     /* mixed modes: applies of the inner solves, DOGIP_FP32
+                         (default, CUDA cores) or DOGIP_TF32 (tensor cores;
+                         nrhs 1, atomic scatter, else DOGIP_EUNSUPPORTED)      */
 } dogip_solve_opts;
 
 typedef struct {
@@ -407,7 +436,8 @@ DOGIP_API int dogip_grad_coef(dogip_ctx* ctx, const double* u, const double* lam
 /*
  * Synchronise cuda_stream and report device-side failures of earlier asynchronous
  * calls on this context: DOGIP_ETIMEOUT if a bounded wait inside a kernel (the
- * staged apply's shared-memory pipeline) gave up; the flag is then cleared.
+ * copy pipelines of the staged and self-feeding applies, the copy and MMA waits of
+ * the tensor-core apply) gave up; the flag is then cleared.
  */
 DOGIP_API int dogip_check(dogip_ctx* ctx, void* cuda_stream);
 
@@ -418,20 +448,26 @@ DOGIP_API int dogip_check(dogip_ctx* ctx, void* cuda_stream);
  * a framework whose allocator owns all device memory and forbids raw cudaMalloc,
  * a latency-critical loop that cannot afford cudaMalloc/cudaFree (cudaFree
  * synchronises the device), a process held to a fixed device-memory budget.
- * It computes, with the same fused reduction as dogip_solve's residual check,
+ * It computes, in FP64 with a fused grid reduction in a fixed order (the result
+ * does not change from run to run),
  *     r = b - Ky,   rel[k] = ||r_k||_2 / ||b_k||_2   (0 where b_k = 0),
- * for Ky = dogip_apply(u): rel is exactly the relative residual dogip_solve reports.
+ * for Ky = dogip_apply(u): rel equals the relative residual dogip_solve reports to
+ * within FP64 rounding (the two reductions add in different orders).
  *   b, Ky : DEVICE double [n x nrhs] (dof-major); r: DEVICE [n x nrhs] or NULL;
- *   rel   : DEVICE double [nrhs];  1 <= nrhs <= 32 (else DOGIP_EINVAL).
+ *   rel   : DEVICE double [nrhs];  1 <= nrhs <= 32 (else DOGIP_EINVAL); n >= 0
+ *           (b and Ky may be NULL when n = 0).
+ * The arrays must be on the current device and hold the stated sizes: without a
+ * context the call cannot check them.
  * No context is needed.  The reduction scratch is a fixed 128 KiB + 256 B array in
  * the library's device memory, present on every GPU that loads the library until
  * the process exits; no cudaMalloc, cudaFree or allocating library routine is
- * called.  The first call on a device resolves the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call before
- * any stream capture.  Every call shares the array and leaves it holding its last
- * contents (the ticket counter is cleared at the start of each call), so calls
- * whose work overlaps on the GPU -- on different streams, or from different host
- * threads -- race with each other and must be serialised by the caller.
+ * called.  Every call looks up the array's address on the current device
+ * (cudaGetSymbolAddress); the first lookup on a device may load the library's
+ * device code there, so make the first call on each device before any stream
+ * capture.  Every call shares the array and leaves it holding its last contents
+ * (the ticket counter is cleared at the start of each call), so calls whose work
+ * overlaps on the GPU -- on different streams, or from different host threads --
+ * race with each other and must be serialised by the caller.
  * Asynchronous on cuda_stream.
  */
 DOGIP_API int dogip_residual_norms_noalloc(const double* b, const double* Ky, double* r,

@@ -19,11 +19,11 @@ LIB_PATH = os.path.join(_HERE, "libdogip.so")
 OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, EBREAKDOWN, ETIMEOUT, EUNSUPPORTED = range(8)
 PROJECTION, ELLIPTIC = 0, 1
 COEF_ELEM_SCALAR, COEF_ELEM_TENSOR = 0, 1
-FP64, FP32 = 0, 1
+FP64, FP32, TF32 = 0, 1, 2
 SCATTER_ATOMIC, SCATTER_COLOUR = 0, 1
 SOLVE_FP64, SOLVE_MIXED, SOLVE_MIXED_RELIABLE = 0, 1, 2
 FORMS = {"projection": PROJECTION, "elliptic": ELLIPTIC}
-PRECS = {"fp64": FP64, "fp32": FP32}
+PRECS = {"fp64": FP64, "fp32": FP32, "tf32": TF32}
 SCATTERS = {"atomic": SCATTER_ATOMIC, "colour": SCATTER_COLOUR, None: -1}
 MODES = {"fp64": SOLVE_FP64, "mixed": SOLVE_MIXED, "mixed_reliable": SOLVE_MIXED_RELIABLE}
 
@@ -73,7 +73,8 @@ class SolveOpts(C.Structure):
     _fields_ = [("mode", C.c_int), ("tol", C.c_double), ("maxiter", C.c_int),
                 ("inner_tol", C.c_double), ("inner_maxiter", C.c_int), ("max_outer", C.c_int),
                 ("scatter", C.c_int), ("check_every", C.c_int), ("use_x0", C.c_int),
-                ("timeout_ms", C.c_double), ("reliable_delta", C.c_double)]
+                ("timeout_ms", C.c_double), ("reliable_delta", C.c_double),
+                ("inner_prec", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -103,6 +104,7 @@ _SIGS = {
     "dogip_get_wdofmap": (C.c_int, [_vp, _vp, _vp]),
     "dogip_get_tables": (C.c_int, [C.c_int, C.c_int, C.c_int, _vp, _vp, _vp]),
     "dogip_apply": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp]),
+    "dogip_apply_add": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp]),
     "dogip_apply_qp": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, _vp]),
     "dogip_load": (C.c_int, [_vp, _vp, _vp, _vp]),
     "dogip_solve_opts_default": (C.c_int, [C.POINTER(SolveOpts)]),
@@ -156,15 +158,30 @@ def _hptr(a, ctype):
 
 def residual_norms_noalloc(b, Ky, r=None, rel=None, stream=None):
     """||b - Ky|| / ||b|| per rhs on the device without any allocation by the
-    library (b, Ky: float64 CUDA [n] or [n, R]); returns rel (float64 CUDA [R])."""
+    library (b, Ky: float64 CUDA [n] or [n, R]); returns rel (float64 CUDA [R]).
+    The C entry point has no context to check sizes against, so this wrapper
+    checks them: Ky (and r) must have b's shape, rel at least R entries, and all
+    tensors must live on one GPU; the call runs with that GPU current."""
     import torch
+    if b.dim() not in (1, 2):
+        raise ValueError("b must be [n] or [n, R]")
     R = 1 if b.dim() == 1 else b.shape[1]
-    if rel is None:
-        rel = torch.empty(R, dtype=torch.float64, device=b.device)
-    rp = _dptr(r, torch.float64) if r is not None else None
-    _check(lib.dogip_residual_norms_noalloc(_dptr(b, torch.float64), _dptr(Ky, torch.float64), rp,
-                                            b.shape[0], R, _dptr(rel, torch.float64),
-                                            _stream(stream)))
+    if tuple(Ky.shape) != tuple(b.shape):
+        raise ValueError("Ky must have the shape of b")
+    if r is not None and tuple(r.shape) != tuple(b.shape):
+        raise ValueError("r must have the shape of b")
+    devs = {t.device for t in (b, Ky, r, rel) if t is not None}
+    if len(devs) != 1 or not b.is_cuda:
+        raise ValueError("b, Ky, r and rel must be CUDA tensors on one device")
+    with torch.cuda.device(b.device):
+        if rel is None:
+            rel = torch.empty(R, dtype=torch.float64, device=b.device)
+        if rel.numel() < R:
+            raise ValueError("rel must hold at least one entry per right-hand side")
+        rp = _dptr(r, torch.float64) if r is not None else None
+        _check(lib.dogip_residual_norms_noalloc(_dptr(b, torch.float64), _dptr(Ky, torch.float64),
+                                                rp, b.shape[0], R, _dptr(rel, torch.float64),
+                                                _stream(stream)))
     return rel
 
 
@@ -359,7 +376,7 @@ class Context:
         _check(lib.dogip_get_info(self._h, C.byref(self.info)))
 
     def apply(self, u, y=None, prec="fp64", scatter=None, stream=None):
-        """y = K u for u [n] or [n, R] (float64 for fp64, float32 for fp32)."""
+        """y = K u for u [n] or [n, R] (float64 for fp64, float32 for fp32 and tf32)."""
         import torch
         pr = PRECS.get(prec, prec)
         dt = torch.float64 if pr == FP64 else torch.float32
@@ -368,8 +385,22 @@ class Context:
             raise ValueError("u has the wrong number of dofs")
         if y is None:
             y = torch.empty_like(u)
+        if tuple(y.shape) != tuple(u.shape):
+            raise ValueError("y must have the shape of u")
         _check(lib.dogip_apply(self._h, _dptr(u, dt), _dptr(y, dt), R, pr, SCATTERS[scatter],
                                _stream(stream)))
+        return y
+
+    def apply_add(self, u, y, prec="fp64", scatter=None, stream=None):
+        """y += K u (dogip_apply_add): one kernel launch, y is not cleared."""
+        import torch
+        pr = PRECS.get(prec, prec)
+        dt = torch.float64 if pr == FP64 else torch.float32
+        R = 1 if u.dim() == 1 else u.shape[1]
+        if u.shape[0] != self.n or tuple(y.shape) != tuple(u.shape):
+            raise ValueError("u and y must both be [n] or [n, R]")
+        _check(lib.dogip_apply_add(self._h, _dptr(u, dt), _dptr(y, dt), R, pr, SCATTERS[scatter],
+                                   _stream(stream)))
         return y
 
     def apply_qp(self, u, y=None, prec="fp64", stream=None):
@@ -395,7 +426,7 @@ class Context:
         return b
 
     def _solve_opts(self, mode, tol, maxiter, inner_tol, inner_maxiter, max_outer, scatter,
-                    check_every, x0, timeout_ms, reliable_delta=None):
+                    check_every, x0, timeout_ms, reliable_delta=None, inner_prec=None):
         o = SolveOpts()
         lib.dogip_solve_opts_default(C.byref(o))
         o.mode = MODES.get(mode, mode)
@@ -415,18 +446,22 @@ class Context:
         o.timeout_ms = timeout_ms
         if reliable_delta is not None:
             o.reliable_delta = reliable_delta
+        if inner_prec is not None:
+            o.inner_prec = PRECS.get(inner_prec, inner_prec)
         return o
 
     def solve(self, b, u=None, *, mode="fp64", tol=1e-8, maxiter=None, inner_tol=None,
               inner_maxiter=None, max_outer=None, scatter=None, check_every=None, x0=False,
-              timeout_ms=0.0, stream=None, allow_notconv=False, reliable_delta=None):
-        """Solve K u = b on the device; returns (u, info dict)."""
+              timeout_ms=0.0, stream=None, allow_notconv=False, reliable_delta=None,
+              inner_prec=None):
+        """Solve K u = b on the device; returns (u, info dict).  inner_prec ("fp32" or
+        "tf32") selects the applies of the mixed modes' inner solves."""
         import torch
         R = 1 if b.dim() == 1 else b.shape[1]
         if u is None:
             u = torch.zeros_like(b)
         o = self._solve_opts(mode, tol, maxiter, inner_tol, inner_maxiter, max_outer, scatter,
-                             check_every, x0, timeout_ms, reliable_delta)
+                             check_every, x0, timeout_ms, reliable_delta, inner_prec)
         inf = SolveInfo()
         rel = np.zeros(R)
         code = lib.dogip_solve(self._h, _dptr(b, torch.float64), _dptr(u, torch.float64), R,

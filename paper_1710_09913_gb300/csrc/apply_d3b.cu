@@ -2,7 +2,7 @@
 #include "apply_inst.cuh"
 namespace dogip {
 int apply_d3b(const Ctx& c, const void* u, void* y, int R, int prec, bool atomic,
-                 int64_t e0, int64_t e1, cudaStream_t s, const int* skip) {
+                 int64_t e0, int64_t e1, cudaStream_t s, const int* skip, bool add) {
   switch (c.p * 2 + c.form) {
     DOGIP_APPLY_CASES(3, 3)
     default:

@@ -180,7 +180,7 @@ void hi_attr() {
 
 template <int D, int P, int FORM>
 int hi_run(const Ctx& c, int op, const void* u, void* y, int R, int prec, bool atomic, int64_t e0,
-           int64_t e1, cudaStream_t s, const int* skip, AhatArgs* ah, LoadArgs* ld) {
+           int64_t e1, cudaStream_t s, const int* skip, AhatArgs* ah, LoadArgs* ld, bool add) {
   using C = HiCfg<D, P, FORM>;
   if (op == 0) {  // apply
     if (u == nullptr) {  // preparation call (context set-up, outside capture)
@@ -192,7 +192,7 @@ int hi_run(const Ctx& c, int op, const void* u, void* y, int R, int prec, bool a
     // variant 3: the tensor-core kernel (FP32, one right-hand side, whole range)
     const int var = c.apply_variant_prec[prec] >= 0 ? c.apply_variant_prec[prec] : c.apply_variant;
     if (var == 3 && prec == DOGIP_FP32 && R == 1 && atomic && e0 == 0 && e1 == c.E &&
-        apply_tc(c, u, y, s, skip))
+        apply_tc(c, u, y, s, skip, add))
       return 2;
     const int64_t nth = (e1 - e0) * (int64_t)R;
     if (nth <= 0) return 1;
@@ -223,10 +223,10 @@ int hi_run(const Ctx& c, int op, const void* u, void* y, int R, int prec, bool a
 
 int hi_dispatch(const Ctx& c, int op, const void* u, void* y, int R, int prec, bool atomic,
                 int64_t e0, int64_t e1, cudaStream_t s, const int* skip, AhatArgs* ah,
-                LoadArgs* ld) {
+                LoadArgs* ld, bool add = false) {
 #define HI_CASE(D, P, F)                                                               \
   if (c.d == D && c.p == P && c.form == F)                                             \
-    return hi_run<D, P, F>(c, op, u, y, R, prec, atomic, e0, e1, s, skip, ah, ld);
+    return hi_run<D, P, F>(c, op, u, y, R, prec, atomic, e0, e1, s, skip, ah, ld, add);
   HI_CASE(2, 5, 0) HI_CASE(2, 5, 1) HI_CASE(2, 6, 0) HI_CASE(2, 6, 1)
   HI_CASE(2, 7, 0) HI_CASE(2, 7, 1) HI_CASE(2, 8, 0) HI_CASE(2, 8, 1)
   HI_CASE(3, 4, 0) HI_CASE(3, 4, 1)
@@ -237,8 +237,8 @@ int hi_dispatch(const Ctx& c, int op, const void* u, void* y, int R, int prec, b
 }  // namespace
 
 int apply_hi(const Ctx& c, const void* u, void* y, int R, int prec, bool atomic, int64_t e0,
-             int64_t e1, cudaStream_t s, const int* skip) {
-  return hi_dispatch(c, 0, u, y, R, prec, atomic, e0, e1, s, skip, nullptr, nullptr);
+             int64_t e1, cudaStream_t s, const int* skip, bool add) {
+  return hi_dispatch(c, 0, u, y, R, prec, atomic, e0, e1, s, skip, nullptr, nullptr, add);
 }
 
 bool ahat_hi(const Ctx& c, AhatArgs& a, cudaStream_t s) {

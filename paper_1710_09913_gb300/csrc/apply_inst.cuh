@@ -51,7 +51,7 @@ const TmaLaunch& tma_launch() {
 
 template <int D, int P, int FORM, typename T, bool FACT>
 void run_apply_tma(const T* A, const Ctx& c, const void* u, void* y, int R, cudaStream_t s,
-                   const int* skip) {
+                   const int* skip, bool add) {
   using Cfg = TmaCfg<D, P, FORM, T, FACT>;
   const TmaLaunch& L = tma_launch<D, P, FORM, T, FACT>();
   const int blocks_per_sm = L.blocks_per_sm, num_sms = L.num_sms;
@@ -62,7 +62,8 @@ void run_apply_tma(const T* A, const Ctx& c, const void* u, void* y, int R, cuda
   const bool r4 = sizeof(T) == 4 && R % 4 == 0 && ((uintptr_t)u & 15u) == 0 &&
                   ((uintptr_t)y & 15u) == 0;
   TmaArgs<T> a{A, c.d_conn, (const T*)u, (T*)y, c.E, ntiles, nchunks, R, skip, c.d_kerr,
-                c.d_bnd, c.dirichlet ? c.nbnd : 0, c.wait_budget, c.test_skip_chunk, r4 ? 1 : 0};
+                c.d_bnd, c.dirichlet ? c.nbnd : 0, c.wait_budget, c.test_skip_chunk, r4 ? 1 : 0,
+                stream_evict_first(c, sizeof(T), FACT ? Cfg::NS : Cfg::W * Cfg::NS), add ? 1 : 0};
   k_apply_tma<D, P, FORM, T, FACT><<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
 }
 
@@ -88,7 +89,7 @@ const TmaLaunch& sfw_launch() {
 
 template <int D, int P, int FORM, typename T>
 void run_apply_sfw(const T* A, const Ctx& c, const void* u, void* y, cudaStream_t s,
-                   const int* skip) {
+                   const int* skip, bool add) {
   using Cfg = SfwCfg<D, P, FORM, T>;
   const TmaLaunch& L = sfw_launch<D, P, FORM, T>();
   const int64_t ntiles = (c.E + kTile - 1) / kTile;
@@ -96,7 +97,8 @@ void run_apply_sfw(const T* A, const Ctx& c, const void* u, void* y, cudaStream_
   const int64_t grid = std::min<int64_t>((ntiles + Cfg::NW - 1) / Cfg::NW,
                                          (int64_t)L.num_sms * L.blocks_per_sm);
   TmaArgs<T> a{A, c.d_conn, (const T*)u, (T*)y, c.E, ntiles, 0, 1, skip, c.d_kerr,
-                c.d_bnd, c.dirichlet ? c.nbnd : 0, c.wait_budget, c.test_skip_chunk, 0};
+                c.d_bnd, c.dirichlet ? c.nbnd : 0, c.wait_budget, c.test_skip_chunk, 0,
+                stream_evict_first(c, sizeof(T), Cfg::W * Cfg::NS), add ? 1 : 0};
   k_apply_sfw<D, P, FORM, T><<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
 }
 
@@ -104,7 +106,7 @@ void run_apply_sfw(const T* A, const Ctx& c, const void* u, void* y, cudaStream_
 // one-thread-per-cell kernel.
 template <int D, int P, int FORM>
 int run_apply(const Ctx& c, const void* u, void* y, int R, int prec, bool atomic, int64_t e0,
-              int64_t e1, cudaStream_t s, const int* skip) {
+              int64_t e1, cudaStream_t s, const int* skip, bool add) {
   constexpr bool ok64 = TmaCfg<D, P, FORM, double>::OK, ok32 = TmaCfg<D, P, FORM, float>::OK;
   if (u == nullptr) {  // preparation call from context set-up
     if (c.factorized) {
@@ -120,24 +122,24 @@ int run_apply(const Ctx& c, const void* u, void* y, int R, int prec, bool atomic
     return 1;
   }
   if (c.factorized) {  // staged kernel over the whole range, atomic scatter only
-    if (prec == DOGIP_FP64) run_apply_tma<D, P, FORM, double, true>(c.d_A64, c, u, y, R, s, skip);
-    else run_apply_tma<D, P, FORM, float, true>(c.d_A32, c, u, y, R, s, skip);
+    if (prec == DOGIP_FP64) run_apply_tma<D, P, FORM, double, true>(c.d_A64, c, u, y, R, s, skip, add);
+    else run_apply_tma<D, P, FORM, float, true>(c.d_A32, c, u, y, R, s, skip, add);
     return 2;
   }
   // variant: 3 tensor cores (FP32), 2 self-feeding warps, 1 staged, 0 one thread per cell
   const int var = c.apply_variant_prec[prec] >= 0 ? c.apply_variant_prec[prec] : c.apply_variant;
   if (var == 3 && prec == DOGIP_FP32 && R == 1 && atomic && e0 == 0 && e1 == c.E &&
-      apply_tc(c, u, y, s, skip))
+      apply_tc(c, u, y, s, skip, add))
     return 2;
   if (var == 2 && R == 1 && atomic && e0 == 0 && e1 == c.E) {
     if (prec == DOGIP_FP64) {
       if constexpr (SfwCfg<D, P, FORM, double>::OK) {
-        run_apply_sfw<D, P, FORM, double>(c.d_A64, c, u, y, s, skip);
+        run_apply_sfw<D, P, FORM, double>(c.d_A64, c, u, y, s, skip, add);
         return 2;
       }
     } else {
       if constexpr (SfwCfg<D, P, FORM, float>::OK) {
-        run_apply_sfw<D, P, FORM, float>(c.d_A32, c, u, y, s, skip);
+        run_apply_sfw<D, P, FORM, float>(c.d_A32, c, u, y, s, skip, add);
         return 2;
       }
     }
@@ -150,7 +152,7 @@ int run_apply(const Ctx& c, const void* u, void* y, int R, int prec, bool atomic
   if (prec == DOGIP_FP64) {
     if constexpr (ok64) {
       if (whole) {
-        run_apply_tma<D, P, FORM, double, false>(c.d_A64, c, u, y, R, s, skip);
+        run_apply_tma<D, P, FORM, double, false>(c.d_A64, c, u, y, R, s, skip, add);
         return 2;
       }
     }
@@ -158,7 +160,7 @@ int run_apply(const Ctx& c, const void* u, void* y, int R, int prec, bool atomic
   } else {
     if constexpr (ok32) {
       if (whole) {
-        run_apply_tma<D, P, FORM, float, false>(c.d_A32, c, u, y, R, s, skip);
+        run_apply_tma<D, P, FORM, float, false>(c.d_A32, c, u, y, R, s, skip, add);
         return 2;
       }
     }
@@ -171,6 +173,6 @@ int run_apply(const Ctx& c, const void* u, void* y, int R, int prec, bool atomic
 
 #define DOGIP_APPLY_CASES(D, P)                                              \
   case P * 2 + 0:                                                            \
-    return run_apply<D, P, 0>(c, u, y, R, prec, atomic, e0, e1, s, skip);     \
+    return run_apply<D, P, 0>(c, u, y, R, prec, atomic, e0, e1, s, skip, add); \
   case P * 2 + 1:                                                            \
-    return run_apply<D, P, 1>(c, u, y, R, prec, atomic, e0, e1, s, skip);
+    return run_apply<D, P, 1>(c, u, y, R, prec, atomic, e0, e1, s, skip, add);

@@ -46,6 +46,8 @@ struct TcArgs {
   int64_t nbnd;
   long long wait_budget;
   const float* B;
+  int add;          // 1: y += K u (Dirichlet rows y_b += u_b); 0: y_b = u_b
+  int evict_first;  // 1: the A_T copies carry the L2 evict-first policy
 };
 
 template <int D, int P, int FORM>
@@ -178,12 +180,14 @@ __global__ void __launch_bounds__(TcCfg<D, P, FORM>::THREADS, 1) k_apply_tc(TcAr
   const int64_t ntiles32 = (a.E + kTile - 1) / kTile;
   const int64_t ntiles128 = (a.E + M - 1) / M, step = (int64_t)NWG * gridDim.x;
   int64_t a_issued = 0, a_waited = 0;  // bulk copies of A^_T (thread m == 0 issues)
+  const bool ef = a.evict_first != 0;
+  const uint64_t pol = ef ? l2_policy_evict_first() : 0;
   auto issue_a = [&](int64_t tt) {
     const int nt = (int)min((int64_t)4, ntiles32 - 4 * tt);
     fence_proxy_async_smem();
     mbar_expect_tx(abar, (uint32_t)nt * C::A_TILE);
-    bulk_copy_g2s(stA, (const unsigned char*)a.A + 4 * tt * C::A_TILE, (uint32_t)nt * C::A_TILE,
-                  abar);
+    stream_copy(stA, (const unsigned char*)a.A + 4 * tt * C::A_TILE, (uint32_t)nt * C::A_TILE,
+                abar, ef, pol);
     ++a_issued;
   };
   auto load_conn = [&](int64_t tt, uint32_t(&cc)[V], bool& act) {
@@ -353,7 +357,7 @@ __global__ void __launch_bounds__(TcCfg<D, P, FORM>::THREADS, 1) k_apply_tc(TcAr
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + tid; i < a.nbnd;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t idx = a.bnd[i];
-    a.y[idx] = a.u[idx];
+    a.y[idx] = a.add ? a.y[idx] + a.u[idx] : a.u[idx];
   }
 }
 
@@ -385,7 +389,7 @@ const TcLaunch& tc_launch() {
 }
 
 template <int D, int P, int FORM>
-bool run_tc(const Ctx& c, const void* u, void* y, cudaStream_t s, const int* skip) {
+bool run_tc(const Ctx& c, const void* u, void* y, cudaStream_t s, const int* skip, bool add) {
   if constexpr (!TcCfg<D, P, FORM>::OK) {
     return false;
   } else {
@@ -397,7 +401,8 @@ bool run_tc(const Ctx& c, const void* u, void* y, cudaStream_t s, const int* ski
     const int64_t grid = std::min<int64_t>((ntiles128 + Cfg::NWG - 1) / Cfg::NWG,
                                            (int64_t)L.num_sms * L.blocks);
     TcArgs a{c.d_A32, c.d_conn, (const float*)u, (float*)y, c.E, skip, c.d_kerr, c.d_bnd,
-             c.dirichlet ? c.nbnd : 0, c.wait_budget, Cfg::RT ? c.d_hiB32 : nullptr};
+             c.dirichlet ? c.nbnd : 0, c.wait_budget, Cfg::RT ? c.d_hiB32 : nullptr, add ? 1 : 0,
+             stream_evict_first(c, sizeof(float), Cfg::W * Cfg::NS)};
     k_apply_tc<D, P, FORM><<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
     return true;
   }
@@ -419,15 +424,15 @@ bool apply_tc_available(int d, int p, int form) {
 // FP32 apply with one right-hand side, atomic scatter over the whole cell range;
 // false when no tensor-core instance exists for (d, p, form).  u == nullptr only sets
 // the kernel attributes (context set-up, outside any stream capture).
-bool apply_tc(const Ctx& c, const void* u, void* y, cudaStream_t s, const int* skip) {
+bool apply_tc(const Ctx& c, const void* u, void* y, cudaStream_t s, const int* skip, bool add) {
   if (c.global_w || c.factorized || !c.keep32 || !apply_tc_available(c.d, c.p, c.form))
     return false;
   if (c.hi && c.d_hiB32 == nullptr) return false;
   const bool ell = c.form == DOGIP_ELLIPTIC;
 #define DOGIP_TC_CASE(D, P)                                                          \
   if (c.d == D && c.p == P)                                                          \
-    return ell ? run_tc<D, P, DOGIP_ELLIPTIC>(c, u, y, s, skip)                      \
-               : run_tc<D, P, DOGIP_PROJECTION>(c, u, y, s, skip);
+    return ell ? run_tc<D, P, DOGIP_ELLIPTIC>(c, u, y, s, skip, add)                 \
+               : run_tc<D, P, DOGIP_PROJECTION>(c, u, y, s, skip, add);
   DOGIP_TC_CASE(2, 1)
   DOGIP_TC_CASE(2, 2)
   DOGIP_TC_CASE(2, 3)

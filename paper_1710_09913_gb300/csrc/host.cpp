@@ -447,6 +447,11 @@ Ctx* setup(const dogip_mesh* m, int p, int form, int coef_kind, const double* co
     if (c->keep32) c->d_qp32 = dev_alloc<float>((size_t)c->E * c->NS);
     c->d_err = dev_alloc<int>(1);
     c->d_kerr = dev_alloc<int>(1);
+    {
+      int l2 = 0;
+      cuda_check(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->device), "L2 size");
+      c->l2_bytes = l2;
+    }
     if (const char* v = std::getenv("DOGIP_APPLY_VARIANT")) c->apply_variant = std::atoi(v);
     // Test hooks for the device-side failure path: a shorter wait budget, and one
     // chunk of the staged apply whose copy is never issued, so that its bounded
@@ -625,8 +630,9 @@ void run_chunk(Ctx& c, int prec, int scatter, double* x64, int k, double delta) 
       const void* dinv = prec == DOGIP_FP64 ? (const void*)c.d_dinv64 : (const void*)c.d_dinv32;
       for (int it = 0; it < k; ++it) {
         if (prec == DOGIP_FP64) launch_apply_cg(c, w.p64, w.q64, w.R, DOGIP_FP64, scatter, s, w);
-        else launch_apply_cg(c, w.p32, w.q32, w.R, DOGIP_FP32, scatter, s, w);
-        c.launches += vec_cg_step(w, prec, x64, dinv, delta, s, scatter == DOGIP_SCATTER_ATOMIC);
+        else launch_apply_cg(c, w.p32, w.q32, w.R, prec, scatter, s, w);  // FP32 or TF32 apply
+        c.launches += vec_cg_step(w, prec == DOGIP_FP64 ? DOGIP_FP64 : DOGIP_FP32, x64, dinv, delta,
+                                  s, scatter == DOGIP_SCATTER_ATOMIC);
       }
       cuda_check(cudaMemcpyAsync(w.h_flags, w.flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, s),
                  "flags copy");
@@ -695,6 +701,13 @@ int solve(Ctx& c, const double* b, double* u, int R, const dogip_solve_opts* opt
   int scatter = o.scatter < 0 ? c.scatter : o.scatter;
   if (scatter == DOGIP_SCATTER_COLOUR && c.scatter != DOGIP_SCATTER_COLOUR)
     fail(DOGIP_EINVAL, "colour scatter needs a context set up with scatter = COLOUR");
+  if (o.inner_prec != DOGIP_FP32 && o.inner_prec != DOGIP_TF32)
+    fail(DOGIP_EINVAL, "inner_prec must be DOGIP_FP32 or DOGIP_TF32");
+  const int ip = o.mode == DOGIP_SOLVE_FP64 ? DOGIP_FP64 : o.inner_prec;  // inner apply
+  if (ip == DOGIP_TF32 && (R != 1 || scatter != DOGIP_SCATTER_ATOMIC || c.global_w ||
+                           c.factorized || !apply_tc_available(c.d, c.p, c.form)))
+    fail(DOGIP_EUNSUPPORTED,
+         "TF32 inner applies need one right-hand side, atomic scatter and a tensor-core instance");
   const int chunk = std::max(1, o.check_every);
   DeviceGuard guard(c.device);
   ensure_w_scratch(c, R);
@@ -760,7 +773,7 @@ int solve(Ctx& c, const double* b, double* u, int R, const dogip_solve_opts* opt
       if (iters >= o.maxiter) { status = DOGIP_ENOTCONV; break; }
       if (timed_out()) { status = DOGIP_ETIMEOUT; break; }
       const int k = std::min(chunk, o.maxiter - iters);
-      run_chunk(c, DOGIP_FP32, scatter, nullptr, k, o.reliable_delta);
+      run_chunk(c, ip, scatter, nullptr, k, o.reliable_delta);
       iters = 0;
       for (int r = 0; r < R; ++r) iters = std::max(iters, w.h_scal[r].iters);
       corrected = false;
@@ -801,7 +814,7 @@ int solve(Ctx& c, const double* b, double* u, int R, const dogip_solve_opts* opt
       while (!w.h_flags[0] && inner < lim) {
         if (timed_out()) break;
         const int k = std::min(chunk, lim - inner);
-        run_chunk(c, DOGIP_FP32, scatter, nullptr, k, 0.0);
+        run_chunk(c, ip, scatter, nullptr, k, 0.0);
         inner = 0;
         for (int r = 0; r < R; ++r) inner = std::max(inner, w.h_scal[r].iters);
         if (w.h_flags[1]) break;
@@ -818,6 +831,11 @@ int solve(Ctx& c, const double* b, double* u, int R, const dogip_solve_opts* opt
     if (rel_out) rel_out[r] = w.h_scal[r].rel;
   }
   if (status == DOGIP_OK && worst > o.tol) status = DOGIP_ENOTCONV;
+  if (status == DOGIP_ENOTCONV)
+    set_last_error("solve stopped at its limits (iterations " + std::to_string(iters) +
+                   ", refinement steps " + std::to_string(outer) + ") with relative residual " +
+                   std::to_string(worst) + " above tol " + std::to_string(o.tol) +
+                   " (the FP64 residual of the operator may not reach a tolerance this small)");
   cuda_check(cudaEventRecord(c.ev_out, s), "event record");
   cuda_check(cudaStreamWaitEvent(user, c.ev_out, 0), "stream wait");
   if (info) {
@@ -1245,6 +1263,7 @@ int dogip_solve_opts_default(dogip_solve_opts* o) {
   o->use_x0 = 0;
   o->timeout_ms = 0.0;
   o->reliable_delta = 0.1;
+  o->inner_prec = DOGIP_FP32;
   return DOGIP_OK;
 }
 
@@ -1468,13 +1487,15 @@ int dogip_get_tables(int dim, int p, int form, double* bhat, double* what, int* 
   });
 }
 
-int dogip_apply(dogip_ctx* c, const void* u, void* y, int nrhs, int prec, int scatter,
-                void* stream) {
+namespace {
+int apply_entry(dogip_ctx* c, const void* u, void* y, int nrhs, int prec, int scatter,
+                void* stream, bool add) {
   return guarded([&] {
     if (!c || !u || !y) fail(DOGIP_EINVAL, "ctx, u and y are required");
     if (nrhs < 1) fail(DOGIP_EINVAL, "nrhs must be >= 1");
-    if (prec != DOGIP_FP64 && prec != DOGIP_FP32) fail(DOGIP_EINVAL, "unknown precision");
-    if (prec == DOGIP_FP32 && !c->keep32) fail(DOGIP_EINVAL, "context has no FP32 copy");
+    if (prec != DOGIP_FP64 && prec != DOGIP_FP32 && prec != DOGIP_TF32)
+      fail(DOGIP_EINVAL, "unknown precision");
+    if (prec != DOGIP_FP64 && !c->keep32) fail(DOGIP_EINVAL, "context has no FP32 copy");
     if (scatter < 0) scatter = c->scatter;
     if (scatter != DOGIP_SCATTER_ATOMIC && scatter != DOGIP_SCATTER_COLOUR)
       fail(DOGIP_EINVAL, "unknown scatter");
@@ -1482,9 +1503,20 @@ int dogip_apply(dogip_ctx* c, const void* u, void* y, int nrhs, int prec, int sc
       fail(DOGIP_EINVAL, "colour scatter needs a context set up with scatter = COLOUR");
     dogip::DeviceGuard g(c->device);
     dogip::ensure_w_scratch(*c, nrhs);
-    dogip::launch_apply(*c, u, y, nrhs, prec, scatter, (cudaStream_t)stream, nullptr);
+    dogip::launch_apply(*c, u, y, nrhs, prec, scatter, (cudaStream_t)stream, nullptr, add);
     return DOGIP_OK;
   });
+}
+}  // namespace
+
+int dogip_apply(dogip_ctx* c, const void* u, void* y, int nrhs, int prec, int scatter,
+                void* stream) {
+  return apply_entry(c, u, y, nrhs, prec, scatter, stream, false);
+}
+
+int dogip_apply_add(dogip_ctx* c, const void* u, void* y, int nrhs, int prec, int scatter,
+                    void* stream) {
+  return apply_entry(c, u, y, nrhs, prec, scatter, stream, true);
 }
 
 int dogip_apply_qp(dogip_ctx* c, const void* u, void* y, int nrhs, int prec, void* stream) {

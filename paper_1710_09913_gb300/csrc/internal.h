@@ -115,6 +115,8 @@ struct dogip_ctx {
   int apply_variant_prec[2] = {-1, -1};  // per precision (autotuner), -1: apply_variant
   int apply_block[2] = {256, 256};       // cells per CTA of the per-cell kernel
   long long wait_budget = 4000000000LL;  // clock cycles per bounded wait in kernels
+  int64_t l2_bytes = 0;        // L2 size of the device: streams larger than half of it
+                               // are copied with the L2 evict-first policy
   int64_t test_skip_chunk = -1;  // test hook (see DOGIP_TEST_SKIP_CHUNK)
   dogip::SolveWork work;
   int64_t launches = 0;           // kernels launched (graph replays count every node)
@@ -148,12 +150,24 @@ struct QuadCoef {
   double inside, outside;
 };
 
+// 1 when the A_T and conn streams of one apply (element size es, A_T entries per cell
+// nsw or, factorised, n_sym) exceed half of L2: such streams are read with the L2
+// evict-first policy so that u and y stay in L2; smaller ones may stay resident
+// between the applies of a solve and are copied without a policy.
+inline int stream_evict_first(const Ctx& c, size_t es, int nsw) {
+  const int64_t bytes = c.Epad * ((int64_t)nsw * (int64_t)es + 4 * (int64_t)c.VT);
+  return c.l2_bytes > 0 && 2 * bytes > c.l2_bytes ? 1 : 0;
+}
+
 // ---- kernel launchers (implemented in the .cu translation units) ----------
 // All take the processing-order state of ctx and enqueue on `s`.
 void launch_ahat(Ctx& c, const double* coef, int coef_kind, cudaStream_t s);
 void launch_ahat_quad(Ctx& c, const QuadCoef& qc, cudaStream_t s);
+// add: y += K u (no clearing of y; Dirichlet rows y_b += u_b) instead of y = K u.
+// prec DOGIP_TF32: FP32 data, the contractions with B on the tensor cores (the
+// tensor-core kernel; EUNSUPPORTED where no instance exists).
 void launch_apply(Ctx& c, const void* u, void* y, int R, int prec, int scatter,
-                  cudaStream_t s, const int* skip);
+                  cudaStream_t s, const int* skip, bool add = false);
 // The apply inside a CG iteration, q = K p.  With atomic scatter q must already be
 // zero (the previous p update clears it); colour scatter clears it itself.
 void launch_apply_cg(Ctx& c, const void* p, void* q, int R, int prec, int scatter,
@@ -166,7 +180,7 @@ void launch_export_ahat(const Ctx& c, double* out, cudaStream_t s);
 struct AhatArgs;
 struct LoadArgs;
 int apply_hi(const Ctx& c, const void* u, void* y, int R, int prec, bool atomic, int64_t e0,
-             int64_t e1, cudaStream_t s, const int* skip);
+             int64_t e1, cudaStream_t s, const int* skip, bool add = false);
 bool ahat_hi(const Ctx& c, AhatArgs& a, cudaStream_t s);
 bool load_hi(const Ctx& c, LoadArgs& a, cudaStream_t s);
 bool hi_table(int d, int p, int form, int* NB, int* W, int* V, long long* nnz, long long* nnz1,
@@ -175,7 +189,8 @@ bool table_is_compiled(int d, int p, int form);
 // Tensor-core FP32 apply (apply_tc.cu): one right-hand side, atomic scatter over the
 // whole cell range.  false when no instance exists for (d, p, form); u == nullptr
 // only sets the kernel attributes (context set-up).
-bool apply_tc(const Ctx& c, const void* u, void* y, cudaStream_t s, const int* skip);
+bool apply_tc(const Ctx& c, const void* u, void* y, cudaStream_t s, const int* skip,
+              bool add = false);
 bool apply_tc_available(int d, int p, int form);
 // Global double-grid apply of the weighted projection (two kernels); false when no
 // instance exists.  The scratch must hold R right-hand sides (ensure_w_scratch).
@@ -186,7 +201,7 @@ void narrow_copy(const double* a, float* b, int64_t n, cudaStream_t s);
 // Quadrature-point matrix-free apply (comparator): y = K~ u, atomic scatter.
 void launch_apply_qp(Ctx& c, const void* u, void* y, int R, int prec, cudaStream_t s);
 void launch_dirichlet_copy(const Ctx& c, const void* u, void* y, int R, int prec,
-                           cudaStream_t s, const int* skip);
+                           cudaStream_t s, const int* skip, bool add = false);
 void launch_diag_finish(Ctx& c, cudaStream_t s);
 // One-time kernel attributes of the apply instances of this context (host only).
 void prepare_apply(Ctx& c);

@@ -232,6 +232,56 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
       "l"(src), "r"(bytes), "r"(smem_addr(bar))
       : "memory");
 }
+// The same copy with an L2 cache-eviction policy (createpolicy) attached: streams read
+// once per apply (A_T, conn) are marked evict-first so that they do not push the
+// gathered u and the scatter-added y out of L2.
+__device__ __forceinline__ void bulk_copy_g2s_hint(void* dst, const void* src, uint32_t bytes,
+                                                   uint64_t* bar, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1], %2, [%3], %4;" ::"r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
+      : "memory");
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+// Copy with the evict-first policy when `ef` is set, plain otherwise.
+__device__ __forceinline__ void stream_copy(void* dst, const void* src, uint32_t bytes,
+                                            uint64_t* bar, bool ef, uint64_t policy) {
+  if (ef) bulk_copy_g2s_hint(dst, src, bytes, bar, policy);
+  else bulk_copy_g2s(dst, src, bytes, bar);
+}
+
+// Step "add" of Algorithm 1 for one warp (32 cells, RW right-hand sides per lane):
+// y[l_T] += Y_T with atomics.  Lanes 2m and 2m+1 that hold the same dof at the same
+// local index -- the common edge of two cells adjacent in the processing order, such
+// as the two triangles of a split square -- first add their values in registers, so
+// one atomic goes to L2 instead of two.  Every lane of the warp must call this (the
+// shuffles); inactive lanes pass conn entries with the Dirichlet bit and Y = 0.
+template <int V, int RW, typename T>
+__device__ __forceinline__ void scatter_pairs(const uint32_t (&c)[V], T (&Y)[RW][V], int lane,
+                                              T* y, int R, int r) {
+  static_for<V>([&](auto lc) {
+    constexpr int l = decltype(lc)::value;
+    const bool same = __shfl_xor_sync(0xffffffffu, c[l], 1) == c[l];
+    static_for<RW>([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      const T other = __shfl_xor_sync(0xffffffffu, Y[q][l], 1);
+      if (same) Y[q][l] += other;
+    });
+    if (!(c[l] & kBndBit) && !(same && (lane & 1))) {
+      T* dst = y + (int64_t)(c[l] & kIdMask) * R + r;
+      if constexpr (RW == 4)
+        atomicAdd((float4*)dst, make_float4(Y[0][l], Y[1][l], Y[2][l], Y[3][l]));
+      else
+        atomicAdd(dst, Y[0][l]);
+    }
+  });
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -300,6 +350,8 @@ struct TmaArgs {
   long long wait_budget;  // clock cycles per bounded mbarrier wait
   int64_t test_skip_chunk;  // test hook: this chunk's copy is never issued (-1: none)
   int r4;                   // 1: FP32, R % 4 == 0, u and y 16-byte aligned
+  int evict_first;          // 1: A_T and conn copies carry the L2 evict-first policy
+  int add;                  // 1: y += K u (Dirichlet rows y_b += u_b); 0: y_b = u_b
 };
 
 template <int D, int P, int FORM, typename T, bool FACT>
@@ -339,12 +391,14 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T, FACT>::THREADS)
     if (lane == 0) {
       int failed = 0;
       int64_t issued = 0;  // chunks whose copies were issued
+      const bool ef = a.evict_first != 0;
+      const uint64_t pol = ef ? l2_policy_evict_first() : 0;
       const bool pro_issued = k0 < a.nchunks;
       if (pro_issued) {
         const int nt0 = (int)min((int64_t)C::TPC, a.ntiles - k0 * C::TPC);
         mbar_expect_tx(pro, (uint32_t)nt0 * C::C_TILE);
-        bulk_copy_g2s(pro_buf, (const unsigned char*)a.conn + k0 * C::TPC * C::C_TILE,
-                      (uint32_t)nt0 * C::C_TILE, pro);
+        stream_copy(pro_buf, (const unsigned char*)a.conn + k0 * C::TPC * C::C_TILE,
+                    (uint32_t)nt0 * C::C_TILE, pro, ef, pol);
       }
       for (int64_t i = 0;; ++i) {
         const int64_t k = k0 + i * G;
@@ -364,11 +418,11 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T, FACT>::THREADS)
         unsigned char* sa = base + (size_t)s * C::CHUNK;
         unsigned char* sc = sa + C::TPC * C::A_TILE;
         mbar_expect_tx(&full[s], (uint32_t)nt * C::A_TILE + (uint32_t)ntn * C::C_TILE);
-        bulk_copy_g2s(sa, (const unsigned char*)a.A + t0 * C::A_TILE, (uint32_t)nt * C::A_TILE,
-                      &full[s]);
+        stream_copy(sa, (const unsigned char*)a.A + t0 * C::A_TILE, (uint32_t)nt * C::A_TILE,
+                    &full[s], ef, pol);
         if (ntn > 0)
-          bulk_copy_g2s(sc, (const unsigned char*)a.conn + kn * C::TPC * C::C_TILE,
-                        (uint32_t)ntn * C::C_TILE, &full[s]);
+          stream_copy(sc, (const unsigned char*)a.conn + kn * C::TPC * C::C_TILE,
+                      (uint32_t)ntn * C::C_TILE, &full[s], ef, pol);
       }
       // drain: wait (bounded) until the last copies issued have landed
       if (pro_issued) mbar_wait_bounded(pro, 0u, a.wait_budget);
@@ -455,8 +509,8 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T, FACT>::THREADS)
             if constexpr (PFW) gather(cn, 0, un);
           }
           if constexpr (!PFW) gather(c, r, ul);  // this unit (no prefetch: register budget)
+          T Y[RW][V];
           if (active) {
-            T Y[RW][V];
             static_for<RW>([&](auto qc) {
               constexpr int q = decltype(qc)::value;
               static_for<V>([&](auto lc) {
@@ -484,17 +538,12 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T, FACT>::THREADS)
                 project<TB, j>(h, Y[q]);
               });
             });
-            static_for<V>([&](auto lc) {
-              constexpr int l = decltype(lc)::value;
-              if (!(c[l] & kBndBit)) {
-                T* dst = a.y + (int64_t)(c[l] & kIdMask) * a.R + r;
-                if constexpr (RW == 4)
-                  atomicAdd((float4*)dst, make_float4(Y[0][l], Y[1][l], Y[2][l], Y[3][l]));
-                else
-                  atomicAdd(dst, Y[0][l]);
-              }
+          } else {
+            static_for<RW>([&](auto qc) {
+              static_for<V>([&](auto lc) { Y[decltype(qc)::value][decltype(lc)::value] = T(0); });
             });
           }
+          scatter_pairs<V, RW, T>(c, Y, lane, a.y, a.R, r);
           if constexpr (PFW) {
             static_for<V>([&](auto lc) {
               constexpr int l = decltype(lc)::value;
@@ -524,7 +573,7 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T, FACT>::THREADS)
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + tid; t < a.nbnd * a.R;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t idx = (int64_t)a.bnd[t / a.R] * a.R + (t % a.R);
-    a.y[idx] = a.u[idx];
+    a.y[idx] = a.add ? a.y[idx] + a.u[idx] : a.u[idx];
   }
 }
 
@@ -582,6 +631,8 @@ __global__ void __launch_bounds__(SfwCfg<D, P, FORM, T>::THREADS)
     mbar_fence_init();
   }
   __syncwarp();
+  const bool ef = a.evict_first != 0;
+  const uint64_t pol = ef ? l2_policy_evict_first() : 0;
   const int64_t w0 = (int64_t)blockIdx.x * C::NW + warp;
   const int64_t wstride = (int64_t)gridDim.x * C::NW;
   // item it of this warp: tile w0 + (it / ITEMS) * wstride, part it % ITEMS
@@ -605,7 +656,7 @@ __global__ void __launch_bounds__(SfwCfg<D, P, FORM, T>::THREADS)
     }
     fence_proxy_async_smem();
     mbar_expect_tx(&bar[s], bytes);
-    bulk_copy_g2s(ring + (size_t)s * C::SLOT, src, bytes, &bar[s]);
+    stream_copy(ring + (size_t)s * C::SLOT, src, bytes, &bar[s], ef, pol);
     return true;
   };
   int64_t issued = 0;  // items issued (or skipped by the test hook)
@@ -643,11 +694,11 @@ __global__ void __launch_bounds__(SfwCfg<D, P, FORM, T>::THREADS)
       });
     }
     advance();
-    T ul[V], Y[V];
+    T ul[V], Y[1][V];
     static_for<V>([&](auto lc) {
       constexpr int l = decltype(lc)::value;
       ul[l] = (c[l] & kBndBit) ? T(0) : __ldg(a.u + (int64_t)(c[l] & kIdMask));
-      if constexpr (col_empty<TB>(l)) Y[l] = T(0);
+      if constexpr (col_empty<TB>(l)) Y[0][l] = T(0);
     });
     static_for<NPC>([&](auto pc) {
       constexpr int pcv = decltype(pc)::value;
@@ -668,18 +719,14 @@ __global__ void __launch_bounds__(SfwCfg<D, P, FORM, T>::THREADS)
           });
           interp<TB, j>(ul, g);
           block_mul<D, FORM>(aj, g, h);
-          project<TB, j>(h, Y);
+          project<TB, j>(h, Y[0]);
         }
       });
       advance();
     });
     if (failed) break;
-    if (active) {
-      static_for<V>([&](auto lc) {
-        constexpr int l = decltype(lc)::value;
-        if (!(c[l] & kBndBit)) atomicAdd(a.y + (int64_t)(c[l] & kIdMask), Y[l]);
-      });
-    }
+    if (!active) static_for<V>([&](auto lc) { Y[0][decltype(lc)::value] = T(0); });
+    scatter_pairs<V, 1, T>(c, Y, lane, a.y, 1, 0);
   }
   // drain (bounded): copies issued and not consumed
   for (int64_t i = it; i < issued; ++i) {
@@ -691,7 +738,7 @@ __global__ void __launch_bounds__(SfwCfg<D, P, FORM, T>::THREADS)
   // Dirichlet rows: y_b = u_b (the scatter skipped them)
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + tid; q < a.nbnd; q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t idx = a.bnd[q];
-    a.y[idx] = a.u[idx];
+    a.y[idx] = a.add ? a.y[idx] + a.u[idx] : a.u[idx];
   }
 }
 

@@ -5,9 +5,7 @@
 // of memory that the library or the caller allocates.
 #include <cuda_runtime.h>
 
-#include <atomic>
 #include <cmath>
-#include <mutex>
 
 #include "internal.h"
 
@@ -29,42 +27,37 @@ __global__ void __launch_bounds__(kNaThreads) k_residual_norms_static(
     int64_t N, int R, double* __restrict__ out, unsigned char* scratch) {
   double* partial = (double*)scratch;                            // [kNaBlocks][2 R]
   unsigned int* counter = (unsigned int*)(scratch + kNaPartialBytes);
-  __shared__ double acc[kNaThreads / 32][2 * kNaMaxRhs];
+  __shared__ double srr[kNaThreads], sbb[kNaThreads];
   __shared__ bool last;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int k = threadIdx.x; k < (kNaThreads / 32) * 2 * kNaMaxRhs; k += blockDim.x)
-    (&acc[0][0])[k] = 0.0;
-  __syncthreads();
-  // grid stride over the dof-major [n x R] arrays; the rhs of entry i is i % R
+  // The grid stride is a multiple of R, so every thread stays on one right-hand side
+  // (entry i of the dof-major [n x R] arrays belongs to rhs i % R); threads past the
+  // rounded stride do no loads.
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = ((int64_t)gridDim.x * blockDim.x / R) * R;
   double rr = 0.0, bb = 0.0;
-  int cur = -1;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += stride) {
-    const int rhs = (int)(i % R);
-    if (rhs != cur) {
-      if (cur >= 0) {
-        atomicAdd(&acc[wid][2 * cur], rr);
-        atomicAdd(&acc[wid][2 * cur + 1], bb);
-      }
-      cur = rhs;
-      rr = bb = 0.0;
+  if (t < stride) {
+    for (int64_t i = t; i < N; i += stride) {
+      const double bi = b[i];
+      const double ri = bi - Ky[i];
+      if (r != nullptr) r[i] = ri;
+      rr += ri * ri;
+      bb += bi * bi;
     }
-    const double bi = b[i];
-    const double ri = bi - Ky[i];
-    if (r != nullptr) r[i] = ri;
-    rr += ri * ri;
-    bb += bi * bi;
   }
-  if (cur >= 0) {
-    atomicAdd(&acc[wid][2 * cur], rr);
-    atomicAdd(&acc[wid][2 * cur + 1], bb);
-  }
-  (void)lane;
+  srr[threadIdx.x] = rr;
+  sbb[threadIdx.x] = bb;
   __syncthreads();
-  if (threadIdx.x < 2 * R) {
-    double s = 0.0;
-    for (int w = 0; w < kNaThreads / 32; ++w) s += acc[w][threadIdx.x];
-    partial[(size_t)blockIdx.x * 2 * kNaMaxRhs + threadIdx.x] = s;
+  // fixed-order block sums per rhs: thread q (< R) adds the threads of its rhs in order
+  const int first = (int)((blockIdx.x * (int64_t)blockDim.x) % R);  // rhs of thread 0
+  if (threadIdx.x < R) {
+    const int q = threadIdx.x;
+    double s1 = 0.0, s2 = 0.0;
+    for (int k = (q - first + R) % R; k < kNaThreads; k += R) {
+      s1 += srr[k];
+      s2 += sbb[k];
+    }
+    partial[(size_t)blockIdx.x * 2 * kNaMaxRhs + 2 * q] = s1;
+    partial[(size_t)blockIdx.x * 2 * kNaMaxRhs + 2 * q + 1] = s2;
   }
   __threadfence();
   __syncthreads();
@@ -72,7 +65,7 @@ __global__ void __launch_bounds__(kNaThreads) k_residual_norms_static(
   __syncthreads();
   if (!last) return;
   __threadfence();
-  if (threadIdx.x < R) {
+  if (threadIdx.x < R) {  // blocks summed in index order: the result is deterministic
     double trr = 0.0, tbb = 0.0;
     for (unsigned blk = 0; blk < gridDim.x; ++blk) {
       trr += __ldcg(partial + (size_t)blk * 2 * kNaMaxRhs + 2 * threadIdx.x);
@@ -83,22 +76,13 @@ __global__ void __launch_bounds__(kNaThreads) k_residual_norms_static(
   if (threadIdx.x == 0) *counter = 0u;
 }
 
-// Device address of the scratch, resolved once per device with that device current.
-constexpr int kMaxDevices = 64;
-std::mutex g_na_mutex;
-unsigned char* g_na_ptr[kMaxDevices] = {};
-
+// Device address of the scratch on the current device.  Looked up on every call (a
+// host call that enqueues nothing), so that it stays valid after the primary context
+// of the device has been reset.
 unsigned char* scratch_on_current_device() {
-  int dev = 0;
-  cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
-  if (dev < 0 || dev >= kMaxDevices) fail(DOGIP_EUNSUPPORTED, "device ordinal out of range");
-  std::lock_guard<std::mutex> lock(g_na_mutex);
-  if (g_na_ptr[dev] == nullptr) {
-    void* p = nullptr;
-    cuda_check(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress");
-    g_na_ptr[dev] = (unsigned char*)p;
-  }
-  return g_na_ptr[dev];
+  void* p = nullptr;
+  cuda_check(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress");
+  return (unsigned char*)p;
 }
 
 }  // namespace
@@ -108,7 +92,8 @@ extern "C" DOGIP_API int dogip_residual_norms_noalloc(const double* b, const dou
                                                       int64_t n, int nrhs, double* rel,
                                                       void* stream) {
   try {
-    if (!b || !Ky || !rel) dogip::fail(DOGIP_EINVAL, "b, Ky and rel are required");
+    if (!rel || (n > 0 && (!b || !Ky)))
+      dogip::fail(DOGIP_EINVAL, "b, Ky and rel are required");
     if (n < 0) dogip::fail(DOGIP_EINVAL, "n must be >= 0");
     if (nrhs < 1 || nrhs > dogip::kNaMaxRhs)
       dogip::fail(DOGIP_EINVAL, "nrhs must be between 1 and 32 (size of the static scratch)");

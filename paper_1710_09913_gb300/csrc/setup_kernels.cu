@@ -34,19 +34,19 @@ void setup_dispatch(Ctx& c, const SetupCall& k, cudaStream_t s, const char* what
 // Apply dispatchers (apply_d*.cu): 0 = not compiled, 1 = per-cell kernel, 2 = staged
 // kernel (which also wrote the Dirichlet rows).
 int apply_d2(const Ctx&, const void*, void*, int, int, bool, int64_t, int64_t, cudaStream_t,
-             const int*);
+             const int*, bool);
 int apply_d3a(const Ctx&, const void*, void*, int, int, bool, int64_t, int64_t, cudaStream_t,
-              const int*);
+              const int*, bool);
 int apply_d3b(const Ctx&, const void*, void*, int, int, bool, int64_t, int64_t, cudaStream_t,
-              const int*);
+              const int*, bool);
 
 namespace {
 int apply_dispatch(const Ctx& c, const void* u, void* y, int R, int prec, bool atomic, int64_t e0,
-                   int64_t e1, cudaStream_t s, const int* skip) {
-  if (c.hi) return apply_hi(c, u, y, R, prec, atomic, e0, e1, s, skip);
-  if (c.d == 2) return apply_d2(c, u, y, R, prec, atomic, e0, e1, s, skip);
-  if (c.p <= 2) return apply_d3a(c, u, y, R, prec, atomic, e0, e1, s, skip);
-  if (c.p == 3) return apply_d3b(c, u, y, R, prec, atomic, e0, e1, s, skip);
+                   int64_t e1, cudaStream_t s, const int* skip, bool add = false) {
+  if (c.hi) return apply_hi(c, u, y, R, prec, atomic, e0, e1, s, skip, add);
+  if (c.d == 2) return apply_d2(c, u, y, R, prec, atomic, e0, e1, s, skip, add);
+  if (c.p <= 2) return apply_d3a(c, u, y, R, prec, atomic, e0, e1, s, skip, add);
+  if (c.p == 3) return apply_d3b(c, u, y, R, prec, atomic, e0, e1, s, skip, add);
   return 0;
 }
 }  // namespace
@@ -60,14 +60,15 @@ __global__ void k_export_ahat(const double* A, const int64_t* perm, double* out,
   out[perm[pos] * nsw + k] = A[(pos >> 5) * ((int64_t)nsw * kTile) + k * kTile + (pos & 31)];
 }
 
+// Dirichlet rows of K~ = P K P + (I - P): y_b = u_b, or y_b += u_b (add).
 template <typename T>
 __global__ void k_dirichlet_copy(const T* u, T* y, const int32_t* bnd, int64_t nb, int R,
-                                 const int* skip) {
+                                 const int* skip, int add) {
   if (skip != nullptr && *skip) return;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nb * R) return;
   const int64_t i = (int64_t)bnd[t / R] * R + (t % R);
-  y[i] = u[i];
+  y[i] = add ? y[i] + u[i] : u[i];
 }
 
 __global__ void k_diag_finish(double* diag, double* dinv64, float* dinv32, const int32_t* bnd,
@@ -198,16 +199,16 @@ void launch_export_ahat(const Ctx& c, double* out, cudaStream_t s) {
 }
 
 void launch_dirichlet_copy(const Ctx& c, const void* u, void* y, int R, int prec, cudaStream_t s,
-                           const int* skip) {
+                           const int* skip, bool add) {
   if (c.nbnd == 0) return;
   const int64_t tot = c.nbnd * R;
   const unsigned nb = (unsigned)((tot + 255) / 256);
   if (prec == DOGIP_FP64)
     k_dirichlet_copy<double><<<nb, 256, 0, s>>>((const double*)u, (double*)y, c.d_bnd, c.nbnd, R,
-                                                 skip);
+                                                 skip, add ? 1 : 0);
   else
     k_dirichlet_copy<float><<<nb, 256, 0, s>>>((const float*)u, (float*)y, c.d_bnd, c.nbnd, R,
-                                                skip);
+                                                skip, add ? 1 : 0);
 }
 
 void prepare_apply(Ctx& c) {
@@ -225,6 +226,13 @@ void launch_apply_cg(Ctx& c, const void* p, void* q, int R, int prec, int scatte
     c.launches += 2;
     return;
   }
+  if (prec == DOGIP_TF32) {  // tensor-core kernel; it writes the Dirichlet rows itself
+    if (R != 1 || scatter != DOGIP_SCATTER_ATOMIC || !apply_tc(c, p, q, s, w.flags))
+      fail(DOGIP_EUNSUPPORTED, "no tensor-core apply for this context and request");
+    cuda_check(cudaGetLastError(), "tensor-core apply launch");
+    c.launches += 1;
+    return;
+  }
   if (scatter == DOGIP_SCATTER_ATOMIC) {
     const int k = apply_dispatch(c, p, q, R, prec, true, 0, c.E, s, w.flags);
     if (!k) fail(DOGIP_EUNSUPPORTED, "no compiled apply instance for this (dim, p, form)");
@@ -240,9 +248,22 @@ void launch_apply_cg(Ctx& c, const void* p, void* q, int R, int prec, int scatte
 }
 
 void launch_apply(Ctx& c, const void* u, void* y, int R, int prec, int scatter, cudaStream_t s,
-                  const int* skip) {
+                  const int* skip, bool add) {
   const size_t es = prec == DOGIP_FP64 ? sizeof(double) : sizeof(float);
-  cuda_check(cudaMemsetAsync(y, 0, es * c.n * R, s), "memset y");
+  if (prec == DOGIP_TF32) {
+    if (R != 1 || scatter != DOGIP_SCATTER_ATOMIC || !apply_tc_available(c.d, c.p, c.form) ||
+        c.global_w || c.factorized)
+      fail(DOGIP_EUNSUPPORTED,
+           "no tensor-core apply for this request (one right-hand side, atomic scatter, "
+           "element-wise A_T, and an instance for this dimension, order and form)");
+    if (!add) cuda_check(cudaMemsetAsync(y, 0, es * c.n * R, s), "memset y");
+    if (!apply_tc(c, u, y, s, skip, add))
+      fail(DOGIP_EUNSUPPORTED, "no tensor-core apply for this context");
+    c.launches += 1;
+    cuda_check(cudaGetLastError(), "tensor-core apply launch");
+    return;
+  }
+  if (!add) cuda_check(cudaMemsetAsync(y, 0, es * c.n * R, s), "memset y");
   if (c.global_w) {
     if (R > c.w_cap) fail(DOGIP_EINVAL, "global double-grid scratch too small for nrhs");
     if (!apply_gw(c, u, y, R, prec, s, skip))
@@ -253,7 +274,7 @@ void launch_apply(Ctx& c, const void* u, void* y, int R, int prec, int scatter, 
   }
   bool staged = false;
   auto run = [&](bool atomic, int64_t e0, int64_t e1) {
-    const int k = apply_dispatch(c, u, y, R, prec, atomic, e0, e1, s, skip);
+    const int k = apply_dispatch(c, u, y, R, prec, atomic, e0, e1, s, skip, add);
     if (!k) fail(DOGIP_EUNSUPPORTED, "no compiled apply instance for this (dim, p, form)");
     staged = staged || k == 2;
   };
@@ -265,7 +286,7 @@ void launch_apply(Ctx& c, const void* u, void* y, int R, int prec, int scatter, 
     c.launches += 1;
   }
   if (c.dirichlet && c.nbnd > 0 && !staged) {
-    launch_dirichlet_copy(c, u, y, R, prec, s, skip);
+    launch_dirichlet_copy(c, u, y, R, prec, s, skip, add);
     c.launches += 1;
   }
   cuda_check(cudaGetLastError(), "apply kernel launch");

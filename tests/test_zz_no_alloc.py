@@ -60,3 +60,34 @@ def test_noalloc_residual_matches_solve():
         B.residual_norms_noalloc(torch.zeros((10, 33), dtype=torch.float64, device="cuda"),
                                  torch.zeros((10, 33), dtype=torch.float64, device="cuda"))
     assert e.value.code == B.EINVAL and "32" in str(e.value)
+
+
+@pytest.mark.parametrize("R", [3, 7, 32])
+def test_noalloc_full_grid_against_torch(R):
+    """Sizes far above the 256-block grid (every thread loops many times), right-hand
+    side counts that do not divide the block size, checked against torch norms; the
+    result is the same on a second call (fixed reduction order)."""
+    from paper_1710_09913_gb300 import build
+    build.build()
+    from paper_1710_09913_gb300 import binding as B
+
+    g = torch.Generator(device="cuda").manual_seed(11 + R)
+    n = 300_001
+    b = torch.randn(n, R, dtype=torch.float64, device="cuda", generator=g)
+    Ky = b + 1e-3 * torch.randn(n, R, dtype=torch.float64, device="cuda", generator=g)
+    r = torch.empty_like(b)
+    rel = B.residual_norms_noalloc(b, Ky, r)
+    ref = torch.linalg.vector_norm(b - Ky, dim=0) / torch.linalg.vector_norm(b, dim=0)
+    torch.testing.assert_close(rel, ref, rtol=1e-13, atol=0)
+    assert torch.equal(r, b - Ky)
+    assert torch.equal(B.residual_norms_noalloc(b, Ky), rel)
+
+
+def test_noalloc_empty():
+    from paper_1710_09913_gb300 import build
+    build.build()
+    from paper_1710_09913_gb300 import binding as B
+
+    e = torch.zeros((0, 5), dtype=torch.float64, device="cuda")
+    rel = B.residual_norms_noalloc(e, e)
+    assert rel.shape == (5,) and torch.all(rel == 0)
