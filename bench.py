@@ -627,7 +627,8 @@ def main():
             if form == "elliptic":
                 b3[torch.tensor(c.boundary(), device="cuda")] = 0.0
             out = {"dofs": c.n, "rhs": R}
-            for prec, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
+            for prec, dt in (("fp32", torch.float32), ("tf32", torch.float32),
+                             ("fp64", torch.float64)):
                 x = b3.to(dt).contiguous()
                 y = torch.empty_like(x)
                 for _ in range(2):
@@ -645,6 +646,16 @@ def main():
                 inf = c.info
                 byt = (c.E * inf.w_loc * inf.n_sym * dt.itemsize + c.E * inf.v_loc * 4
                        + 2 * c.n * R * dt.itemsize)
+                # the kernel alone (dogip_apply_add, no clearing of y)
+                torch.cuda.synchronize()
+                ev0.record(stream)
+                for _ in range(reps):
+                    c.apply_add(x, y, prec=prec)
+                ev1.record(stream)
+                torch.cuda.synchronize()
+                kms = ev0.elapsed_time(ev1) / reps
+                out[f"apply_{prec}_kernel_ms"] = round(kms, 4)
+                out[f"apply_{prec}_kernel_GBps"] = round(byt / kms / 1e6, 1)
                 out[f"apply_{prec}_ms"] = round(ms, 4)
                 out[f"apply_{prec}_gdofs"] = round(c.n * R / ms / 1e6, 3)
                 out[f"apply_{prec}_GBps"] = round(byt / ms / 1e6, 1)
@@ -892,6 +903,40 @@ def main():
         del cc
         torch.cuda.empty_cache()
 
+    _section("contrast")
+    # high-contrast inclusions (matrix 1, 200 balls r in U[0.03, 0.08] valued 1e2 / 1e4 /
+    # 1e6, centroid rule), 3D 32^3 x 6 tetrahedra, P2 elliptic, one N(0,1) load: mixed
+    # solve to 1e-8 against FP64 PCG (FP32 A_T keeps its relative precision at any of
+    # these contrasts; the Jacobi preconditioner and the FP64 refinement carry the rest)
+    contrast = {}
+    from paper_1710_09913_gb300 import inputs as _ci
+    cc3, ct3 = _ci.lattice_mesh(3, 32)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    for cval in (1e2, 1e4, 1e6):
+        mc = _ci.coef_inclusions(_ci.centroids(cc3, ct3), 200, 0.03, 0.08, seed=3, inside=cval)
+        cx = B.Context(cc3, ct3, 2, "elliptic", mc)
+        bx = torch.tensor(_ci.rhs_normal(cx.n, 1, seed=3)[:, 0], device="cuda")
+        bx[torch.tensor(cx.boundary(), device="cuda")] = 0.0
+        out = {"dofs": cx.n}
+        for mode in ("mixed", "fp64"):
+            ux = torch.zeros_like(bx)
+            cx.solve(bx, ux, mode=mode, tol=TOL, check_every=args.check_every, allow_notconv=True)
+            ux.zero_()
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            _, info = cx.solve(bx, ux, mode=mode, tol=TOL, check_every=args.check_every,
+                               allow_notconv=True)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            out[f"{mode}_ms"] = round(ev0.elapsed_time(ev1), 2)
+            out[f"{mode}_iters"] = info["iterations"]
+            out[f"{mode}_rel_residual"] = info["rel_residual"]
+            out[f"{mode}_status"] = info["status"]
+        contrast[f"{cval:.0e}"] = out
+        del cx
+    torch.cuda.empty_cache()
+
     _section("gradient")
     # differentiation workload: compliance J = b^T u(A) of FP32 leaf SPD tensors
     # (log-eigenvalues N(0, 0.5^2)), forward mixed solve and backward (adjoint solve +
@@ -992,7 +1037,7 @@ def main():
                 "time_to_tol": t2t, "apply": applies, "csr_baseline": csr, "batch_uneven": batch,
                 "cube_p2_16rhs": multi, "factorized": fact, "quadrature_point_comparator": qp,
                 "global_double_grid_projection": gw, "high_order": hi_ord,
-                "tensor_core_apply": tcore, "scatter_compare": scat, "gradient": grad,
+                "tensor_core_apply": tcore, "scatter_compare": scat, "gradient": grad, "contrast_sweep": contrast,
                 "roofline": roofline,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks}
         print(json.dumps(line), flush=True)

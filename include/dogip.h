@@ -320,7 +320,9 @@ typedef struct {
   int mode;           /* DOGIP_SOLVE_FP64 or DOGIP_SOLVE_MIXED                */
   double tol;         /* target ||b - K u||_2 / ||b||_2 (FP64), per rhs        */
   int maxiter;        /* FP64 mode: PCG iterations; mixed: total inner ones    */
-  double inner_tol;   /* mixed: relative residual reduction per inner solve   */
+  double inner_tol;   /* mixed: relative residual reduction per inner solve;
+                         a step asks for no more than the FP64 residual still
+                         needs (0.2 tol / current residual, if that is larger) */
   int inner_maxiter;  /* mixed: iteration limit of one inner solve             */
   int max_outer;      /* mixed: refinement steps                               */
   int scatter;        /* -1 context default, else DOGIP_SCATTER_*              */
@@ -332,7 +334,17 @@ typedef struct {
                             residual has dropped by this factor (0.1)         */
   int inner_prec;     /* mixed modes: applies of the inner solves, DOGIP_FP32
                          (default, CUDA cores) or DOGIP_TF32 (tensor cores;
-                         nrhs 1, atomic scatter, else DOGIP_EUNSUPPORTED)      */
+                         nrhs 1 or a multiple of 16, atomic scatter, else
+                         DOGIP_EUNSUPPORTED)                                   */
+  int inner_recurrence; /* MIXED inner FP32 PCG: 0 (default) the standard
+                         Hestenes-Stiefel recurrence, with (p, K p) reduced from
+                         the element energies p_T . (K_T p_T) inside the apply
+                         where that kernel is the staged one (nrhs 1, FP32,
+                         atomic scatter: 3 kernels an iteration), else with a
+                         separate p.q kernel (4); 1 always the separate kernel;
+                         2 the single-reduction recurrence of Chronopoulos and
+                         Gear (2 kernels: s = K p by recurrence; more FP32
+                         iterations; EUNSUPPORTED where it does not apply)    */
 } dogip_solve_opts;
 
 typedef struct {
@@ -385,10 +397,14 @@ typedef struct {
  * on its own data: the tensor-core kernel (FP32, where an instance exists), the
  * self-feeding-warps kernel, the bulk-async staged kernel, and the
  * one-thread-per-cell kernel with 64, 128 or 256 cells per CTA (orders above the
- * compiled tables: the run-time-table kernel against the tensor cores, FP32 only) (median of 5
- * CUDA-event timings after 2 warm-up applies, atomic scatter, one right-hand side).
+ * compiled tables: the run-time-table kernel against the tensor cores, FP32 only):
+ * the kernel alone, best of 3 CUDA-event samples of 8 back-to-back launches after 3
+ * warm-up launches, atomic scatter, one right-hand side.  In FP32 the staged kernel
+ * is kept unless another is faster by more than 3 % (it also carries the (p, K p)
+ * reduction of the mixed solve, one kernel less per inner iteration).
  * Applies with several right-hand sides use the staged kernel where it exists
- * (FP32 with nrhs a multiple of 4 and V_T <= 10 always), and the choice otherwise.  Choices are cached for the process
+ * (FP32 with nrhs a multiple of 4 and V_T <= 10 always), and the choice otherwise;
+ * prec DOGIP_TF32 selects the tensor cores whatever the choice.  Choices are cached for the process
  * per (dim, p, form, precision, log2 cells) and reused without timing unless
  * force != 0; the environment variable DOGIP_TUNE_CACHE names a text file the cache
  * is read from and appended to.  Allocates two temporary vectors (stream-ordered)

@@ -26,6 +26,7 @@ FORMS = {"projection": PROJECTION, "elliptic": ELLIPTIC}
 PRECS = {"fp64": FP64, "fp32": FP32, "tf32": TF32}
 SCATTERS = {"atomic": SCATTER_ATOMIC, "colour": SCATTER_COLOUR, None: -1}
 MODES = {"fp64": SOLVE_FP64, "mixed": SOLVE_MIXED, "mixed_reliable": SOLVE_MIXED_RELIABLE}
+RECURRENCES = {"auto": 0, "standard": 1, "single_reduction": 2}
 
 
 class DogipError(RuntimeError):
@@ -74,7 +75,7 @@ class SolveOpts(C.Structure):
                 ("inner_tol", C.c_double), ("inner_maxiter", C.c_int), ("max_outer", C.c_int),
                 ("scatter", C.c_int), ("check_every", C.c_int), ("use_x0", C.c_int),
                 ("timeout_ms", C.c_double), ("reliable_delta", C.c_double),
-                ("inner_prec", C.c_int)]
+                ("inner_prec", C.c_int), ("inner_recurrence", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -426,7 +427,8 @@ class Context:
         return b
 
     def _solve_opts(self, mode, tol, maxiter, inner_tol, inner_maxiter, max_outer, scatter,
-                    check_every, x0, timeout_ms, reliable_delta=None, inner_prec=None):
+                    check_every, x0, timeout_ms, reliable_delta=None, inner_prec=None,
+                    inner_recurrence=None):
         o = SolveOpts()
         lib.dogip_solve_opts_default(C.byref(o))
         o.mode = MODES.get(mode, mode)
@@ -448,12 +450,14 @@ class Context:
             o.reliable_delta = reliable_delta
         if inner_prec is not None:
             o.inner_prec = PRECS.get(inner_prec, inner_prec)
+        if inner_recurrence is not None:
+            o.inner_recurrence = RECURRENCES.get(inner_recurrence, inner_recurrence)
         return o
 
     def solve(self, b, u=None, *, mode="fp64", tol=1e-8, maxiter=None, inner_tol=None,
               inner_maxiter=None, max_outer=None, scatter=None, check_every=None, x0=False,
               timeout_ms=0.0, stream=None, allow_notconv=False, reliable_delta=None,
-              inner_prec=None):
+              inner_prec=None, inner_recurrence=None):
         """Solve K u = b on the device; returns (u, info dict).  inner_prec ("fp32" or
         "tf32") selects the applies of the mixed modes' inner solves."""
         import torch
@@ -461,7 +465,8 @@ class Context:
         if u is None:
             u = torch.zeros_like(b)
         o = self._solve_opts(mode, tol, maxiter, inner_tol, inner_maxiter, max_outer, scatter,
-                             check_every, x0, timeout_ms, reliable_delta, inner_prec)
+                             check_every, x0, timeout_ms, reliable_delta, inner_prec,
+                             inner_recurrence)
         inf = SolveInfo()
         rel = np.zeros(R)
         code = lib.dogip_solve(self._h, _dptr(b, torch.float64), _dptr(u, torch.float64), R,

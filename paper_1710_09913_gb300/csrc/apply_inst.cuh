@@ -63,7 +63,8 @@ void run_apply_tma(const T* A, const Ctx& c, const void* u, void* y, int R, cuda
                   ((uintptr_t)y & 15u) == 0;
   TmaArgs<T> a{A, c.d_conn, (const T*)u, (T*)y, c.E, ntiles, nchunks, R, skip, c.d_kerr,
                 c.d_bnd, c.dirichlet ? c.nbnd : 0, c.wait_budget, c.test_skip_chunk, r4 ? 1 : 0,
-                stream_evict_first(c, sizeof(T), FACT ? Cfg::NS : Cfg::W * Cfg::NS), add ? 1 : 0};
+                stream_evict_first(c, sizeof(T), FACT ? Cfg::NS : Cfg::W * Cfg::NS), add ? 1 : 0,
+                sizeof(T) == 4 && R == 1 && c.energy != nullptr ? *c.energy : CGEnergy{}};
   k_apply_tma<D, P, FORM, T, FACT><<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
 }
 

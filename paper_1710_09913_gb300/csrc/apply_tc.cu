@@ -48,9 +48,12 @@ struct TcArgs {
   const float* B;
   int add;          // 1: y += K u (Dirichlet rows y_b += u_b); 0: y_b = u_b
   int evict_first;  // 1: the A_T copies carry the L2 evict-first policy
+  int R;            // right-hand sides (1, or a multiple of 16 for the MR = 16 kernel)
+  int64_t test_skip;  // test hook: the A^_T copy of this work unit is never issued (-1: none)
 };
 
-template <int D, int P, int FORM>
+// MR: right-hand sides per cell in one MMA tile (1: 128 cells; 16: 8 cells x 16).
+template <int D, int P, int FORM, int MR = 1>
 struct TcCfg {
   // RT: B^ comes from the context's run-time table (2D p > 4, 3D p > 3)
   static constexpr bool RT = P > (D == 2 ? 4 : 3);
@@ -66,7 +69,7 @@ struct TcCfg {
   // for its 128 cells (four AoSoA tiles, one bulk copy)
   static constexpr uint32_t BTAB = 2 * (N1 * K1 + N2 * K2) * 4;
   static constexpr uint32_t A_TILE = W * NS * kTile * 4;
-  static constexpr uint32_t WGB = 4 * A_TILE;
+  static constexpr uint32_t WGB = MR == 1 ? 4 * A_TILE : 2 * A_TILE;
   static constexpr uint32_t kBudget = 224 * 1024;
   // tensor-memory columns of a warpgroup: [0, N1) G = D1, whose first K2 columns then
   // hold the TF32 hi part of H (the A operand of GEMM 2); [K2, 2 K2) the lo part of H;
@@ -118,9 +121,9 @@ constexpr TcTab<D, P, FORM> make_tc_tab() {
 template <int D, int P, int FORM>
 __device__ const TcTab<D, P, FORM> kTcTab = make_tc_tab<D, P, FORM>();
 
-template <int D, int P, int FORM>
-__global__ void __launch_bounds__(TcCfg<D, P, FORM>::THREADS, 1) k_apply_tc(TcArgs a) {
-  using C = TcCfg<D, P, FORM>;
+template <int D, int P, int FORM, int MR>
+__global__ void __launch_bounds__(TcCfg<D, P, FORM, MR>::THREADS, 1) k_apply_tc(TcArgs a) {
+  using C = TcCfg<D, P, FORM, MR>;
   static_assert(C::OK, "tensor-core apply does not fit in shared / tensor memory");
   constexpr int V = C::V, W = C::W, NB = C::NB, NS = C::NS, M = C::M;
   constexpr int K1 = C::K1, N1 = C::N1, K2 = C::K2, N2 = C::N2, NWG = C::NWG, CH = C::CH;
@@ -130,16 +133,16 @@ __global__ void __launch_bounds__(TcCfg<D, P, FORM>::THREADS, 1) k_apply_tc(TcAr
   float* b1l = b1h + N1 * K1;
   float* b2h = b1l + N1 * K1;
   float* b2l = b2h + N2 * K2;
-  uint64_t* bars = (uint64_t*)(base + C::BTAB + NWG * C::WGB);  // [NWG][3]
-  uint32_t* tslot = (uint32_t*)(bars + 3 * NWG);
+  uint64_t* bars = (uint64_t*)(base + C::BTAB + NWG * C::WGB);  // [NWG][4]
+  uint32_t* tslot = (uint32_t*)(bars + 4 * NWG);
   if (a.skip != nullptr && *a.skip) return;
   const int tid = threadIdx.x, wg = tid / M, m = tid % M, warp = m >> 5, lane = tid & 31;
-  unsigned char* stA = base + C::BTAB + wg * C::WGB;  // A^_T of the warpgroup's tile
-  uint64_t* mma1 = bars + 3 * wg;
+  unsigned char* stA = base + C::BTAB + wg * C::WGB;  // A^_T stage(s) of the warpgroup
+  uint64_t* mma1 = bars + 4 * wg;
   uint64_t* mma2 = mma1 + 1;
-  uint64_t* abar = mma1 + 2;
+  uint64_t* abar = mma1 + 2;  // [2]: stage barriers (MR = 16 double-buffers one 32-cell tile)
   if (tid == 0) {
-    for (int g = 0; g < 3 * NWG; ++g) mbar_init(&bars[g], 1);
+    for (int g = 0; g < 4 * NWG; ++g) mbar_init(&bars[g], 1);
     mbar_fence_init();
   }
   if constexpr (!C::RT) {  // reference tables -> shared memory, split into TF32 hi + lo
@@ -175,34 +178,60 @@ __global__ void __launch_bounds__(TcCfg<D, P, FORM>::THREADS, 1) k_apply_tc(TcAr
   const uint32_t s_b1h = smem_addr(b1h), s_b1l = smem_addr(b1l);
   const uint32_t s_b2h = smem_addr(b2h), s_b2l = smem_addr(b2l);
 
-  // Warpgroup wg takes the 128-cell tiles wg + NWG * blockIdx.x, stepping by NWG *
-  // gridDim.x: tile t holds the AoSoA tiles 4t .. 4t+3, warp w the cells of 4t + w.
+  // Work units of warpgroup wg: u = wg + NWG * blockIdx.x + k * step.  MR = 1: a unit
+  // is a 128-cell tile (AoSoA tiles 4u .. 4u+3, warp w the cells of tile 4u + w) worked
+  // as one item, its A^_T in the warpgroup's single stage.  MR = 16: a unit is one
+  // 32-cell AoSoA tile, worked as NI = R / 4 items of 8 cells x 16 right-hand sides
+  // (item i = 4 rb + q: thread m takes cell 8 q + m / 16 and right-hand side
+  // 16 rb + m % 16), so the 16 threads of a cell gather and scatter-add its dofs'
+  // 64-byte rows; its A^_T sits in one of two stages while the next unit's lands.
   const int64_t ntiles32 = (a.E + kTile - 1) / kTile;
-  const int64_t ntiles128 = (a.E + M - 1) / M, step = (int64_t)NWG * gridDim.x;
+  const int64_t nunits = MR == 1 ? (a.E + M - 1) / M : ntiles32;
+  const int64_t step = (int64_t)NWG * gridDim.x;
+  const int NI = MR == 1 ? 1 : a.R / 4;
   int64_t a_issued = 0, a_waited = 0;  // bulk copies of A^_T (thread m == 0 issues)
   const bool ef = a.evict_first != 0;
   const uint64_t pol = ef ? l2_policy_evict_first() : 0;
   auto issue_a = [&](int64_t tt) {
-    const int nt = (int)min((int64_t)4, ntiles32 - 4 * tt);
+    if (tt == a.test_skip) {  // test hook: this copy never lands, its bounded wait expires
+      ++a_issued;
+      return;
+    }
     fence_proxy_async_smem();
-    mbar_expect_tx(abar, (uint32_t)nt * C::A_TILE);
-    stream_copy(stA, (const unsigned char*)a.A + 4 * tt * C::A_TILE, (uint32_t)nt * C::A_TILE,
-                abar, ef, pol);
+    if constexpr (MR == 1) {
+      const int nt = (int)min((int64_t)4, ntiles32 - 4 * tt);
+      mbar_expect_tx(abar, (uint32_t)nt * C::A_TILE);
+      stream_copy(stA, (const unsigned char*)a.A + 4 * tt * C::A_TILE, (uint32_t)nt * C::A_TILE,
+                  abar, ef, pol);
+    } else {
+      const int sx = (int)(a_issued & 1);
+      mbar_expect_tx(abar + sx, C::A_TILE);
+      stream_copy(stA + sx * C::A_TILE, (const unsigned char*)a.A + tt * C::A_TILE, C::A_TILE,
+                  abar + sx, ef, pol);
+    }
     ++a_issued;
   };
-  auto load_conn = [&](int64_t tt, uint32_t(&cc)[V], bool& act) {
-    const int64_t at = 4 * tt + warp;
-    act = tt < ntiles128 && at * kTile + lane < a.E;
-    const uint32_t* src = a.conn + at * (V * kTile) + lane;
+  // the bounded wait for copy number q (its stage and phase)
+  auto wait_a = [&](int64_t q) {
+    if constexpr (MR == 1) return mbar_wait_bounded(abar, (uint32_t)(q & 1), a.wait_budget);
+    else return mbar_wait_bounded(abar + (q & 1), (uint32_t)((q >> 1) & 1), a.wait_budget);
+  };
+  auto cell32_of = [&](int i) { return MR == 1 ? lane : 8 * (i & 3) + (m >> 4); };
+  auto rhs_of = [&](int i) { return MR == 1 ? 0 : 16 * (i >> 2) + (m & 15); };
+  auto load_conn = [&](int64_t tt, int i, uint32_t(&cc)[V], bool& act) {
+    const int64_t at = MR == 1 ? 4 * tt + warp : tt;
+    const int cl = cell32_of(i);
+    act = tt < nunits && at * kTile + cl < a.E;
+    const uint32_t* src = a.conn + at * (V * kTile) + cl;
     static_for<V>([&](auto lc) {
       constexpr int l = decltype(lc)::value;
       cc[l] = act ? __ldg(src + l * kTile) : kBndBit;
     });
   };
-  auto gather = [&](const uint32_t(&cc)[V], float(&dst)[V]) {
+  auto gather = [&](const uint32_t(&cc)[V], int r, float(&dst)[V]) {
     static_for<V>([&](auto lc) {
       constexpr int l = decltype(lc)::value;
-      dst[l] = (cc[l] & kBndBit) ? 0.0f : __ldg(a.u + (cc[l] & kIdMask));
+      dst[l] = (cc[l] & kBndBit) ? 0.0f : __ldg(a.u + (int64_t)(cc[l] & kIdMask) * a.R + r);
     });
   };
   int failed = 0;
@@ -211,10 +240,15 @@ __global__ void __launch_bounds__(TcCfg<D, P, FORM>::THREADS, 1) k_apply_tc(TcAr
   float ul[V], un[V];
   bool active, active_n;
   int64_t t = (int64_t)blockIdx.x * NWG + wg;
-  if (m == 0 && t < ntiles128) issue_a(t);
-  load_conn(t, c, active);
-  gather(c, ul);
-  for (; t < ntiles128; t += step) {  // the same trip count in the whole warpgroup
+  int it = 0;
+  if (m == 0 && t < nunits) issue_a(t);
+  if constexpr (MR != 1)
+    if (m == 0 && t + step < nunits) issue_a(t + step);  // the second stage
+  load_conn(t, 0, c, active);
+  gather(c, rhs_of(0), ul);
+  while (t < nunits) {  // the same trip count in the whole warpgroup
+    const int64_t tn = it + 1 < NI ? t : t + step;  // next item
+    const int itn = it + 1 < NI ? it + 1 : 0;
     // U -> tensor memory (hi, lo); columns V..K1-1 are zero
     static_for<K1 / 8>([&](auto qc) {
       constexpr int q = decltype(qc)::value;
@@ -228,7 +262,7 @@ __global__ void __launch_bounds__(TcCfg<D, P, FORM>::THREADS, 1) k_apply_tc(TcAr
       tc::tmem_st8(uhi + lane_base + (uint32_t)(8 * q), h);
       tc::tmem_st8(ulo + lane_base + (uint32_t)(8 * q), l);
     });
-    load_conn(t + step, cn, active_n);  // next tile's conn: in flight during this tile
+    load_conn(tn, itn, cn, active_n);  // next item's conn: in flight during this item
     tc::tmem_st_wait();
     tc::fence_before_sync();
     if (tc::bar_or(1 + wg, M, failed)) {
@@ -250,14 +284,16 @@ __global__ void __launch_bounds__(TcCfg<D, P, FORM>::THREADS, 1) k_apply_tc(TcAr
       tc::mma_commit(mma1);
     }
     int f = __any_sync(0xffffffffu, mbar_wait_bounded(mma1, phase, a.wait_budget) ? 0 : 1);
-    f |= __any_sync(0xffffffffu,
-                    mbar_wait_bounded(abar, (uint32_t)(a_waited & 1), a.wait_budget) ? 0 : 1);
-    ++a_waited;
+    if (it == 0) {  // the unit's A^_T stage
+      f |= __any_sync(0xffffffffu, wait_a(a_waited) ? 0 : 1);
+      ++a_waited;
+    }
     tc::fence_after_sync();
     // G (tensor memory) -> H_j = A^_T,j G_j -> H hi over the G columns, H lo at K2.
     // Only the K2 columns GEMM 2 reads are stored: the G columns from K2 on are the
     // zero rows of B1, never used, and may be overwritten by H lo before they are read.
-    const float* sA = (const float*)(stA + warp * C::A_TILE) + lane;
+    const float* sA = MR == 1 ? (const float*)(stA + warp * C::A_TILE) + lane
+                              : (const float*)(stA + ((a_waited - 1) & 1) * C::A_TILE) + cell32_of(it);
     static_for<N1 / CH>([&](auto bc) {
       constexpr int b = decltype(bc)::value;
       constexpr int j0 = b * CH / NB, j1 = (b + 1) * CH / NB < W ? (b + 1) * CH / NB : W;
@@ -295,14 +331,20 @@ __global__ void __launch_bounds__(TcCfg<D, P, FORM>::THREADS, 1) k_apply_tc(TcAr
       });
     });
     tc::tmem_st_wait();
-    gather(cn, un);  // next tile's u (its conn has arrived by now)
+    gather(cn, rhs_of(itn), un);  // next item's u (its conn has arrived by now)
     tc::fence_before_sync();
     if (tc::bar_or(1 + wg, M, f)) {  // the warpgroup is done with the A^_T stage and H
       failed = 1;
       break;
     }
     if (m == 0) {
-      if (t + step < ntiles128) issue_a(t + step);  // next tile's A^_T into the free stage
+      // refill the stage just read: the next unit (MR = 1), or the unit after next once
+      // the last item of this one has read its A^_T (MR = 16)
+      if constexpr (MR == 1) {
+        if (t + step < nunits) issue_a(t + step);
+      } else {
+        if (it + 1 == NI && t + 2 * step < nunits) issue_a(t + 2 * step);
+      }
       tc::fence_after_sync();  // GEMM 2: Y = H B2, H from tensor memory
       constexpr uint32_t idesc = tc::idesc_tf32(M, N2);
       static_for<K2 / 8>([&](auto sc) {
@@ -319,18 +361,18 @@ __global__ void __launch_bounds__(TcCfg<D, P, FORM>::THREADS, 1) k_apply_tc(TcAr
     f = __any_sync(0xffffffffu, mbar_wait_bounded(mma2, phase, a.wait_budget) ? 0 : 1);
     tc::fence_after_sync();
     phase ^= 1u;
-    if (!f) {  // Y (tensor memory) -> y += P_T^T Y_T
+    if (!f) {  // Y (tensor memory) -> y += P_T^T Y_T, shared dofs of paired cells pre-summed
+      float Y[1][V];
       static_for<N2 / 16>([&](auto bc) {
         constexpr int b = decltype(bc)::value;
         float v[16];
         tc::tmem_ld16(d2 + lane_base + (uint32_t)(16 * b), v);
         static_for<16>([&](auto ec) {
           constexpr int l = 16 * b + decltype(ec)::value;
-          if constexpr (l < V) {
-            if (!(c[l] & kBndBit)) atomicAdd(a.y + (c[l] & kIdMask), v[l - 16 * b]);
-          }
+          if constexpr (l < V) Y[0][l] = v[l - 16 * b];
         });
       });
+      scatter_pairs<V, 1, float, MR == 1 ? 1 : 16>(c, Y, lane, a.y, a.R, rhs_of(it));
     }
     tc::fence_before_sync();
     failed = f;
@@ -340,12 +382,13 @@ __global__ void __launch_bounds__(TcCfg<D, P, FORM>::THREADS, 1) k_apply_tc(TcAr
       ul[l] = un[l];
     });
     active = active_n;
+    t = tn;
+    it = itn;
   }
-  // a copy issued for a tile this warpgroup did not reach (after a failed wait) must
+  // a copy issued for a unit this warpgroup did not reach (after a failed wait) must
   // land before the shared memory is released
   if (m == 0)
-    for (int64_t q = a_waited; q < a_issued; ++q)
-      mbar_wait_bounded(abar, (uint32_t)(q & 1), a.wait_budget);
+    for (int64_t q = a_waited; q < a_issued; ++q) wait_a(q);
   if (failed && lane == 0) atomicOr(a.err, 1);
   tc::fence_before_sync();
   __syncthreads();
@@ -353,10 +396,10 @@ __global__ void __launch_bounds__(TcCfg<D, P, FORM>::THREADS, 1) k_apply_tc(TcAr
     tc::fence_after_sync();
     tc::tmem_dealloc(tmem, C::TMC);
   }
-  // Dirichlet rows: y_b = u_b (the scatter skipped them)
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + tid; i < a.nbnd;
+  // Dirichlet rows: y_b = u_b, or y_b += u_b (the scatter skipped them)
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + tid; i < a.nbnd * a.R;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t idx = a.bnd[i];
+    const int64_t idx = (int64_t)a.bnd[i / a.R] * a.R + i % a.R;
     a.y[idx] = a.add ? a.y[idx] + a.u[idx] : a.u[idx];
   }
 }
@@ -368,11 +411,11 @@ struct TcLaunch {
   int num_sms = 1;
 };
 
-template <int D, int P, int FORM>
+template <int D, int P, int FORM, int MR>
 const TcLaunch& tc_launch() {
   static const TcLaunch info = [] {
-    using Cfg = TcCfg<D, P, FORM>;
-    auto kern = k_apply_tc<D, P, FORM>;
+    using Cfg = TcCfg<D, P, FORM, MR>;
+    auto kern = k_apply_tc<D, P, FORM, MR>;
     TcLaunch t;
     cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM),
                "tensor-core apply smem attribute");
@@ -388,24 +431,39 @@ const TcLaunch& tc_launch() {
   return info;
 }
 
-template <int D, int P, int FORM>
-bool run_tc(const Ctx& c, const void* u, void* y, cudaStream_t s, const int* skip, bool add) {
-  if constexpr (!TcCfg<D, P, FORM>::OK) {
+template <int D, int P, int FORM, int MR>
+bool run_tc_mr(const Ctx& c, const void* u, void* y, int R, cudaStream_t s, const int* skip,
+               bool add) {
+  if constexpr (!TcCfg<D, P, FORM, MR>::OK) {
     return false;
   } else {
-    using Cfg = TcCfg<D, P, FORM>;
-    const TcLaunch& L = tc_launch<D, P, FORM>();
+    using Cfg = TcCfg<D, P, FORM, MR>;
+    const TcLaunch& L = tc_launch<D, P, FORM, MR>();
     if (u == nullptr) return true;  // preparation call from context set-up
-    const int64_t ntiles128 = (c.E + Cfg::M - 1) / Cfg::M;
-    if (ntiles128 == 0) return true;
-    const int64_t grid = std::min<int64_t>((ntiles128 + Cfg::NWG - 1) / Cfg::NWG,
+    const int64_t units = MR == 1 ? (c.E + Cfg::M - 1) / Cfg::M : (c.E + kTile - 1) / kTile;
+    if (units == 0) return true;
+    const int64_t grid = std::min<int64_t>((units + Cfg::NWG - 1) / Cfg::NWG,
                                            (int64_t)L.num_sms * L.blocks);
     TcArgs a{c.d_A32, c.d_conn, (const float*)u, (float*)y, c.E, skip, c.d_kerr, c.d_bnd,
              c.dirichlet ? c.nbnd : 0, c.wait_budget, Cfg::RT ? c.d_hiB32 : nullptr, add ? 1 : 0,
-             stream_evict_first(c, sizeof(float), Cfg::W * Cfg::NS)};
-    k_apply_tc<D, P, FORM><<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
+             stream_evict_first(c, sizeof(float), Cfg::W * Cfg::NS), R, c.test_skip_chunk};
+    k_apply_tc<D, P, FORM, MR><<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
     return true;
   }
+}
+
+// One right-hand side: 128-cell MMA tiles; a multiple of 16: 8 cells x 16 rhs tiles.
+template <int D, int P, int FORM>
+bool run_tc(const Ctx& c, const void* u, void* y, int R, cudaStream_t s, const int* skip,
+            bool add) {
+  if (u == nullptr) {
+    const bool a1 = run_tc_mr<D, P, FORM, 1>(c, u, y, R, s, skip, add);
+    const bool a16 = run_tc_mr<D, P, FORM, 16>(c, u, y, R, s, skip, add);
+    return a1 || a16;
+  }
+  if (R == 1) return run_tc_mr<D, P, FORM, 1>(c, u, y, R, s, skip, add);
+  if (R % 16 == 0) return run_tc_mr<D, P, FORM, 16>(c, u, y, R, s, skip, add);
+  return false;
 }
 
 }  // namespace
@@ -421,18 +479,19 @@ bool apply_tc_available(int d, int p, int form) {
   return false;
 }
 
-// FP32 apply with one right-hand side, atomic scatter over the whole cell range;
-// false when no tensor-core instance exists for (d, p, form).  u == nullptr only sets
-// the kernel attributes (context set-up, outside any stream capture).
-bool apply_tc(const Ctx& c, const void* u, void* y, cudaStream_t s, const int* skip, bool add) {
+// FP32 apply with R = 1 or a multiple of 16 right-hand sides, atomic scatter over the
+// whole cell range; false when no tensor-core instance exists for (d, p, form) or R.
+// u == nullptr only sets the kernel attributes (context set-up, outside any capture).
+bool apply_tc(const Ctx& c, const void* u, void* y, cudaStream_t s, const int* skip, bool add,
+              int R) {
   if (c.global_w || c.factorized || !c.keep32 || !apply_tc_available(c.d, c.p, c.form))
     return false;
   if (c.hi && c.d_hiB32 == nullptr) return false;
   const bool ell = c.form == DOGIP_ELLIPTIC;
 #define DOGIP_TC_CASE(D, P)                                                          \
   if (c.d == D && c.p == P)                                                          \
-    return ell ? run_tc<D, P, DOGIP_ELLIPTIC>(c, u, y, s, skip, add)                 \
-               : run_tc<D, P, DOGIP_PROJECTION>(c, u, y, s, skip, add);
+    return ell ? run_tc<D, P, DOGIP_ELLIPTIC>(c, u, y, R, s, skip, add)              \
+               : run_tc<D, P, DOGIP_PROJECTION>(c, u, y, R, s, skip, add);
   DOGIP_TC_CASE(2, 1)
   DOGIP_TC_CASE(2, 2)
   DOGIP_TC_CASE(2, 3)

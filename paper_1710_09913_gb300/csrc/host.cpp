@@ -614,13 +614,17 @@ bool r_ok(int R) { return R == 1 || R == 2 || R == 4 || R == 8 || R == 16 || R =
 
 // One chunk of `k` CG iterations on the solver stream, captured once as a CUDA
 // graph and replayed; ends with a copy of the flags and scalars to pinned host.
-void run_chunk(Ctx& c, int prec, int scatter, double* x64, int k, double delta) {
+// rec (FP32, one right-hand side): 0 the standard recurrence in four kernels (apply,
+// p.q, x/r update, p update); 1 the same with p.Kp reduced from the element energies
+// inside the apply (three kernels); 2 the single-reduction recurrence of Chronopoulos
+// and Gear (two kernels: vec_cgcg_step, then the apply with the energy reduction).
+void run_chunk(Ctx& c, int prec, int scatter, double* x64, int k, double delta, int rec = 0) {
   SolveWork& w = c.work;
   cudaStream_t s = c.stream;
   const void* key0 = prec == DOGIP_FP64 ? (const void*)x64 : (const void*)w.x32;
   const bool hit = w.graph && w.graph_prec == prec && w.graph_scatter == scatter &&
                    w.graph_chunk == k && w.graph_key[0] == key0 && w.graph_key[1] == (void*)w.p64 &&
-                   w.graph_delta == delta;
+                   w.graph_delta == delta && w.graph_fused == rec;
   if (!hit) {
     if (w.graph) cudaGraphExecDestroy(w.graph);
     w.graph = nullptr;
@@ -628,7 +632,15 @@ void run_chunk(Ctx& c, int prec, int scatter, double* x64, int k, double delta) 
     cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
     try {
       const void* dinv = prec == DOGIP_FP64 ? (const void*)c.d_dinv64 : (const void*)c.d_dinv32;
-      for (int it = 0; it < k; ++it) {
+      for (int it = 0; it < k && rec == 2; ++it) {
+        c.launches += vec_cgcg_step(w, c.d_dinv32, s);
+        launch_apply_energy(c, w.p32, w.q32, s, w, 1);
+      }
+      for (int it = 0; it < k && rec == 1; ++it) {
+        launch_apply_energy(c, w.p32, w.q32, s, w, 0);  // q = K p, alpha = rho / (p, K p)
+        c.launches += vec_cg_step(w, DOGIP_FP32, x64, dinv, delta, s, true, false);
+      }
+      for (int it = 0; it < k && rec == 0; ++it) {
         if (prec == DOGIP_FP64) launch_apply_cg(c, w.p64, w.q64, w.R, DOGIP_FP64, scatter, s, w);
         else launch_apply_cg(c, w.p32, w.q32, w.R, prec, scatter, s, w);  // FP32 or TF32 apply
         c.launches += vec_cg_step(w, prec == DOGIP_FP64 ? DOGIP_FP64 : DOGIP_FP32, x64, dinv, delta,
@@ -666,6 +678,7 @@ void run_chunk(Ctx& c, int prec, int scatter, double* x64, int k, double delta) 
     w.graph_scatter = scatter;
     w.graph_chunk = k;
     w.graph_delta = delta;
+    w.graph_fused = rec;
     w.graph_key[0] = key0;
     w.graph_key[1] = w.p64;
   }
@@ -704,10 +717,20 @@ int solve(Ctx& c, const double* b, double* u, int R, const dogip_solve_opts* opt
   if (o.inner_prec != DOGIP_FP32 && o.inner_prec != DOGIP_TF32)
     fail(DOGIP_EINVAL, "inner_prec must be DOGIP_FP32 or DOGIP_TF32");
   const int ip = o.mode == DOGIP_SOLVE_FP64 ? DOGIP_FP64 : o.inner_prec;  // inner apply
-  if (ip == DOGIP_TF32 && (R != 1 || scatter != DOGIP_SCATTER_ATOMIC || c.global_w ||
-                           c.factorized || !apply_tc_available(c.d, c.p, c.form)))
+  if (o.inner_recurrence < 0 || o.inner_recurrence > 2)
+    fail(DOGIP_EINVAL, "inner_recurrence must be 0, 1 or 2");
+  // inner FP32 recurrence of the mixed mode (run_chunk's rec)
+  const bool fusable = o.mode == DOGIP_SOLVE_MIXED && cgcg_eligible(c, R, ip, scatter);
+  const int rec = o.inner_recurrence == 2 ? 2 : (o.inner_recurrence == 0 && fusable ? 1 : 0);
+  if (o.mode == DOGIP_SOLVE_MIXED && rec == 2 && !fusable)
     fail(DOGIP_EUNSUPPORTED,
-         "TF32 inner applies need one right-hand side, atomic scatter and a tensor-core instance");
+         "the single-reduction inner CG needs one right-hand side, FP32 inner applies, atomic "
+         "scatter and the staged apply kernel");
+  if (ip == DOGIP_TF32 && ((R != 1 && R % 16 != 0) || scatter != DOGIP_SCATTER_ATOMIC ||
+                           c.global_w || c.factorized || !apply_tc_available(c.d, c.p, c.form)))
+    fail(DOGIP_EUNSUPPORTED,
+         "TF32 inner applies need 1 or a multiple of 16 right-hand sides, atomic scatter and a "
+         "tensor-core instance");
   const int chunk = std::max(1, o.check_every);
   DeviceGuard guard(c.device);
   ensure_w_scratch(c, R);
@@ -807,14 +830,27 @@ int solve(Ctx& c, const double* b, double* u, int R, const dogip_solve_opts* opt
       if (outer >= o.max_outer) { status = DOGIP_ENOTCONV; break; }
       if (budget <= 0) { status = DOGIP_ENOTCONV; break; }
       if (timed_out()) { status = DOGIP_ETIMEOUT; break; }
-      c.launches += vec_inner_init32(w, c.d_dinv32, o.inner_tol, s);
+      // Each inner solve reduces the FP32 residual by inner_tol, but never by more
+      // than the FP64 residual still needs (with a margin of 5 for the FP32 solve's
+      // own accuracy): the last refinement step then takes a few iterations instead
+      // of a whole inner solve.
+      double worst_rel = 0.0;
+      for (int r = 0; r < R; ++r)
+        if (!w.h_scal[r].odone) worst_rel = std::max(worst_rel, w.h_scal[r].rel);
+      double itol = o.inner_tol;
+      if (worst_rel > 0.0) itol = std::max(itol, std::min(0.5, 0.2 * o.tol / worst_rel));
+      c.launches += vec_inner_init32(w, c.d_dinv32, itol, s);
+      if (rec == 2) {  // w0 = K u0 and alpha0 = gamma0 / (w0, u0)
+        vec_alloc_cgcg(w);
+        launch_apply_energy(c, w.p32, w.q32, s, w, 1);
+      }
       read_scal(c);
       int inner = 0;
       const int lim = std::min(o.inner_maxiter, budget);
       while (!w.h_flags[0] && inner < lim) {
         if (timed_out()) break;
         const int k = std::min(chunk, lim - inner);
-        run_chunk(c, ip, scatter, nullptr, k, 0.0);
+        run_chunk(c, ip, scatter, nullptr, k, 0.0, rec);
         inner = 0;
         for (int r = 0; r < R; ++r) inner = std::max(inner, w.h_scal[r].iters);
         if (w.h_flags[1]) break;
@@ -1082,9 +1118,10 @@ int batch_solve(Ctx* const* ctxs, int np, const double* const* b, double* const*
 
 // --------------------------------------------------------------- autotuner
 //
-// Picks, per precision, the apply kernel (bulk-async staged, or one thread per
-// cell with 64 / 128 / 256 cells per CTA) by timing each on the context's own data
-// (CUDA events, median of 5 after 2 warm-up applies).  Choices are cached process-
+// Picks, per precision, the apply kernel (tensor cores, self-feeding warps, bulk-async
+// staged, or one thread per cell with 64 / 128 / 256 cells per CTA) by timing each on
+// the context's own data (the kernel alone: best of 3 samples of 8 launches, CUDA
+// events; FP32 keeps the staged kernel within 3 %).  Choices are cached process-
 // wide per (dim, p, form, precision, log2 of the cell count); with DOGIP_TUNE_CACHE
 // set they are also read from and appended to that text file.
 
@@ -1160,6 +1197,7 @@ int autotune(Ctx& c, int force, cudaStream_t s) {
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     TuneChoice best{1, 256, 1e30f};
+    float staged_ms = 1e30f;
     try {
       cuda_check(cudaMemsetAsync(u, 0, es * c.n, s), "tuning input");
       cuda_check(cudaEventCreate(&e0), "event");
@@ -1173,18 +1211,29 @@ int autotune(Ctx& c, int force, cudaStream_t s) {
         if (c.hi && var != 3 && var != 1) continue;  // 1: the run-time-table kernel
         c.apply_variant_prec[prec] = var;
         c.apply_block[prec] = blk;
-        for (int w = 0; w < 2; ++w) launch_apply(c, u, y, 1, prec, DOGIP_SCATTER_ATOMIC, s, nullptr);
-        std::vector<float> t(5);
-        for (float& ti : t) {
+        // the kernel alone (y += K u into a buffer that stays finite: u = 0), eight
+        // launches back to back per sample, best of three samples after a warm-up
+        for (int w = 0; w < 3; ++w)
+          launch_apply(c, u, y, 1, prec, DOGIP_SCATTER_ATOMIC, s, nullptr, true);
+        float tbest = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
           cuda_check(cudaEventRecord(e0, s), "event record");
-          launch_apply(c, u, y, 1, prec, DOGIP_SCATTER_ATOMIC, s, nullptr);
+          for (int w = 0; w < 8; ++w)
+            launch_apply(c, u, y, 1, prec, DOGIP_SCATTER_ATOMIC, s, nullptr, true);
           cuda_check(cudaEventRecord(e1, s), "event record");
           cuda_check(cudaEventSynchronize(e1), "tuning sync");
+          float ti = 0.0f;
           cuda_check(cudaEventElapsedTime(&ti, e0, e1), "elapsed");
+          tbest = std::min(tbest, ti / 8.0f);
         }
-        std::sort(t.begin(), t.end());
-        if (t[2] < best.ms) best = TuneChoice{var, blk, t[2]};
+        if (var == 1) staged_ms = tbest;
+        if (tbest < best.ms) best = TuneChoice{var, blk, tbest};
       }
+      // FP32: the staged kernel also carries the (p, K p) reduction of the mixed
+      // solve's inner iterations (one kernel less each), so it is kept unless another
+      // kernel is faster by more than 3 %
+      if (prec == DOGIP_FP32 && !c.hi && staged_ms <= 1.03f * best.ms)
+        best = TuneChoice{1, 256, staged_ms};
     } catch (...) {
       if (e0) cudaEventDestroy(e0);
       if (e1) cudaEventDestroy(e1);
@@ -1264,6 +1313,7 @@ int dogip_solve_opts_default(dogip_solve_opts* o) {
   o->timeout_ms = 0.0;
   o->reliable_delta = 0.1;
   o->inner_prec = DOGIP_FP32;
+  o->inner_recurrence = 0;
   return DOGIP_OK;
 }
 

@@ -40,6 +40,9 @@ struct SolveWork {
   double *x64 = nullptr, *r64 = nullptr, *p64 = nullptr, *q64 = nullptr;
   // FP32 vectors [n x R]
   float *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+  // Chronopoulos-Gear inner CG (R = 1): search direction p and s = K p; u (= M r) and
+  // w (= K u) live in p32 and q32
+  float *pc32 = nullptr, *sc32 = nullptr;
   // reductions
   double* partial = nullptr;     // [kMaxRedBlocks x 32 x 2]
   unsigned int* counter = nullptr;
@@ -52,7 +55,20 @@ struct SolveWork {
   const void* graph_key[4] = {nullptr, nullptr, nullptr, nullptr};
   int graph_chunk = 0, graph_prec = -1, graph_scatter = -1;
   double graph_delta = -1.0;
+  int graph_fused = -1;
   int64_t graph_kernels = 0;  // kernel nodes in the captured chunk
+};
+
+// Reduction target of the energy form of the apply (CG with one right-hand side): the
+// apply kernel adds (y, u) = sum_T u_T . Y_T (+ the Dirichlet rows) per CTA into
+// partial[CTA], and its last CTA sets alpha in scal: rho / (p, K p) for the standard
+// recurrence (mode 0), the single-reduction formula of Chronopoulos and Gear (mode 1).
+struct CGEnergy {
+  double* partial;
+  unsigned int* counter;
+  CGScal* scal;
+  int* flags;
+  int mode;
 };
 
 constexpr int kMaxRedBlocks = 1216;  // 8 blocks of 256 threads on each of 152 SMs
@@ -118,6 +134,9 @@ struct dogip_ctx {
   int64_t l2_bytes = 0;        // L2 size of the device: streams larger than half of it
                                // are copied with the L2 evict-first policy
   int64_t test_skip_chunk = -1;  // test hook (see DOGIP_TEST_SKIP_CHUNK)
+  // set around one launch by launch_apply_energy (host, one thread per context): the
+  // staged kernel then also reduces (w, u) and sets alpha
+  mutable const dogip::CGEnergy* energy = nullptr;
   dogip::SolveWork work;
   int64_t launches = 0;           // kernels launched (graph replays count every node)
   cudaStream_t stream = nullptr;  // private stream for graph-captured solves
@@ -186,11 +205,11 @@ bool load_hi(const Ctx& c, LoadArgs& a, cudaStream_t s);
 bool hi_table(int d, int p, int form, int* NB, int* W, int* V, long long* nnz, long long* nnz1,
               const double** B, const double** w, const double** iv);
 bool table_is_compiled(int d, int p, int form);
-// Tensor-core FP32 apply (apply_tc.cu): one right-hand side, atomic scatter over the
-// whole cell range.  false when no instance exists for (d, p, form); u == nullptr
-// only sets the kernel attributes (context set-up).
+// Tensor-core FP32 apply (apply_tc.cu): R = 1 or a multiple of 16 right-hand sides,
+// atomic scatter over the whole cell range.  false when no instance exists for
+// (d, p, form) or R; u == nullptr only sets the kernel attributes (context set-up).
 bool apply_tc(const Ctx& c, const void* u, void* y, cudaStream_t s, const int* skip,
-              bool add = false);
+              bool add = false, int R = 1);
 bool apply_tc_available(int d, int p, int form);
 // Global double-grid apply of the weighted projection (two kernels); false when no
 // instance exists.  The scratch must hold R right-hand sides (ensure_w_scratch).
@@ -228,7 +247,18 @@ int vec_init64(SolveWork& w, const double* dinv, double tol, cudaStream_t st);
 // zero_q: clear q for the next scatter-add apply (every atomic-scatter iteration;
 // colour passes clear it themselves).
 int vec_cg_step(SolveWork& w, int prec, double* x64, const void* dinv, double delta,
-                cudaStream_t st, bool zero_q);
+                cudaStream_t st, bool zero_q, bool with_pq = true);
+// Chronopoulos-Gear FP32 inner CG (R = 1), two kernels per iteration:
+//   vec_cgcg_step: p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = Dinv r,
+//                  w = 0, gamma = r.u, rr = r.r; beta = gamma / gamma_old; convergence test
+//   launch_apply_energy: w = K u with (w, u) reduced in the apply; alpha = gamma /
+//                  ((w, u) - beta gamma / alpha_old)
+// false from launch_apply_energy when the context's FP32 apply is not the staged kernel.
+int vec_cgcg_step(SolveWork& w, const float* dinv, cudaStream_t st);
+void vec_alloc_cgcg(SolveWork& w);
+bool cgcg_eligible(const Ctx& c, int R, int prec, int scatter);
+void launch_apply_energy(Ctx& c, const float* u, float* w, cudaStream_t s, SolveWork& wk,
+                         int mode);
 // Reliable-update mixed CG (FP32 recursion, FP64 corrections):
 // start: r32 = r64, x32 = 0, p = Dinv r32, rho, r0 = ||b||, rmax = ||r64||.
 int vec_rel_init(SolveWork& w, const float* dinv, double tol, cudaStream_t st);

@@ -261,18 +261,20 @@ __device__ __forceinline__ void stream_copy(void* dst, const void* src, uint32_t
 // as the two triangles of a split square -- first add their values in registers, so
 // one atomic goes to L2 instead of two.  Every lane of the warp must call this (the
 // shuffles); inactive lanes pass conn entries with the Dirichlet bit and Y = 0.
-template <int V, int RW, typename T>
+// LD: lane distance of the two cells (1 with one cell per lane; 4 when four lanes
+// share a cell, each with 4 of its right-hand sides).
+template <int V, int RW, typename T, int LD = 1>
 __device__ __forceinline__ void scatter_pairs(const uint32_t (&c)[V], T (&Y)[RW][V], int lane,
                                               T* y, int R, int r) {
   static_for<V>([&](auto lc) {
     constexpr int l = decltype(lc)::value;
-    const bool same = __shfl_xor_sync(0xffffffffu, c[l], 1) == c[l];
+    const bool same = __shfl_xor_sync(0xffffffffu, c[l], LD) == c[l];
     static_for<RW>([&](auto qc) {
       constexpr int q = decltype(qc)::value;
-      const T other = __shfl_xor_sync(0xffffffffu, Y[q][l], 1);
+      const T other = __shfl_xor_sync(0xffffffffu, Y[q][l], LD);
       if (same) Y[q][l] += other;
     });
-    if (!(c[l] & kBndBit) && !(same && (lane & 1))) {
+    if (!(c[l] & kBndBit) && !(same && (lane & LD))) {
       T* dst = y + (int64_t)(c[l] & kIdMask) * R + r;
       if constexpr (RW == 4)
         atomicAdd((float4*)dst, make_float4(Y[0][l], Y[1][l], Y[2][l], Y[3][l]));
@@ -327,7 +329,9 @@ struct TmaCfg {
   static constexpr uint32_t CHUNK = TPC * (A_TILE + C_TILE);
   static constexpr uint32_t PRO = TPC * C_TILE;  // conn of the CTA's first chunk
   static constexpr int S0 = (int)((kBudget - PRO) / CHUNK);
-  static constexpr int S = S0 > 4 ? 4 : (S0 < 2 ? 2 : S0);  // pipeline stages
+  // pipeline stages: up to 8 where the tiles are small (low orders), so that enough
+  // bytes are in flight per SM
+  static constexpr int S = S0 > 8 ? 8 : (S0 < 2 ? 2 : S0);
   static constexpr uint32_t SMEM = S * CHUNK + PRO + (2 * S + 1) * 8 + 128;  // + bars, align
   static constexpr int THREADS = (TPC + 1) * 32;  // TPC consumer warps + 1 producer warp
   // Instances whose double-buffered 2-warp ring does not fit (3D P3 FP64) use the
@@ -352,7 +356,63 @@ struct TmaArgs {
   int r4;                   // 1: FP32, R % 4 == 0, u and y 16-byte aligned
   int evict_first;          // 1: A_T and conn copies carry the L2 evict-first policy
   int add;                  // 1: y += K u (Dirichlet rows y_b += u_b); 0: y_b = u_b
+  CGEnergy en;              // en.partial != null (FP32, R = 1): also reduce (y, u), set alpha
 };
+
+// End of an apply with the energy reduction (one right-hand side): the CTA's
+// (y, u) = sum of its cells' u_T . Y_T and Dirichlet rows u_b^2 goes to
+// en.partial[CTA]; the last CTA adds the partials -- one per thread, xor-shuffle
+// sums per warp, warps in order: a fixed order, so the result is deterministic --
+// and sets alpha: rho / delta (standard recurrence, en.mode 0) or gamma / (delta -
+// beta gamma / alpha_old) (single-reduction recurrence, en.mode 1), or flags a
+// breakdown.
+__device__ __forceinline__ void cg_energy_finish(const CGEnergy& en, double e) {
+  __shared__ double ws[32];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
+  if (lane == 0) ws[wid] = e;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += ws[w];
+    en.partial[blockIdx.x] = t;
+    __threadfence();
+    last = atomicAdd(en.counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double v = 0.0;
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) v += __ldcg(en.partial + b);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  __syncthreads();  // every warp has read ws above
+  if (lane == 0) ws[wid] = v;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double delta = 0.0;
+  for (int w = 0; w < nw; ++w) delta += ws[w];
+  CGScal& sc = en.scal[0];
+  if (!sc.done) {
+    const double den = en.mode == 0 || sc.beta == 0.0 ? delta : delta - sc.beta * sc.rho / sc.alpha;
+    if (!(den > 0.0) || !isfinite(den)) {
+      sc.brk = 1;
+      sc.done = 1;
+      sc.alpha = 0.0;
+    } else {
+      sc.pq = delta;
+      sc.alpha = sc.rho / den;
+    }
+  }
+  en.flags[0] = sc.done | sc.upd;
+  en.flags[1] = sc.brk;
+  en.flags[2] = sc.done;
+  en.flags[3] = sc.upd;
+  *en.counter = 0u;
+}
+
 
 template <int D, int P, int FORM, typename T, bool FACT>
 __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T, FACT>::THREADS)
@@ -375,6 +435,7 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T, FACT>::THREADS)
   if (a.skip != nullptr && *a.skip) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t G = gridDim.x, k0 = blockIdx.x;
+  double e_acc = 0.0;  // (y, u) of this thread's cells (energy reduction only)
   if (tid == 0) {
     for (int s = 0; s < C::S; ++s) {
       mbar_init(&full[s], 1);
@@ -543,6 +604,16 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T, FACT>::THREADS)
               static_for<V>([&](auto lc) { Y[decltype(qc)::value][decltype(lc)::value] = T(0); });
             });
           }
+          if constexpr (RW == 1 && std::is_same<T, float>::value) {
+            if (a.en.partial != nullptr) {  // this cell's energy u_T . Y_T
+              float el = 0.0f;
+              static_for<V>([&](auto lc) {
+                constexpr int l = decltype(lc)::value;
+                el = fmaf(ul[0][l], Y[0][l], el);
+              });
+              e_acc += (double)el;
+            }
+          }
           scatter_pairs<V, RW, T>(c, Y, lane, a.y, a.R, r);
           if constexpr (PFW) {
             static_for<V>([&](auto lc) {
@@ -573,8 +644,12 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T, FACT>::THREADS)
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + tid; t < a.nbnd * a.R;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t idx = (int64_t)a.bnd[t / a.R] * a.R + (t % a.R);
-    a.y[idx] = a.add ? a.y[idx] + a.u[idx] : a.u[idx];
+    const T ub = a.u[idx];
+    a.y[idx] = a.add ? a.y[idx] + ub : ub;
+    if constexpr (std::is_same<T, float>::value) e_acc += (double)ub * (double)ub;
   }
+  if constexpr (std::is_same<T, float>::value)
+    if (a.en.partial != nullptr) cg_energy_finish(a.en, e_acc);
 }
 
 // ------------------------------------------------- self-feeding warps apply

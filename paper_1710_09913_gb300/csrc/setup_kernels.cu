@@ -227,7 +227,8 @@ void launch_apply_cg(Ctx& c, const void* p, void* q, int R, int prec, int scatte
     return;
   }
   if (prec == DOGIP_TF32) {  // tensor-core kernel; it writes the Dirichlet rows itself
-    if (R != 1 || scatter != DOGIP_SCATTER_ATOMIC || !apply_tc(c, p, q, s, w.flags))
+    if ((R != 1 && R % 16 != 0) || scatter != DOGIP_SCATTER_ATOMIC ||
+        !apply_tc(c, p, q, s, w.flags, false, R))
       fail(DOGIP_EUNSUPPORTED, "no tensor-core apply for this context and request");
     cuda_check(cudaGetLastError(), "tensor-core apply launch");
     c.launches += 1;
@@ -247,17 +248,44 @@ void launch_apply_cg(Ctx& c, const void* p, void* q, int R, int prec, int scatte
   launch_apply(c, p, q, R, prec, scatter, s, w.flags);  // colour passes (memset inside)
 }
 
+bool cgcg_eligible(const Ctx& c, int R, int prec, int scatter) {
+  if (R != 1 || prec != DOGIP_FP32 || scatter != DOGIP_SCATTER_ATOMIC || c.hi || c.global_w ||
+      !c.keep32)
+    return false;
+  const int var = c.apply_variant_prec[DOGIP_FP32] >= 0 ? c.apply_variant_prec[DOGIP_FP32]
+                                                         : c.apply_variant;
+  return c.factorized || var == 1;  // the staged kernel carries the energy reduction
+}
+
+void launch_apply_energy(Ctx& c, const float* u, float* w, cudaStream_t s, SolveWork& wk,
+                         int mode) {
+  const CGEnergy en{wk.partial, wk.counter, wk.scal, wk.flags, mode};
+  c.energy = &en;  // copied into the kernel arguments by the staged launcher
+  int k = 0;
+  try {
+    k = apply_dispatch(c, u, w, 1, DOGIP_FP32, true, 0, c.E, s, wk.flags);
+  } catch (...) {
+    c.energy = nullptr;
+    throw;
+  }
+  c.energy = nullptr;
+  if (k != 2) fail(DOGIP_EUNSUPPORTED, "the fused p.Kp reduction needs the staged apply kernel");
+  cuda_check(cudaGetLastError(), "apply kernel launch");
+  c.launches += 1;
+}
+
 void launch_apply(Ctx& c, const void* u, void* y, int R, int prec, int scatter, cudaStream_t s,
                   const int* skip, bool add) {
   const size_t es = prec == DOGIP_FP64 ? sizeof(double) : sizeof(float);
   if (prec == DOGIP_TF32) {
-    if (R != 1 || scatter != DOGIP_SCATTER_ATOMIC || !apply_tc_available(c.d, c.p, c.form) ||
-        c.global_w || c.factorized)
+    if ((R != 1 && R % 16 != 0) || scatter != DOGIP_SCATTER_ATOMIC ||
+        !apply_tc_available(c.d, c.p, c.form) || c.global_w || c.factorized)
       fail(DOGIP_EUNSUPPORTED,
-           "no tensor-core apply for this request (one right-hand side, atomic scatter, "
-           "element-wise A_T, and an instance for this dimension, order and form)");
+           "no tensor-core apply for this request (1 or a multiple of 16 right-hand sides, "
+           "atomic scatter, element-wise A_T, and an instance for this dimension, order and "
+           "form)");
     if (!add) cuda_check(cudaMemsetAsync(y, 0, es * c.n * R, s), "memset y");
-    if (!apply_tc(c, u, y, s, skip, add))
+    if (!apply_tc(c, u, y, s, skip, add, R))
       fail(DOGIP_EUNSUPPORTED, "no tensor-core apply for this context");
     c.launches += 1;
     cuda_check(cudaGetLastError(), "tensor-core apply launch");

@@ -281,6 +281,84 @@ __global__ void __launch_bounds__(kRedThreads) k_pupdate(T* __restrict__ p, cons
   }
 }
 
+// Chronopoulos-Gear CG step (one right-hand side, FP32 vectors) before the apply:
+//   p = u + beta p,  s = w + beta s  (first step: p = u, s = w),
+//   x += alpha p,  r -= alpha s,  u = Dinv r,  w = 0 (for the scatter-add apply),
+//   gamma = r.u, rr = r.r; the last block sets beta = gamma / gamma_old and tests
+//   convergence.  With s = K p kept by recurrence, one reduction phase (here) and the
+//   energy reduction of the apply replace the three of the standard recurrence.
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_cgcg(T* __restrict__ x, T* __restrict__ r,
+                                                      T* __restrict__ u, T* __restrict__ w,
+                                                      T* __restrict__ p, T* __restrict__ sv,
+                                                      const T* __restrict__ dinv, int64_t N,
+                                                      Red rd) {
+  if (rd.flags[0]) return;
+  const CGScal& s0 = rd.scal[0];
+  const bool first = s0.iters == 0;
+  const T al = (T)s0.alpha, be = first ? T(0) : (T)s0.beta;
+  T a0 = T(0), a1 = T(0);
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  auto step = [&](T& xv, T& rv, T& uv, T& wv, T& pv, T& svv, T dv) {
+    pv = first ? uv : uv + be * pv;
+    svv = first ? wv : wv + be * svv;
+    xv += al * pv;
+    rv -= al * svv;
+    uv = dv * rv;
+    wv = T(0);
+    a0 += rv * uv;
+    a1 += rv * rv;
+  };
+  int64_t head = 0;
+  if (aligned16(x) && aligned16(r) && aligned16(u) && aligned16(w) && aligned16(p) &&
+      aligned16(sv) && aligned16(dinv)) {
+    using V = Vec16<T>;
+    const int64_t nv = N / V::L;
+    V *x4 = (V*)x, *r4 = (V*)r, *u4 = (V*)u, *w4 = (V*)w, *p4 = (V*)p, *s4 = (V*)sv;
+    const V* d4 = (const V*)dinv;
+    for (int64_t k = t0; k < nv; k += stride) {
+      V xv = x4[k], rv = r4[k], uv = u4[k], wv = w4[k], pv = p4[k], svv = s4[k];
+      const V dv = d4[k];
+#pragma unroll
+      for (int e = 0; e < V::L; ++e) step(xv.v[e], rv.v[e], uv.v[e], wv.v[e], pv.v[e], svv.v[e], dv.v[e]);
+      x4[k] = xv;
+      r4[k] = rv;
+      u4[k] = uv;
+      w4[k] = wv;
+      p4[k] = pv;
+      s4[k] = svv;
+    }
+    head = nv * V::L;
+  }
+  for (int64_t i = head + t0; i < N; i += stride) {
+    T xv = x[i], rv = r[i], uv = u[i], wv = w[i], pv = p[i], svv = sv[i];
+    step(xv, rv, uv, wv, pv, svv, dinv[i]);
+    x[i] = xv;
+    r[i] = rv;
+    u[i] = uv;
+    w[i] = wv;
+    p[i] = pv;
+    sv[i] = svv;
+  }
+  double acc[2] = {(double)a0, (double)a1};
+  __shared__ double tot[2];
+  if (!grid_reduce<1, 2>(rd, acc, tot)) return;
+  if (threadIdx.x == 0) {
+    CGScal& s = rd.scal[0];
+    if (!s.done) {
+      const double gam = tot[0], rr = tot[1];
+      s.beta = gam / s.rho;
+      s.rho_prev = s.rho;
+      s.rho = gam;
+      s.rr = rr;
+      s.iters += 1;
+      if (sqrt(rr) <= s.tol * s.r0) s.done = 1;
+    }
+    set_all_done(rd, 1);
+  }
+}
+
 // Start of a PCG run from the residual r: p = Dinv r, rho = r.p, r0.
 template <typename T, int R>
 __global__ void __launch_bounds__(kRedThreads) k_init(const T* __restrict__ r, T* __restrict__ p,
@@ -475,12 +553,22 @@ void vec_alloc(SolveWork& w, int64_t n, int R) {
   w.n = n;
 }
 
+void vec_alloc_cgcg(SolveWork& w) {
+  if (w.pc32 != nullptr) return;
+  const size_t N = (size_t)w.n * w.R;
+  if (cudaMalloc((void**)&w.pc32, N * 4) != cudaSuccess ||
+      cudaMalloc((void**)&w.sc32, N * 4) != cudaSuccess) {
+    cudaGetLastError();
+    fail(DOGIP_ENOMEM, "device allocation of solver workspace failed");
+  }
+}
+
 void vec_free(SolveWork& w) {
   if (w.graph) cudaGraphExecDestroy(w.graph);
   w.graph = nullptr;
   for (void* p : {(void*)w.x64, (void*)w.r64, (void*)w.p64, (void*)w.q64, (void*)w.x32,
                   (void*)w.r32, (void*)w.p32, (void*)w.q32, (void*)w.partial, (void*)w.counter,
-                  (void*)w.scal, (void*)w.flags})
+                  (void*)w.scal, (void*)w.flags, (void*)w.pc32, (void*)w.sc32})
     if (p) cudaFree(p);
   if (w.h_flags) cudaFreeHost(w.h_flags);
   if (w.h_scal) cudaFreeHost(w.h_scal);
@@ -524,7 +612,7 @@ int vec_init64(SolveWork& w, const double* dinv, double tol, cudaStream_t st) {
 }
 
 int vec_cg_step(SolveWork& w, int prec, double* x64, const void* dinv, double delta,
-                cudaStream_t st, bool zero_q) {
+                cudaStream_t st, bool zero_q, bool with_pq) {
   const int64_t N = w.n * w.R;
   Red rd = red_of(w);
   const unsigned nb = red_blocks(N);
@@ -540,7 +628,7 @@ int vec_cg_step(SolveWork& w, int prec, double* x64, const void* dinv, double de
   } else {
     const float* di = (const float*)dinv;
 #define CALL(RR)                                                                           \
-  k_pq<float, RR><<<nb, kRedThreads, 0, st>>>(w.p32, w.q32, N, rd);                        \
+  if (with_pq) k_pq<float, RR><<<nb, kRedThreads, 0, st>>>(w.p32, w.q32, N, rd);           \
   k_update<float, RR><<<nb, kRedThreads, 0, st>>>(w.x32, w.r32, w.p32, w.q32, di, N, delta, rd); \
   k_pupdate<float, RR><<<nb, kRedThreads, 0, st>>>(w.p32, w.r32, di, N, w.scal, w.flags,   \
                                                     zero_q ? w.q32 : nullptr)
@@ -548,7 +636,7 @@ int vec_cg_step(SolveWork& w, int prec, double* x64, const void* dinv, double de
 #undef CALL
   }
   cuda_check(cudaGetLastError(), "cg step kernels");
-  return 3;
+  return with_pq || prec == DOGIP_FP64 ? 3 : 2;
 }
 
 int vec_rel_init(SolveWork& w, const float* dinv, double tol, cudaStream_t st) {
@@ -592,6 +680,15 @@ int vec_correct(SolveWork& w, double* x64, cudaStream_t st) {
   DOGIP_R_SWITCH(w.R, CALL);
 #undef CALL
   cuda_check(cudaGetLastError(), "correct kernel");
+  return 1;
+}
+
+int vec_cgcg_step(SolveWork& w, const float* dinv, cudaStream_t st) {
+  const int64_t N = w.n * w.R;
+  Red rd = red_of(w);
+  k_cgcg<float><<<red_blocks(N), kRedThreads, 0, st>>>(w.x32, w.r32, w.p32, w.q32, w.pc32,
+                                                       w.sc32, dinv, N, rd);
+  cuda_check(cudaGetLastError(), "cg step kernel");
   return 1;
 }
 

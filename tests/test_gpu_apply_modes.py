@@ -65,7 +65,7 @@ def test_apply_add(B, d, p, form, variant, monkeypatch):
     ctx.check()
 
 
-@pytest.mark.parametrize("R", [1, 4])
+@pytest.mark.parametrize("R", [1, 4, 16])
 def test_apply_add_colour_and_multi_rhs(B, R):
     ctx, P = make(B, 2, 2, "elliptic", 12, scatter="colour")
     u = inputs.rhs_normal(P.n, R, seed=43)
@@ -75,6 +75,14 @@ def test_apply_add_colour_and_multi_rhs(B, R):
         ctx.apply_add(torch.tensor(u if R > 1 else u[:, 0], device="cuda"), y, scatter=scat)
         got = y.cpu().numpy().reshape(P.n, R)
         assert np.all(np.abs(got - (P.apply(u) + y0)) <= TOL64 * (P.apply_abs(u) + np.abs(y0)))
+    # FP32 atomic (16 right-hand sides: the 8-cell x 16-rhs warp units)
+    u32, y32 = u.astype(np.float32), y0.astype(np.float32)
+    y = torch.tensor(y32 if R > 1 else y32[:, 0], device="cuda")
+    ctx.apply_add(torch.tensor(u32 if R > 1 else u32[:, 0], device="cuda"), y, prec="fp32",
+                  scatter="atomic")
+    got = y.cpu().numpy().astype(np.float64).reshape(P.n, R)
+    u64 = u32.astype(np.float64)
+    assert np.all(np.abs(got - (P.apply(u64) + y32)) <= TOL32 * (P.apply_abs(u64) + np.abs(y32)))
 
 
 TF32_CASES = [(2, p, "elliptic") for p in (1, 2, 3, 4)] + [(2, 3, "projection"), (3, 2, "elliptic"),
@@ -93,10 +101,32 @@ def test_apply_tf32(B, d, p, form):
     ctx.check()
 
 
+TF32_MULTI = [(3, 2, "elliptic", 16), (3, 2, "projection", 32), (2, 3, "elliptic", 16),
+              (2, 1, "projection", 16)]
+
+
+@pytest.mark.parametrize("d,p,form,R", TF32_MULTI,
+                         ids=[f"{d}D-P{p}-{f}-R{R}" for d, p, f, R in TF32_MULTI])
+def test_apply_tf32_multi_rhs(B, d, p, form, R):
+    """Several right-hand sides on the tensor cores: MMA tiles of 8 cells x 16
+    right-hand sides (apply and apply_add), against the oracle, FP32 bound."""
+    ctx, P = make(B, d, p, form, NSMALL[d])
+    u32 = inputs.rhs_normal(P.n, R, seed=46).astype(np.float32)
+    u64 = u32.astype(np.float64)
+    y = ctx.apply(torch.tensor(u32, device="cuda"), prec="tf32").cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(y - P.apply(u64)) <= TOL32 * P.apply_abs(u64))
+    y0 = inputs.rhs_normal(P.n, R, seed=47).astype(np.float32)
+    yg = torch.tensor(y0, device="cuda")
+    ctx.apply_add(torch.tensor(u32, device="cuda"), yg, prec="tf32")
+    got = yg.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(got - (P.apply(u64) + y0)) <= TOL32 * (P.apply_abs(u64) + np.abs(y0)))
+    ctx.check()
+
+
 def test_tf32_unsupported_requests(B):
     ctx, P = make(B, 2, 2, "elliptic", 8)
     u = torch.zeros((P.n, 4), dtype=torch.float32, device="cuda")
-    with pytest.raises(B.DogipError) as e:  # one right-hand side only
+    with pytest.raises(B.DogipError) as e:  # 1 or a multiple of 16 right-hand sides
         ctx.apply(u, prec="tf32")
     assert e.value.code == B.EUNSUPPORTED
     c8, P8 = make(B, 2, 8, "elliptic", 3)  # no tensor-core instance at 2D P8 elliptic

@@ -1,7 +1,9 @@
-"""Device-side failure detection without a GPU fault: the staged apply's bounded
-mbarrier wait runs out on a copy that is never issued (a test hook, the analogue of
-a flag that nothing sets); the kernel drains its other copies, raises its error word
-and returns; dogip_check reports DOGIP_ETIMEOUT and the CUDA context stays usable."""
+"""Device-side failure detection without a GPU fault: a bounded mbarrier wait runs
+out on a copy that is never issued (a test hook, the analogue of a flag that nothing
+sets), in the staged apply and in the tensor-core apply (one and 16 right-hand sides
+per cell); the kernel drains its other copies, raises its error word and returns
+(the tensor-core kernel after its warpgroups leave together and free their tensor
+memory); dogip_check reports DOGIP_ETIMEOUT and the CUDA context stays usable."""
 
 import os
 import subprocess
@@ -19,8 +21,9 @@ from paper_1710_09913_gb300 import binding as B, inputs
 coords, cells = inputs.lattice_mesh(2, 64, 0.2, seed=3)
 A = inputs.coef_tensor_lognormal(len(cells), 2, 1.0, seed=3)
 ctx = B.Context(coords, cells, 2, "elliptic", A)
-u = torch.randn(ctx.n, dtype=torch.float32, device="cuda")
-ctx.apply(u, prec="fp32")
+R = int(os.environ.get("DOGIP_CHILD_R", "1"))
+u = torch.randn(ctx.n, R, dtype=torch.float32, device="cuda").squeeze(1)
+ctx.apply(u, prec=os.environ.get("DOGIP_CHILD_PREC", "fp32"))
 try:
     ctx.check()
     print("NO-TIMEOUT")
@@ -35,12 +38,15 @@ print("USABLE", np.isfinite(y).all())
 """
 
 
-def test_apply_wait_timeout_is_reported():
+@pytest.mark.parametrize("prec,R", [("fp32", 1), ("tf32", 1), ("tf32", 16)],
+                         ids=["staged", "tensor-cores", "tensor-cores-16rhs"])
+def test_apply_wait_timeout_is_reported(prec, R):
     from paper_1710_09913_gb300 import build
     build.build()
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     env = dict(os.environ, DOGIP_ROOT=root, DOGIP_TEST_SKIP_CHUNK="0",
-               DOGIP_TEST_WAIT_CYCLES="2000000")  # ~1 ms per bounded wait
+               DOGIP_TEST_WAIT_CYCLES="2000000",  # ~1 ms per bounded wait
+               DOGIP_CHILD_PREC=prec, DOGIP_CHILD_R=str(R))
     out = subprocess.run([sys.executable, "-c", CHILD], env=env, capture_output=True, text=True,
                          timeout=300)
     assert out.returncode == 0, out.stderr[-2000:]
