@@ -336,6 +336,25 @@ def only_solve(args):
     return 0
 
 
+def only_cube(args):
+    """Profiling mode: the 3D workload (64^3 cubes x 6 tetrahedra, P2, inclusions) and
+    --reps applies of 16 right-hand sides in precision --prec (fp32 or tf32)."""
+    import torch
+    from paper_1710_09913_gb300 import build
+    build.build()
+    from paper_1710_09913_gb300 import binding as B
+    from paper_1710_09913_gb300 import inputs
+    c3, t3 = inputs.lattice_mesh(3, 64)
+    m3 = inputs.coef_inclusions(inputs.centroids(c3, t3), 200, 0.03, 0.08, seed=3)
+    c = B.Context(c3, t3, 2, "elliptic", m3)
+    u = torch.randn(c.n, 16, dtype=torch.float32, device="cuda")
+    y = torch.empty_like(u)
+    for _ in range(args.reps):
+        c.apply(u, y, prec=args.prec)
+    torch.cuda.synchronize()
+    return 0
+
+
 def only_apply(args):
     """Profiling mode: build the workload at order P and run the apply alone."""
     import torch
@@ -380,11 +399,15 @@ def main():
                     help="profiling mode: only run --reps applies of order P (no JSON line)")
     ap.add_argument("--only-solve", type=int, default=0, metavar="P",
                     help="profiling mode: one mixed solve of order P (no JSON line)")
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--only-cube", action="store_true",
+                    help="profiling mode: --reps 16-rhs applies of the 3D P2 workload (no JSON line)")
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "tf32"])
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.only_cube:
+        return only_cube(args)
     if args.only_apply:
         return only_apply(args)
     if args.only_solve:

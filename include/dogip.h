@@ -43,6 +43,9 @@
  *    (default), 0 one thread per cell; the orders above the compiled tables have
  *    one CUDA-core kernel, taken for every value but 3).
  *  - DOGIP_TUNE_CACHE: file of autotuner choices (see dogip_autotune).
+ *  - DOGIP_GRAPH_PDL: 1 (default) launches the kernels of a captured CG chunk as
+ *    programmatic dependents of each other where they are written for it (the next
+ *    kernel starts while the previous one drains); 0 keeps full serialisation.
  *  - DOGIP_TEST_WAIT_CYCLES, DOGIP_TEST_SKIP_CHUNK: test hooks of the device-side
  *    failure path (a shorter bound on the kernels' waits, and one chunk of the
  *    staged apply whose copy is never issued, so that its bounded wait expires).

@@ -30,11 +30,11 @@ struct TmaLaunch {
 
 // Kernel attributes and residency of one instance, set once (thread-safe static);
 // first called from context set-up, outside any stream capture.
-template <int D, int P, int FORM, typename T, bool FACT>
+template <int D, int P, int FORM, typename T, bool FACT, bool EN = false>
 const TmaLaunch& tma_launch() {
   static const TmaLaunch info = [] {
     using Cfg = TmaCfg<D, P, FORM, T, FACT>;
-    auto kern = k_apply_tma<D, P, FORM, T, FACT>;
+    auto kern = k_apply_tma<D, P, FORM, T, FACT, EN>;
     TmaLaunch t;
     cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM),
                "apply smem attribute");
@@ -53,7 +53,9 @@ template <int D, int P, int FORM, typename T, bool FACT>
 void run_apply_tma(const T* A, const Ctx& c, const void* u, void* y, int R, cudaStream_t s,
                    const int* skip, bool add) {
   using Cfg = TmaCfg<D, P, FORM, T, FACT>;
-  const TmaLaunch& L = tma_launch<D, P, FORM, T, FACT>();
+  constexpr bool F32 = std::is_same<T, float>::value;
+  const bool en = F32 && R == 1 && c.energy != nullptr;
+  const TmaLaunch& L = en ? tma_launch<D, P, FORM, T, FACT, F32>() : tma_launch<D, P, FORM, T, FACT>();
   const int blocks_per_sm = L.blocks_per_sm, num_sms = L.num_sms;
   const int64_t ntiles = (c.E + kTile - 1) / kTile;
   const int64_t nchunks = (ntiles + Cfg::TPC - 1) / Cfg::TPC;
@@ -63,9 +65,15 @@ void run_apply_tma(const T* A, const Ctx& c, const void* u, void* y, int R, cuda
                   ((uintptr_t)y & 15u) == 0;
   TmaArgs<T> a{A, c.d_conn, (const T*)u, (T*)y, c.E, ntiles, nchunks, R, skip, c.d_kerr,
                 c.d_bnd, c.dirichlet ? c.nbnd : 0, c.wait_budget, c.test_skip_chunk, r4 ? 1 : 0,
-                stream_evict_first(c, sizeof(T), FACT ? Cfg::NS : Cfg::W * Cfg::NS), add ? 1 : 0,
-                sizeof(T) == 4 && R == 1 && c.energy != nullptr ? *c.energy : CGEnergy{}};
-  k_apply_tma<D, P, FORM, T, FACT><<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
+                stream_evict_first(c, sizeof(T), FACT ? Cfg::NS : Cfg::W * Cfg::NS), add ? 1 : 0};
+  const CGEnergy e = en ? *c.energy : CGEnergy{};
+  if (en) {
+    pdl_mark((const void*)k_apply_tma<D, P, FORM, T, FACT, F32>);
+    k_apply_tma<D, P, FORM, T, FACT, F32><<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, s>>>(a, e);
+  } else {
+    pdl_mark((const void*)k_apply_tma<D, P, FORM, T, FACT>);
+    k_apply_tma<D, P, FORM, T, FACT><<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, s>>>(a, e);
+  }
 }
 
 // Self-feeding warps variant (one right-hand side, atomic scatter, whole range).
@@ -113,9 +121,11 @@ int run_apply(const Ctx& c, const void* u, void* y, int R, int prec, bool atomic
     if (c.factorized) {
       tma_launch<D, P, FORM, double, true>();
       tma_launch<D, P, FORM, float, true>();
+      tma_launch<D, P, FORM, float, true, true>();
     } else {
       if constexpr (ok64) tma_launch<D, P, FORM, double, false>();
       if constexpr (ok32) tma_launch<D, P, FORM, float, false>();
+      if constexpr (ok32) tma_launch<D, P, FORM, float, false, true>();
       if constexpr (SfwCfg<D, P, FORM, double>::OK) sfw_launch<D, P, FORM, double>();
       if constexpr (SfwCfg<D, P, FORM, float>::OK) sfw_launch<D, P, FORM, float>();
       if (c.keep32) apply_tc(c, nullptr, nullptr, nullptr, nullptr);

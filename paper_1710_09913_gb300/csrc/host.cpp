@@ -11,6 +11,7 @@
 #include <tuple>
 #include <numeric>
 #include <string>
+#include <unordered_set>
 #include <vector>
 
 #include "internal.h"
@@ -453,6 +454,7 @@ Ctx* setup(const dogip_mesh* m, int p, int form, int coef_kind, const double* co
       c->l2_bytes = l2;
     }
     if (const char* v = std::getenv("DOGIP_APPLY_VARIANT")) c->apply_variant = std::atoi(v);
+    if (const char* v = std::getenv("DOGIP_GRAPH_PDL")) c->graph_pdl = std::atoi(v) != 0;
     // Test hooks for the device-side failure path: a shorter wait budget, and one
     // chunk of the staged apply whose copy is never issued, so that its bounded
     // wait expires (nothing faults or hangs; the kernel reports and returns).
@@ -612,6 +614,38 @@ void set_coef_inclusions(Ctx& c, int nb, const double* centres, const double* ra
 
 bool r_ok(int R) { return R == 1 || R == 2 || R == 4 || R == 8 || R == 16 || R == 32; }
 
+// Turn every edge of g between two marked kernel nodes into a programmatic dependency
+// (the downstream kernel is launched once all blocks of the upstream one have started,
+// and waits inside for its completion); returns the number of edges changed.
+int make_programmatic_edges(cudaGraph_t g) {
+  size_t ne = 0;
+  cuda_check(cudaGraphGetEdges(g, nullptr, nullptr, nullptr, &ne), "graph edges");
+  if (ne == 0) return 0;
+  std::vector<cudaGraphNode_t> from(ne), to(ne);
+  std::vector<cudaGraphEdgeData> ed(ne);
+  cuda_check(cudaGraphGetEdges(g, from.data(), to.data(), ed.data(), &ne), "graph edges");
+  auto marked_kernel = [](cudaGraphNode_t nd) {
+    cudaGraphNodeType ty;
+    cuda_check(cudaGraphNodeGetType(nd, &ty), "graph node type");
+    if (ty != cudaGraphNodeTypeKernel) return false;
+    cudaKernelNodeParams kp{};
+    cuda_check(cudaGraphKernelNodeGetParams(nd, &kp), "kernel node params");
+    return pdl_marked(kp.func);
+  };
+  int changed = 0;
+  for (size_t i = 0; i < ne; ++i) {
+    if (ed[i].type != cudaGraphDependencyTypeDefault || ed[i].from_port != 0) continue;
+    if (!marked_kernel(from[i]) || !marked_kernel(to[i])) continue;
+    cuda_check(cudaGraphRemoveDependencies(g, &from[i], &to[i], &ed[i], 1), "remove edge");
+    cudaGraphEdgeData pe{};
+    pe.from_port = cudaGraphKernelNodePortProgrammatic;
+    pe.type = cudaGraphDependencyTypeProgrammatic;
+    cuda_check(cudaGraphAddDependencies(g, &from[i], &to[i], &pe, 1), "programmatic edge");
+    ++changed;
+  }
+  return changed;
+}
+
 // One chunk of `k` CG iterations on the solver stream, captured once as a CUDA
 // graph and replayed; ends with a copy of the flags and scalars to pinned host.
 // rec (FP32, one right-hand side): 0 the standard recurrence in four kernels (apply,
@@ -661,6 +695,12 @@ void run_chunk(Ctx& c, int prec, int scatter, double* x64, int k, double delta, 
     c.launches = launches_before;
     cudaGraph_t g = nullptr;
     cuda_check(cudaStreamEndCapture(s, &g), "end capture");
+    try {
+      if (c.graph_pdl) make_programmatic_edges(g);
+    } catch (...) {
+      cudaGraphDestroy(g);
+      throw;
+    }
     size_t nn = 0;
     cuda_check(cudaGraphGetNodes(g, nullptr, &nn), "graph nodes");
     std::vector<cudaGraphNode_t> nodes(nn);
@@ -1276,6 +1316,19 @@ int guarded(F&& f) {
 }
 
 }  // namespace
+std::mutex g_pdl_mutex;
+std::unordered_set<const void*> g_pdl_kernels;
+
+void pdl_mark(const void* kernel) {
+  std::lock_guard<std::mutex> lock(g_pdl_mutex);
+  g_pdl_kernels.insert(kernel);
+}
+
+bool pdl_marked(const void* kernel) {
+  std::lock_guard<std::mutex> lock(g_pdl_mutex);
+  return g_pdl_kernels.count(kernel) != 0;
+}
+
 }  // namespace dogip
 
 using dogip::Ctx;

@@ -134,6 +134,7 @@ struct dogip_ctx {
   int64_t l2_bytes = 0;        // L2 size of the device: streams larger than half of it
                                // are copied with the L2 evict-first policy
   int64_t test_skip_chunk = -1;  // test hook (see DOGIP_TEST_SKIP_CHUNK)
+  bool graph_pdl = true;          // programmatic edges in captured CG chunks (DOGIP_GRAPH_PDL)
   // set around one launch by launch_apply_energy (host, one thread per context): the
   // staged kernel then also reduces (w, u) and sets alpha
   mutable const dogip::CGEnergy* energy = nullptr;
@@ -224,6 +225,15 @@ void launch_dirichlet_copy(const Ctx& c, const void* u, void* y, int R, int prec
 void launch_diag_finish(Ctx& c, cudaStream_t s);
 // One-time kernel attributes of the apply instances of this context (host only).
 void prepare_apply(Ctx& c);
+
+// Programmatic dependent launch inside captured CG chunks: kernels whose first act
+// is griddepcontrol.launch_dependents + griddepcontrol.wait (they touch nothing of the
+// previous kernel before the wait) are marked by their launchers; run_chunk turns the
+// graph edges between two marked kernels into programmatic ones, so the next kernel
+// is launched while the previous one drains.  Edges to or from any other node keep
+// full serialisation.
+void pdl_mark(const void* kernel);
+bool pdl_marked(const void* kernel);
 
 // Static table access for the host (dogip_get_tables, info).
 bool table_info(int d, int p, int form, int* NB, int* W, int* V, long long* nnz,

@@ -209,6 +209,13 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> a) {
 // is bounded by a clock budget; on expiry the kernel raises an error flag, drains its
 // copies in flight (bounded again) and returns.
 
+// Start of a kernel that may run as the programmatic dependent of the previous kernel
+// in a CUDA graph: allow the next kernel to be launched, then wait until the previous
+// grid has completed and its memory is visible (a no-op without such a dependency).
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -356,8 +363,11 @@ struct TmaArgs {
   int r4;                   // 1: FP32, R % 4 == 0, u and y 16-byte aligned
   int evict_first;          // 1: A_T and conn copies carry the L2 evict-first policy
   int add;                  // 1: y += K u (Dirichlet rows y_b += u_b); 0: y_b = u_b
-  CGEnergy en;              // en.partial != null (FP32, R = 1): also reduce (y, u), set alpha
-};
+};  // 128 bytes: keep it so (a larger argument block changed the register allocation of
+    // the staged kernel and slowed it by a tenth; the energy target is a parameter of
+    // its own)
+static_assert(sizeof(TmaArgs<float>) <= 128 && sizeof(TmaArgs<double>) <= 128,
+              "staged-apply argument block above 128 bytes");
 
 // End of an apply with the energy reduction (one right-hand side): the CTA's
 // (y, u) = sum of its cells' u_T . Y_T and Dirichlet rows u_b^2 goes to
@@ -414,9 +424,11 @@ __device__ __forceinline__ void cg_energy_finish(const CGEnergy& en, double e) {
 }
 
 
-template <int D, int P, int FORM, typename T, bool FACT>
+// EN: the instance with the energy reduction into en (FP32, one right-hand side) -- a
+// separate instance, so that the plain apply is compiled without it.
+template <int D, int P, int FORM, typename T, bool FACT, bool EN = false>
 __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T, FACT>::THREADS)
-    k_apply_tma(TmaArgs<T> a) {
+    k_apply_tma(TmaArgs<T> a, CGEnergy en) {
   using C = TmaCfg<D, P, FORM, T, FACT>;
   static_assert(C::OK, "stage does not fit in shared memory");
   using TB = typename C::TB;
@@ -432,6 +444,7 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T, FACT>::THREADS)
   uint64_t* full = (uint64_t*)(pro_buf + C::PRO);            // chunk landed (tx count)
   uint64_t* empty = full + C::S;                             // all consumer warps done with it
   uint64_t* pro = empty + C::S;                              // prologue landed
+  pdl_enter();
   if (a.skip != nullptr && *a.skip) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t G = gridDim.x, k0 = blockIdx.x;
@@ -604,15 +617,13 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T, FACT>::THREADS)
               static_for<V>([&](auto lc) { Y[decltype(qc)::value][decltype(lc)::value] = T(0); });
             });
           }
-          if constexpr (RW == 1 && std::is_same<T, float>::value) {
-            if (a.en.partial != nullptr) {  // this cell's energy u_T . Y_T
-              float el = 0.0f;
-              static_for<V>([&](auto lc) {
-                constexpr int l = decltype(lc)::value;
-                el = fmaf(ul[0][l], Y[0][l], el);
-              });
-              e_acc += (double)el;
-            }
+          if constexpr (EN && RW == 1) {  // this cell's energy u_T . Y_T
+            float el = 0.0f;
+            static_for<V>([&](auto lc) {
+              constexpr int l = decltype(lc)::value;
+              el = fmaf(ul[0][l], Y[0][l], el);
+            });
+            e_acc += (double)el;
           }
           scatter_pairs<V, RW, T>(c, Y, lane, a.y, a.R, r);
           if constexpr (PFW) {
@@ -632,7 +643,7 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T, FACT>::THREADS)
       }
       if (failed && lane == 0) atomicOr(a.err, 1);
     };
-    if constexpr (Q4) {
+    if constexpr (Q4 && !EN) {
       if (a.r4) consume(std::integral_constant<int, 4>{});
       else consume(std::integral_constant<int, 1>{});
     } else {
@@ -646,10 +657,9 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T, FACT>::THREADS)
     const int64_t idx = (int64_t)a.bnd[t / a.R] * a.R + (t % a.R);
     const T ub = a.u[idx];
     a.y[idx] = a.add ? a.y[idx] + ub : ub;
-    if constexpr (std::is_same<T, float>::value) e_acc += (double)ub * (double)ub;
+    if constexpr (EN) e_acc += (double)ub * (double)ub;
   }
-  if constexpr (std::is_same<T, float>::value)
-    if (a.en.partial != nullptr) cg_energy_finish(a.en, e_acc);
+  if constexpr (EN) cg_energy_finish(en, e_acc);
 }
 
 // ------------------------------------------------- self-feeding warps apply

@@ -16,6 +16,11 @@ namespace dogip {
 
 namespace {
 
+// See kernels.cuh: first act of a kernel that may be a programmatic dependent.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 constexpr int kNV = 2;  // values reduced per rhs
 
 // 16-byte vector of T (4 floats or 2 doubles) for the one-rhs streaming loops.
@@ -126,6 +131,7 @@ unsigned red_blocks(int64_t N) {
 template <typename T, int R>
 __global__ void __launch_bounds__(kRedThreads) k_pq(const T* __restrict__ p, const T* __restrict__ q,
                                                     int64_t N, Red rd) {
+  pdl_enter();
   if (rd.flags[0]) return;
   double acc[1] = {0.0};
   T a = T(0);
@@ -176,6 +182,7 @@ __global__ void __launch_bounds__(kRedThreads) k_update(T* __restrict__ x, T* __
                                                         const T* __restrict__ q,
                                                         const T* __restrict__ dinv, int64_t N,
                                                         double delta, Red rd) {
+  pdl_enter();
   if (rd.flags[0]) return;
   const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const T al = (T)rd.scal[t0 % R].alpha;
@@ -243,6 +250,7 @@ __global__ void __launch_bounds__(kRedThreads) k_pupdate(T* __restrict__ p, cons
                                                          const T* __restrict__ dinv, int64_t N,
                                                          const CGScal* scal, const int* flags,
                                                          T* __restrict__ qzero) {
+  pdl_enter();
   if (flags[0]) return;
   const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -293,6 +301,7 @@ __global__ void __launch_bounds__(kRedThreads) k_cgcg(T* __restrict__ x, T* __re
                                                       T* __restrict__ p, T* __restrict__ sv,
                                                       const T* __restrict__ dinv, int64_t N,
                                                       Red rd) {
+  pdl_enter();
   if (rd.flags[0]) return;
   const CGScal& s0 = rd.scal[0];
   const bool first = s0.iters == 0;
@@ -619,6 +628,9 @@ int vec_cg_step(SolveWork& w, int prec, double* x64, const void* dinv, double de
   if (prec == DOGIP_FP64) {
     const double* di = (const double*)dinv;
 #define CALL(RR)                                                                           \
+  pdl_mark((const void*)k_pq<double, RR>);                                                 \
+  pdl_mark((const void*)k_update<double, RR>);                                             \
+  pdl_mark((const void*)k_pupdate<double, RR>);                                            \
   k_pq<double, RR><<<nb, kRedThreads, 0, st>>>(w.p64, w.q64, N, rd);                       \
   k_update<double, RR><<<nb, kRedThreads, 0, st>>>(x64, w.r64, w.p64, w.q64, di, N, delta, rd); \
   k_pupdate<double, RR><<<nb, kRedThreads, 0, st>>>(w.p64, w.r64, di, N, w.scal, w.flags,  \
@@ -628,6 +640,9 @@ int vec_cg_step(SolveWork& w, int prec, double* x64, const void* dinv, double de
   } else {
     const float* di = (const float*)dinv;
 #define CALL(RR)                                                                           \
+  pdl_mark((const void*)k_pq<float, RR>);                                                  \
+  pdl_mark((const void*)k_update<float, RR>);                                              \
+  pdl_mark((const void*)k_pupdate<float, RR>);                                             \
   if (with_pq) k_pq<float, RR><<<nb, kRedThreads, 0, st>>>(w.p32, w.q32, N, rd);           \
   k_update<float, RR><<<nb, kRedThreads, 0, st>>>(w.x32, w.r32, w.p32, w.q32, di, N, delta, rd); \
   k_pupdate<float, RR><<<nb, kRedThreads, 0, st>>>(w.p32, w.r32, di, N, w.scal, w.flags,   \
@@ -686,6 +701,7 @@ int vec_correct(SolveWork& w, double* x64, cudaStream_t st) {
 int vec_cgcg_step(SolveWork& w, const float* dinv, cudaStream_t st) {
   const int64_t N = w.n * w.R;
   Red rd = red_of(w);
+  pdl_mark((const void*)k_cgcg<float>);
   k_cgcg<float><<<red_blocks(N), kRedThreads, 0, st>>>(w.x32, w.r32, w.p32, w.q32, w.pc32,
                                                        w.sc32, dinv, N, rd);
   cuda_check(cudaGetLastError(), "cg step kernel");
