@@ -340,14 +340,15 @@ typedef struct {
                          nrhs 1 or a multiple of 16, atomic scatter, else
                          DOGIP_EUNSUPPORTED)                                   */
   int inner_recurrence; /* MIXED inner FP32 PCG: 0 (default) the standard
-                         Hestenes-Stiefel recurrence, with (p, K p) reduced from
-                         the element energies p_T . (K_T p_T) inside the apply
-                         where that kernel is the staged one (nrhs 1, FP32,
-                         atomic scatter: 3 kernels an iteration), else with a
-                         separate p.q kernel (4); 1 always the separate kernel;
-                         2 the single-reduction recurrence of Chronopoulos and
-                         Gear (2 kernels: s = K p by recurrence; more FP32
-                         iterations; EUNSUPPORTED where it does not apply)    */
+                         Hestenes-Stiefel recurrence, 4 kernels an iteration
+                         (apply, p.q, x/r update, p update); 1 the same with
+                         (p, K p) reduced from the element energies
+                         p_T . (K_T p_T) inside the apply (3 kernels); 2 the
+                         single-reduction recurrence of Chronopoulos and Gear
+                         (2 kernels: s = K p by recurrence; more FP32
+                         iterations).  1 and 2 need nrhs 1, FP32, atomic
+                         scatter and the staged apply kernel (else
+                         EUNSUPPORTED); both measured slower than 0 on GB300  */
 } dogip_solve_opts;
 
 typedef struct {

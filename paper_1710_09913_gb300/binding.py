@@ -26,7 +26,7 @@ FORMS = {"projection": PROJECTION, "elliptic": ELLIPTIC}
 PRECS = {"fp64": FP64, "fp32": FP32, "tf32": TF32}
 SCATTERS = {"atomic": SCATTER_ATOMIC, "colour": SCATTER_COLOUR, None: -1}
 MODES = {"fp64": SOLVE_FP64, "mixed": SOLVE_MIXED, "mixed_reliable": SOLVE_MIXED_RELIABLE}
-RECURRENCES = {"auto": 0, "standard": 1, "single_reduction": 2}
+RECURRENCES = {"standard": 0, "fused_pq": 1, "single_reduction": 2}
 
 
 class DogipError(RuntimeError):

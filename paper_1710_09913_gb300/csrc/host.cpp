@@ -761,11 +761,11 @@ int solve(Ctx& c, const double* b, double* u, int R, const dogip_solve_opts* opt
     fail(DOGIP_EINVAL, "inner_recurrence must be 0, 1 or 2");
   // inner FP32 recurrence of the mixed mode (run_chunk's rec)
   const bool fusable = o.mode == DOGIP_SOLVE_MIXED && cgcg_eligible(c, R, ip, scatter);
-  const int rec = o.inner_recurrence == 2 ? 2 : (o.inner_recurrence == 0 && fusable ? 1 : 0);
-  if (o.mode == DOGIP_SOLVE_MIXED && rec == 2 && !fusable)
+  const int rec = o.mode == DOGIP_SOLVE_MIXED ? o.inner_recurrence : 0;
+  if (rec != 0 && !fusable)
     fail(DOGIP_EUNSUPPORTED,
-         "the single-reduction inner CG needs one right-hand side, FP32 inner applies, atomic "
-         "scatter and the staged apply kernel");
+         "the fused (p, K p) and single-reduction inner recurrences need one right-hand side, "
+         "FP32 inner applies, atomic scatter and the staged apply kernel");
   if (ip == DOGIP_TF32 && ((R != 1 && R % 16 != 0) || scatter != DOGIP_SCATTER_ATOMIC ||
                            c.global_w || c.factorized || !apply_tc_available(c.d, c.p, c.form)))
     fail(DOGIP_EUNSUPPORTED,

@@ -1,6 +1,6 @@
 """Inner recurrences of the mixed solve (GPU): the standard Hestenes-Stiefel PCG
-recurrence with (p, K p) reduced from the element energies inside the apply
-(default, three kernels per iteration) or by a separate kernel (four), and the
+recurrence (default, four kernels per iteration), the same with (p, K p) reduced
+from the element energies inside the apply (three kernels), and the
 single-reduction recurrence of Chronopoulos and Gear (two kernels: s = K p kept by
 recurrence, (K u, u) from the element energies).  Both must reach the FP64 true
 residual the oracle's apply confirms; the adaptive inner tolerance of the last
@@ -29,7 +29,7 @@ CASES = [(2, 1, "elliptic", 24), (2, 2, "elliptic", 16), (2, 4, "elliptic", 12),
          (2, 3, "projection", 12), (3, 2, "elliptic", 5), (3, 1, "projection", 6)]
 
 
-@pytest.mark.parametrize("rec", ["auto", "standard", "single_reduction"])
+@pytest.mark.parametrize("rec", ["standard", "fused_pq", "single_reduction"])
 @pytest.mark.parametrize("d,p,form,N", CASES, ids=[f"{d}D-P{p}-{f}" for d, p, f, _ in CASES])
 def test_mixed_recurrences_reach_tolerance(B, d, p, form, N, rec):
     coords, cells = inputs.lattice_mesh(d, N, 0.2 if d == 2 else 0.1, 3)
@@ -54,8 +54,8 @@ def test_single_reduction_factorized_and_repeat(B):
     A = inputs.coef_tensor_lognormal(len(cells), 2, 1.0, 4)
     ctx = B.Context(coords, cells, 3, "elliptic", A, factorized=True)
     b = ctx.load()
-    x1, i1 = ctx.solve(b, mode="mixed", tol=1e-9)
-    x2, i2 = ctx.solve(b, mode="mixed", tol=1e-9)
+    x1, i1 = ctx.solve(b, mode="mixed", tol=1e-9, inner_recurrence="fused_pq")
+    x2, i2 = ctx.solve(b, mode="mixed", tol=1e-9, inner_recurrence="fused_pq")
     assert i1["status"] == 0 and i2["status"] == 0
     # atomic scatter: the order of the FP32 adds differs between runs, and the FP32
     # recurrences amplify it into iteration counts a few percent apart
