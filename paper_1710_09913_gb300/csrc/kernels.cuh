@@ -125,6 +125,67 @@ __device__ __forceinline__ void block_mul(const T* a, const T* g, T* h) {
   }
 }
 
+// Packed FP32x2 forms of interp / block_mul / project for two right-hand sides of the
+// same cell (sm_100 family FFMA2): both lanes of a pair share every constant of B and
+// every entry of A_T, so one packed instruction does the work of two.
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+template <class TB, int J>
+__device__ __forceinline__ void interp2(const float2 (&ul)[TB::V], float2 (&g)[TB::NB]) {
+  static_for<TB::NB>([&](auto rc) {
+    constexpr int r = decltype(rc)::value;
+    constexpr int L0 = row_first<TB>(r, J);
+    if constexpr (L0 < 0) {
+      g[r] = f2(0.0f);
+    } else {
+      static_for<TB::V>([&](auto lc) {
+        constexpr int l = decltype(lc)::value;
+        constexpr double b = TB::B[r][J][l];
+        if constexpr (l == L0) {
+          if constexpr (b == 1.0) g[r] = ul[l];
+          else g[r] = __fmul2_rn(f2((float)b), ul[l]);
+        } else if constexpr (l > L0 && b != 0.0) {
+          if constexpr (b == 1.0) g[r] = __fadd2_rn(g[r], ul[l]);
+          else g[r] = __ffma2_rn(f2((float)b), ul[l], g[r]);
+        }
+      });
+    }
+  });
+}
+template <class TB, int J>
+__device__ __forceinline__ void project2(const float2 (&h)[TB::NB], float2 (&Y)[TB::V]) {
+  static_for<TB::NB>([&](auto rc) {
+    constexpr int r = decltype(rc)::value;
+    static_for<TB::V>([&](auto lc) {
+      constexpr int l = decltype(lc)::value;
+      constexpr double b = TB::B[r][J][l];
+      if constexpr (b != 0.0) {
+        if constexpr (col_first<TB>(J, r, l)) {
+          if constexpr (b == 1.0) Y[l] = h[r];
+          else Y[l] = __fmul2_rn(f2((float)b), h[r]);
+        } else {
+          if constexpr (b == 1.0) Y[l] = __fadd2_rn(Y[l], h[r]);
+          else Y[l] = __ffma2_rn(f2((float)b), h[r], Y[l]);
+        }
+      }
+    });
+  });
+}
+template <int D, int FORM, typename S>
+__device__ __forceinline__ void block_mul2(const S* a, const float2* g, float2* h) {
+  if constexpr (FORM == DOGIP_PROJECTION) {
+    h[0] = __fmul2_rn(f2((float)a[0]), g[0]);
+  } else {
+    static_for<D>([&](auto rc) {
+      constexpr int r = decltype(rc)::value;
+      h[r] = __fmul2_rn(f2((float)a[sym_idx(D, r, 0)]), g[0]);
+      static_for<D - 1>([&](auto sc) {
+        constexpr int s = decltype(sc)::value + 1;
+        h[r] = __ffma2_rn(f2((float)a[sym_idx(D, r, s)]), g[s], h[r]);
+      });
+    });
+  }
+}
+
 template <typename T>
 struct ApplyArgs {
   const T* A;            // AoSoA [Epad/32][W*NS][32]
@@ -592,6 +653,17 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T, FACT>::THREADS)
                 if constexpr (col_empty<TB>(l)) Y[q][l] = T(0);
               });
             });
+            // packed pairs of right-hand sides (RW = 4, FP32)
+            constexpr int NP = RW == 4 && std::is_same<T, float>::value ? 2 : 1;
+            float2 u2[NP][V], Y2[NP][V];
+            if constexpr (NP == 2) {
+              static_for<V>([&](auto lc) {
+                constexpr int l = decltype(lc)::value;
+                u2[0][l] = make_float2(ul[0][l], ul[1][l]);
+                u2[1][l] = make_float2(ul[2][l], ul[3][l]);
+                if constexpr (col_empty<TB>(l)) Y2[0][l] = Y2[1][l] = f2(0.0f);
+              });
+            }
             static_for<W>([&](auto jc) {
               constexpr int j = decltype(jc)::value;
               T aj[NS];
@@ -604,14 +676,34 @@ __global__ void __launch_bounds__(TmaCfg<D, P, FORM, T, FACT>::THREADS)
                   aj[kk] = sA[(j * NS + kk) * kTile];
                 }
               });
-              static_for<RW>([&](auto qc) {
-                constexpr int q = decltype(qc)::value;
-                T g[NB], h[NB];
-                interp<TB, j>(ul[q], g);
-                block_mul<D, FORM>(aj, g, h);
-                project<TB, j>(h, Y[q]);
-              });
+              if constexpr (RW == 4 && std::is_same<T, float>::value) {
+                // right-hand sides (0, 1) and (2, 3) as packed pairs
+                static_for<2>([&](auto pc) {
+                  constexpr int pp = decltype(pc)::value;
+                  float2 g2[NB], h2[NB];
+                  interp2<TB, j>(u2[pp], g2);
+                  block_mul2<D, FORM>(aj, g2, h2);
+                  project2<TB, j>(h2, Y2[pp]);
+                });
+              } else {
+                static_for<RW>([&](auto qc) {
+                  constexpr int q = decltype(qc)::value;
+                  T g[NB], h[NB];
+                  interp<TB, j>(ul[q], g);
+                  block_mul<D, FORM>(aj, g, h);
+                  project<TB, j>(h, Y[q]);
+                });
+              }
             });
+            if constexpr (RW == 4 && std::is_same<T, float>::value) {
+              static_for<V>([&](auto lc) {
+                constexpr int l = decltype(lc)::value;
+                Y[0][l] = Y2[0][l].x;
+                Y[1][l] = Y2[0][l].y;
+                Y[2][l] = Y2[1][l].x;
+                Y[3][l] = Y2[1][l].y;
+              });
+            }
           } else {
             static_for<RW>([&](auto qc) {
               static_for<V>([&](auto lc) { Y[decltype(qc)::value][decltype(lc)::value] = T(0); });
