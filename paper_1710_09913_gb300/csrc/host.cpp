@@ -986,6 +986,116 @@ void replay(BatchGraph& bg, std::vector<Ctx*>& cs, cudaStream_t main) {
   cuda_check(cudaStreamSynchronize(main), "batch round");
 }
 
+// The inner CG chunk of a grouped batch: per iteration the apply once per (dim, p,
+// form) group, then the Dirichlet rows and the three vector kernels, all over the
+// items of every problem; at the end the scalars and flags of all problems go to the
+// host in one copy.  Allocates the problem table, the item tables and the status
+// buffers (stream-ordered on main; the caller frees them).  Kernel launches are
+// counted on the first context.
+BatchGraph capture_grouped(std::vector<Ctx*>& cs, cudaStream_t main, int chunk, BProb*& d_probs,
+                           int2*& d_items, CGScal*& d_stat, int*& d_statf, CGScal*& h_stat,
+                           int*& h_statf) {
+  const int np = (int)cs.size();
+  std::vector<BProb> probs(np);
+  std::map<int, std::vector<int2>> cells;  // key d*100 + p*2 + form
+  std::vector<int2> bitems, vitems;
+  const int64_t cpi = batch_cells_per_item(), dpi = batch_dofs_per_item();
+  for (int i = 0; i < np; ++i) {
+    Ctx& c = *cs[i];
+    SolveWork& w = c.work;
+    BProb& pr = probs[i];
+    pr.A = c.d_A32;
+    pr.conn = c.d_conn;
+    pr.E = c.E;
+    pr.n = c.n;
+    pr.x = w.x32;
+    pr.r = w.r32;
+    pr.p = w.p32;
+    pr.q = w.q32;
+    pr.dinv = c.d_dinv32;
+    pr.bnd = c.d_bnd;
+    pr.nbnd = c.dirichlet ? c.nbnd : 0;
+    pr.scal = w.scal;
+    pr.flags = w.flags;
+    pr.partial = w.partial;
+    pr.counter = w.counter;
+    pr.nvblocks = (int)((c.n + dpi - 1) / dpi);
+    if (2 * (int64_t)pr.nvblocks > (int64_t)kMaxRedBlocks * 64)
+      fail(DOGIP_EUNSUPPORTED, "problem too large for the grouped batch reduction");
+    auto& cl = cells[c.d * 100 + c.p * 2 + c.form];
+    for (int64_t b = 0; b < (c.E + cpi - 1) / cpi; ++b) cl.push_back(make_int2(i, (int)b));
+    for (int64_t b = 0; b < (pr.nbnd + cpi - 1) / cpi; ++b) bitems.push_back(make_int2(i, (int)b));
+    for (int b = 0; b < pr.nvblocks; ++b) vitems.push_back(make_int2(i, b));
+  }
+  std::vector<int2> all;
+  std::vector<std::pair<int, std::pair<size_t, int>>> groups;  // key, (offset, count)
+  for (auto& kv : cells) {
+    groups.push_back({kv.first, {all.size(), (int)kv.second.size()}});
+    all.insert(all.end(), kv.second.begin(), kv.second.end());
+  }
+  const size_t boff = all.size();
+  all.insert(all.end(), bitems.begin(), bitems.end());
+  const size_t voff = all.size();
+  all.insert(all.end(), vitems.begin(), vitems.end());
+  if (all.size() > (size_t)INT32_MAX) fail(DOGIP_EUNSUPPORTED, "batch too large");
+  cuda_check(cudaMallocAsync((void**)&d_probs, sizeof(BProb) * np, main), "batch table");
+  cuda_check(cudaMallocAsync((void**)&d_items, sizeof(int2) * all.size(), main), "batch items");
+  cuda_check(cudaMallocAsync((void**)&d_stat, sizeof(CGScal) * np, main), "batch status");
+  cuda_check(cudaMallocAsync((void**)&d_statf, sizeof(int) * 4 * np, main), "batch flags");
+  if (cudaMallocHost((void**)&h_stat, sizeof(CGScal) * np) != cudaSuccess ||
+      cudaMallocHost((void**)&h_statf, sizeof(int) * 4 * np) != cudaSuccess) {
+    cudaGetLastError();
+    fail(DOGIP_ENOMEM, "pinned host allocation failed");
+  }
+  cuda_check(cudaMemcpyAsync(d_probs, probs.data(), sizeof(BProb) * np, cudaMemcpyHostToDevice, main),
+             "batch table upload");
+  cuda_check(cudaMemcpyAsync(d_items, all.data(), sizeof(int2) * all.size(), cudaMemcpyHostToDevice,
+                             main), "batch items upload");
+  cuda_check(cudaStreamSynchronize(main), "batch tables");
+  BatchGraph bg;
+  bg.kernels.assign(cs.size(), 0);
+  int64_t nk = 0;
+  cuda_check(cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal), "begin capture");
+  try {
+    for (int it = 0; it < chunk; ++it) {
+      for (auto& g : groups) {
+        const int key = g.first;
+        batch_apply_group(key / 100, (key % 100) / 2, key % 2, d_probs, d_items + g.second.first,
+                          g.second.second, main);
+        nk += g.second.second > 0 ? 1 : 0;
+      }
+      batch_vec_step(d_probs, d_items + boff, (int)bitems.size(), d_items + voff,
+                     (int)vitems.size(), main);
+      nk += (bitems.empty() ? 0 : 1) + 3;
+    }
+    batch_status(d_probs, np, d_stat, d_statf, main);
+    nk += 1;
+    cuda_check(cudaMemcpyAsync(h_stat, d_stat, sizeof(CGScal) * np, cudaMemcpyDeviceToHost, main),
+               "status copy");
+    cuda_check(cudaMemcpyAsync(h_statf, d_statf, sizeof(int) * 4 * np, cudaMemcpyDeviceToHost, main),
+               "flags copy");
+  } catch (...) {
+    cudaGraph_t g = nullptr;
+    cudaStreamEndCapture(main, &g);
+    if (g) cudaGraphDestroy(g);
+    throw;
+  }
+  cudaGraph_t g = nullptr;
+  cuda_check(cudaStreamEndCapture(main, &g), "end capture");
+  cudaError_t e = cudaGraphInstantiate(&bg.exec, g, 0);
+  cudaGraphDestroy(g);
+  cuda_check(e, "batch graph instantiate");
+  bg.kernels[0] = nk;
+  return bg;
+}
+
+void unpack_status(std::vector<Ctx*>& cs, const CGScal* h_stat, const int* h_statf) {
+  for (size_t i = 0; i < cs.size(); ++i) {
+    std::memcpy(cs[i]->work.h_scal, h_stat + i, sizeof(CGScal));
+    std::memcpy(cs[i]->work.h_flags, h_statf + 4 * i, sizeof(int) * 4);
+  }
+}
+
 int batch_solve(Ctx* const* ctxs, int np, const double* const* b, double* const* u,
                 const dogip_solve_opts* opts, dogip_solve_info* infos, double* seconds_out,
                 cudaStream_t user) {
@@ -1016,9 +1126,28 @@ int batch_solve(Ctx* const* ctxs, int np, const double* const* b, double* const*
   cudaEvent_t ev = nullptr;
   cuda_check(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
   std::vector<BatchGraph> graphs;
+  // grouped inner iterations (mixed mode): one launch per kernel for the whole batch
+  // where every context has FP32 element-wise A_T in caller cell order and compiled
+  // tables (DOGIP_BATCH_GROUPED=0: one graph branch per problem instead)
+  bool grouped = o.mode == DOGIP_SOLVE_MIXED;
+  if (const char* v = std::getenv("DOGIP_BATCH_GROUPED")) grouped = grouped && std::atoi(v) != 0;
+  for (Ctx* c : cs)
+    grouped = grouped && c->keep32 && !c->hi && !c->global_w && !c->factorized &&
+              c->scatter == DOGIP_SCATTER_ATOMIC && batch_apply_compiled(c->d, c->p, c->form);
+  BProb* d_probs = nullptr;
+  int2* d_items = nullptr;
+  CGScal* d_stat = nullptr;
+  int* d_statf = nullptr;
+  CGScal* h_stat = nullptr;
+  int* h_statf = nullptr;
   auto cleanup = [&]() {
     for (auto& g : graphs)
       if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (void* q : {(void*)d_probs, (void*)d_items, (void*)d_stat, (void*)d_statf})
+      if (q) cudaFreeAsync(q, main);
+    cudaStreamSynchronize(main);
+    if (h_stat) cudaFreeHost(h_stat);
+    if (h_statf) cudaFreeHost(h_statf);
     cudaEventDestroy(ev);
     cudaStreamDestroy(main);
   };
@@ -1049,6 +1178,10 @@ int batch_solve(Ctx* const* ctxs, int np, const double* const* b, double* const*
       scal_copy(c, s);
     }));
     // phase 1: a chunk of CG iterations (FP32 inner or FP64)
+    if (grouped) {
+      graphs.push_back(capture_grouped(cs, main, chunk, d_probs, d_items, d_stat, d_statf, h_stat,
+                                       h_statf));
+    } else
     graphs.push_back(capture_batch(cs, main, [&](int i, Ctx& c, cudaStream_t s) {
       SolveWork& w = c.work;
       for (int it = 0; it < chunk; ++it) {
@@ -1101,6 +1234,7 @@ int batch_solve(Ctx* const* ctxs, int np, const double* const* b, double* const*
           for (Ctx* c : cs) all_in = all_in && c->work.h_flags[2];
           if (all_in) break;
           replay(graphs[1], cs, main);
+          if (grouped) unpack_status(cs, h_stat, h_statf);
           inner += chunk;
           bool brk = false;
           for (Ctx* c : cs) brk = brk || c->work.h_flags[1];

@@ -226,6 +226,33 @@ void launch_diag_finish(Ctx& c, cudaStream_t s);
 // One-time kernel attributes of the apply instances of this context (host only).
 void prepare_apply(Ctx& c);
 
+// ---- grouped kernels of the batched mixed solve (batch.cu) ----------------------
+// One problem of a batch as the grouped kernels see it (device memory, FP32 inner CG).
+struct BProb {
+  const float* A;           // A_T, AoSoA, processing order = caller order
+  const uint32_t* conn;
+  int64_t E, n;
+  float *x, *r, *p, *q;     // inner CG vectors
+  const float* dinv;
+  const int32_t* bnd;       // Dirichlet rows
+  int64_t nbnd;
+  CGScal* scal;
+  int* flags;
+  double* partial;          // per-problem reduction buffer
+  unsigned int* counter;
+  int nvblocks;             // vector work items of this problem
+};
+// Items are (problem, block) pairs; cells per apply item and dofs per vector item:
+int64_t batch_cells_per_item();
+int64_t batch_dofs_per_item();
+bool batch_apply_compiled(int d, int p, int form);
+void batch_apply_group(int d, int p, int form, const BProb* probs, const int2* items, int nitems,
+                       cudaStream_t s);
+// Dirichlet rows (bitems: blocks of 256 boundary dofs), then p.q, x/r update, p update.
+void batch_vec_step(const BProb* probs, const int2* bitems, int nbitems, const int2* vitems,
+                    int nvitems, cudaStream_t s);
+void batch_status(const BProb* probs, int np, CGScal* scal_out, int* flags_out, cudaStream_t s);
+
 // Programmatic dependent launch inside captured CG chunks: kernels whose first act
 // is griddepcontrol.launch_dependents + griddepcontrol.wait (they touch nothing of the
 // previous kernel before the wait) are marked by their launchers; run_chunk turns the

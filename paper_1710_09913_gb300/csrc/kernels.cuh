@@ -200,22 +200,11 @@ struct ApplyArgs {
 // Algorithm 1 for one (element, rhs) per thread: gather u_T, then per W node
 // interpolate (B u_T), multiply by A_T,j, project back (B^*), and finally
 // scatter-add Y into y.  The W-node loop is fused, so B u_T is never stored.
+// Algorithm 1 for cell e (processing order) and right-hand side r of a.
 template <int D, int P, int FORM, typename T, bool ATOMIC, bool MULTI>
-__global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> a) {
+__device__ __forceinline__ void apply_cell(const ApplyArgs<T>& a, int64_t e, int r) {
   using TB = dogip_tab::Tab<D, P, FORM>;
   constexpr int V = TB::V, W = TB::W, NB = TB::NB, NS = NSym<D, FORM>::value;
-  if (a.skip != nullptr && *a.skip) return;
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int64_t e;
-  int r = 0;
-  if constexpr (MULTI) {
-    const int64_t q = t / a.R;
-    e = a.e0 + q;
-    r = (int)(t - q * a.R);
-  } else {
-    e = a.e0 + t;
-  }
-  if (e >= a.e1) return;
   const int64_t tile = e >> 5;
   const int lane = (int)(e & 31);
   const uint32_t* ct = a.conn + tile * (V * kTile) + lane;
@@ -252,6 +241,23 @@ __global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> a) {
       else *dst += Y[l];
     }
   });
+}
+
+template <int D, int P, int FORM, typename T, bool ATOMIC, bool MULTI>
+__global__ void __launch_bounds__(256) k_apply(ApplyArgs<T> a) {
+  if (a.skip != nullptr && *a.skip) return;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t e;
+  int r = 0;
+  if constexpr (MULTI) {
+    const int64_t q = t / a.R;
+    e = a.e0 + q;
+    r = (int)(t - q * a.R);
+  } else {
+    e = a.e0 + t;
+  }
+  if (e >= a.e1) return;
+  apply_cell<D, P, FORM, T, ATOMIC, MULTI>(a, e, r);
 }
 
 // ------------------------------------------------- bulk-async staged apply

@@ -64,3 +64,24 @@ def test_batch_config_uneven_256(B):
     assert worst <= 1.01e-8
     times = sorted(i["seconds"] for i in infos)
     assert times[0] > 0 and times[-1] >= times[len(times) // 2]
+
+
+@pytest.mark.parametrize("grouped", ["1", "0"])
+def test_batch_grouped_and_branches_agree(B, grouped, monkeypatch):
+    """The grouped inner iterations (one launch per kernel for the whole batch) and the
+    per-problem graph branches reach the same tolerance, confirmed by the oracle; 3D
+    problems and the projection form join the 2D elliptic ones in one batch."""
+    monkeypatch.setenv("DOGIP_BATCH_GROUPED", grouped)
+    probs = _problems(B, [(6, 2, 11), (10, 1, 12), (4, 3, 13)])
+    c3, t3 = inputs.lattice_mesh(3, 3)
+    m3 = inputs.coef_uniform(len(t3), 1.0, 5.0, 14)
+    for form in ("elliptic", "projection"):
+        probs.append((B.Context(c3, t3, 2, form, m3), odogip.Problem(form, 2, c3, t3, m3)))
+    bs = [c.load() for c, _ in probs]
+    us = [torch.zeros_like(b) for b in bs]
+    infos = B.batch_solve([c for c, _ in probs], bs, us, mode="mixed", tol=1e-10, check_every=4)
+    for (c, P), b, u, inf in zip(probs, bs, us, infos):
+        assert inf["status"] == 0, inf
+        bb = b.cpu().numpy()
+        r = bb - P.apply(u.cpu().numpy())
+        assert np.linalg.norm(r) <= 1.01e-10 * np.linalg.norm(bb)
