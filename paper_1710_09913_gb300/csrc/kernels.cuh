@@ -403,9 +403,9 @@ struct TmaCfg {
   static constexpr uint32_t CHUNK = TPC * (A_TILE + C_TILE);
   static constexpr uint32_t PRO = TPC * C_TILE;  // conn of the CTA's first chunk
   static constexpr int S0 = (int)((kBudget - PRO) / CHUNK);
-  // pipeline stages: up to 8 where the tiles are small (low orders), so that enough
-  // bytes are in flight per SM
-  static constexpr int S = S0 > 8 ? 8 : (S0 < 2 ? 2 : S0);
+  // pipeline stages: at most 4 (more stages of small tiles raise the shared memory per
+  // CTA and lower the CTAs resident per SM: measured slower at P2, no gain at P1)
+  static constexpr int S = S0 > 4 ? 4 : (S0 < 2 ? 2 : S0);
   static constexpr uint32_t SMEM = S * CHUNK + PRO + (2 * S + 1) * 8 + 128;  // + bars, align
   static constexpr int THREADS = (TPC + 1) * 32;  // TPC consumer warps + 1 producer warp
   // Instances whose double-buffered 2-warp ring does not fit (3D P3 FP64) use the
