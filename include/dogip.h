@@ -47,8 +47,10 @@
  *    programmatic dependents of each other where they are written for it (the next
  *    kernel starts while the previous one drains); 0 keeps full serialisation.
  *  - DOGIP_TEST_WAIT_CYCLES, DOGIP_TEST_SKIP_CHUNK: test hooks of the device-side
- *    failure path (a shorter bound on the kernels' waits, and one chunk of the
- *    staged apply whose copy is never issued, so that its bounded wait expires).
+ *    failure path (a shorter bound on the kernels' waits; one chunk of the staged
+ *    apply, or one tile of the tensor-core apply, whose copy is never issued, and
+ *    one block of the single-launch PCG that never arrives at its first grid
+ *    barrier, so that the bounded waits of the others expire).
  */
 #ifndef DOGIP_H
 #define DOGIP_H
@@ -349,6 +351,17 @@ typedef struct {
                          iterations).  1 and 2 need nrhs 1, FP32, atomic
                          scatter and the staged apply kernel (else
                          EUNSUPPORTED); both measured slower than 0 on GB300  */
+  int single_launch;  /* FP64 PCG and the MIXED inner FP32 PCG with the standard
+                         recurrence can run the iterations of a solve inside
+                         one cooperative kernel (two grid-wide barriers an
+                         iteration, up to min(4096, 256 check_every)
+                         iterations a launch; nrhs 1, atomic scatter, 2D and
+                         3D p <= 2, element-wise storage).  -1 (default): the
+                         FP32 inner solves whose operator and vectors fit in
+                         L2 take it (FP64 PCG measured faster per step);
+                         0 never (one kernel per step, graph-captured chunks
+                         of check_every iterations); 1 whenever supported,
+                         FP64 included (else as 0)                          */
 } dogip_solve_opts;
 
 typedef struct {

@@ -75,7 +75,8 @@ class SolveOpts(C.Structure):
                 ("inner_tol", C.c_double), ("inner_maxiter", C.c_int), ("max_outer", C.c_int),
                 ("scatter", C.c_int), ("check_every", C.c_int), ("use_x0", C.c_int),
                 ("timeout_ms", C.c_double), ("reliable_delta", C.c_double),
-                ("inner_prec", C.c_int), ("inner_recurrence", C.c_int)]
+                ("inner_prec", C.c_int), ("inner_recurrence", C.c_int),
+                ("single_launch", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -428,7 +429,7 @@ class Context:
 
     def _solve_opts(self, mode, tol, maxiter, inner_tol, inner_maxiter, max_outer, scatter,
                     check_every, x0, timeout_ms, reliable_delta=None, inner_prec=None,
-                    inner_recurrence=None):
+                    inner_recurrence=None, single_launch=None):
         o = SolveOpts()
         lib.dogip_solve_opts_default(C.byref(o))
         o.mode = MODES.get(mode, mode)
@@ -452,21 +453,24 @@ class Context:
             o.inner_prec = PRECS.get(inner_prec, inner_prec)
         if inner_recurrence is not None:
             o.inner_recurrence = RECURRENCES.get(inner_recurrence, inner_recurrence)
+        if single_launch is not None:
+            o.single_launch = {"auto": -1, False: 0, True: 1}.get(single_launch, single_launch)
         return o
 
     def solve(self, b, u=None, *, mode="fp64", tol=1e-8, maxiter=None, inner_tol=None,
               inner_maxiter=None, max_outer=None, scatter=None, check_every=None, x0=False,
               timeout_ms=0.0, stream=None, allow_notconv=False, reliable_delta=None,
-              inner_prec=None, inner_recurrence=None):
+              inner_prec=None, inner_recurrence=None, single_launch=None):
         """Solve K u = b on the device; returns (u, info dict).  inner_prec ("fp32" or
-        "tf32") selects the applies of the mixed modes' inner solves."""
+        "tf32") selects the applies of the mixed modes' inner solves; single_launch
+        ("auto", True, False) the one-kernel PCG iterations for problems that fit in L2."""
         import torch
         R = 1 if b.dim() == 1 else b.shape[1]
         if u is None:
             u = torch.zeros_like(b)
         o = self._solve_opts(mode, tol, maxiter, inner_tol, inner_maxiter, max_outer, scatter,
                              check_every, x0, timeout_ms, reliable_delta, inner_prec,
-                             inner_recurrence)
+                             inner_recurrence, single_launch)
         inf = SolveInfo()
         rel = np.zeros(R)
         code = lib.dogip_solve(self._h, _dptr(b, torch.float64), _dptr(u, torch.float64), R,

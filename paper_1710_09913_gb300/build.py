@@ -26,7 +26,7 @@ NVCC_FLAGS = ["-std=c++17", "--expt-relaxed-constexpr", "-O3", "-lineinfo", "-Xc
               "-Xcompiler", "-fvisibility=hidden"]
 UNITS = ["host.cpp", "setup_kernels.cu", "setup_d2.cu", "setup_d3.cu", "vec.cu", "apply_d2.cu",
          "apply_d3a.cu", "apply_d3b.cu", "apply_qp2.cu", "apply_qp3.cu", "apply_gw.cu",
-         "apply_hi.cu", "apply_tc.cu", "noalloc.cu", "batch.cu"]
+         "apply_hi.cu", "apply_tc.cu", "noalloc.cu", "batch.cu", "cg_small.cu"]
 
 PMAX2, PMAX3 = 4, 3  # orders with compile-time tables (unrolled kernels)
 PHI2, PHI3 = 8, 4  # highest orders, served by the run-time-table kernels

@@ -777,6 +777,21 @@ int solve(Ctx& c, const double* b, double* u, int R, const dogip_solve_opts* opt
   vec_alloc(c.work, c.n, R);
   SolveWork& w = c.work;
   cudaStream_t s = c.stream;
+  // The PCG iterations (FP64 mode, or the standard FP32 inner recurrence of MIXED) in
+  // one cooperative launch when the problem stays in L2: its iteration cost is then
+  // latency, which the kernel boundaries of the graph-captured chunks would dominate.
+  // By default only the FP32 inner solves take it: measured on GB300 (2D P1 and P2 on
+  // 512 x 512 squares) it is faster there, while FP64 PCG, whose one-thread-per-cell
+  // apply is bound by the FP64 rate, is faster with the per-step kernels.
+  const int cg_prec = o.mode == DOGIP_SOLVE_FP64 ? DOGIP_FP64 : DOGIP_FP32;
+  bool single = false;
+  if (o.single_launch != 0 && R == 1 && scatter == DOGIP_SCATTER_ATOMIC && rec == 0 &&
+      o.mode != DOGIP_SOLVE_MIXED_RELIABLE && (o.mode == DOGIP_SOLVE_FP64 || ip == DOGIP_FP32) &&
+      pcg_small_supported(c, cg_prec))
+    single = o.single_launch == 1 ||
+             (cg_prec == DOGIP_FP32 && c.l2_bytes > 0 && pcg_small_bytes(c, cg_prec) <= c.l2_bytes);
+  // iterations per single launch (host checks for timeouts between launches)
+  const int step_iters = single ? std::min(4096, 256 * chunk) : chunk;
   cuda_check(cudaEventRecord(c.ev_in, user), "event record");
   cuda_check(cudaStreamWaitEvent(s, c.ev_in, 0), "stream wait");
   auto timed_out = [&]() {
@@ -808,8 +823,9 @@ int solve(Ctx& c, const double* b, double* u, int R, const dogip_solve_opts* opt
       while (!w.h_flags[0]) {
         if (iters + done_here >= o.maxiter) break;
         if (timed_out()) break;
-        const int k = std::min(chunk, o.maxiter - iters - done_here);
-        run_chunk(c, DOGIP_FP64, scatter, u, k, 0.0);
+        const int k = std::min(step_iters, o.maxiter - iters - done_here);
+        if (single) pcg_small_run(c, DOGIP_FP64, u, k);
+        else run_chunk(c, DOGIP_FP64, scatter, u, k, 0.0);
         done_here = 0;
         for (int r = 0; r < R; ++r) done_here = std::max(done_here, w.h_scal[r].iters);
         if (w.h_flags[1]) break;
@@ -889,8 +905,9 @@ int solve(Ctx& c, const double* b, double* u, int R, const dogip_solve_opts* opt
       const int lim = std::min(o.inner_maxiter, budget);
       while (!w.h_flags[0] && inner < lim) {
         if (timed_out()) break;
-        const int k = std::min(chunk, lim - inner);
-        run_chunk(c, ip, scatter, nullptr, k, 0.0, rec);
+        const int k = std::min(step_iters, lim - inner);
+        if (single) pcg_small_run(c, DOGIP_FP32, nullptr, k);
+        else run_chunk(c, ip, scatter, nullptr, k, 0.0, rec);
         inner = 0;
         for (int r = 0; r < R; ++r) inner = std::max(inner, w.h_scal[r].iters);
         if (w.h_flags[1]) break;
@@ -1501,6 +1518,7 @@ int dogip_solve_opts_default(dogip_solve_opts* o) {
   o->reliable_delta = 0.1;
   o->inner_prec = DOGIP_FP32;
   o->inner_recurrence = 0;
+  o->single_launch = -1;
   return DOGIP_OK;
 }
 

@@ -43,6 +43,9 @@ struct SolveWork {
   // Chronopoulos-Gear inner CG (R = 1): search direction p and s = K p; u (= M r) and
   // w (= K u) live in p32 and q32
   float *pc32 = nullptr, *sc32 = nullptr;
+  // second search-direction buffers of the single-launch PCG (pcg_small_run)
+  float* pb32 = nullptr;
+  double* pb64 = nullptr;
   // reductions
   double* partial = nullptr;     // [kMaxRedBlocks x 32 x 2]
   unsigned int* counter = nullptr;
@@ -306,5 +309,12 @@ int vec_fold(SolveWork& w, double* x64, cudaStream_t st);
 int vec_rel_restart(SolveWork& w, const float* dinv, cudaStream_t st);
 // x64 += s * x32 for rhs still refining.
 int vec_correct(SolveWork& w, double* x64, cudaStream_t st);
+
+// Single-launch PCG (one cooperative kernel runs up to maxit iterations of the PCG
+// started by vec_init64 / vec_inner_init32, nrhs 1, atomic scatter): FP64 iterates x64,
+// FP32 iterates x32.  Leaves scal, flags and their host mirrors as run_chunk does.
+bool pcg_small_supported(const Ctx& c, int prec);
+int64_t pcg_small_bytes(const Ctx& c, int prec);  // operator + vectors it streams
+void pcg_small_run(Ctx& c, int prec, double* x64, int maxit);
 
 }  // namespace dogip

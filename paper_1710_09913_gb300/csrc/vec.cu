@@ -577,7 +577,8 @@ void vec_free(SolveWork& w) {
   w.graph = nullptr;
   for (void* p : {(void*)w.x64, (void*)w.r64, (void*)w.p64, (void*)w.q64, (void*)w.x32,
                   (void*)w.r32, (void*)w.p32, (void*)w.q32, (void*)w.partial, (void*)w.counter,
-                  (void*)w.scal, (void*)w.flags, (void*)w.pc32, (void*)w.sc32})
+                  (void*)w.scal, (void*)w.flags, (void*)w.pc32, (void*)w.sc32, (void*)w.pb32,
+                  (void*)w.pb64})
     if (p) cudaFree(p);
   if (w.h_flags) cudaFreeHost(w.h_flags);
   if (w.h_scal) cudaFreeHost(w.h_scal);

@@ -1,0 +1,117 @@
+"""The single-launch PCG (one cooperative kernel runs the iterations of a solve, two
+grid-wide barriers per iteration, the search direction formed where it is read, and
+(p, K p) from the cells' energies): FP64 PCG and the FP32 inner solves of the mixed
+mode reach the FP64 true residual the oracle's apply confirms, with iteration counts
+close to the kernel-per-step PCG (the same recurrence in another rounding order), on
+both forms in 2D and 3D, with and without Dirichlet rows, across several launches of
+one solve, and chosen by default for problems that fit in L2."""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import dogip as odogip  # noqa: E402
+from paper_1710_09913_gb300 import inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_1710_09913_gb300 import build
+    build.build()
+    from paper_1710_09913_gb300 import binding
+    return binding
+
+
+CASES = [(2, 1, "elliptic", 24), (2, 2, "elliptic", 16), (2, 1, "projection", 20),
+         (2, 2, "projection", 12), (3, 1, "elliptic", 8), (3, 2, "elliptic", 5),
+         (3, 2, "projection", 4)]
+
+
+def _problem(B, d, p, form, N, seed=3):
+    coords, cells = inputs.lattice_mesh(d, N, 0.2 if d == 2 else 0.1, seed)
+    E = len(cells)
+    coef = inputs.coef_tensor_lognormal(E, d, 1.0, seed) if form == "elliptic" else \
+        inputs.coef_uniform(E, 1.0, 10.0, seed)
+    return B.Context(coords, cells, p, form, coef), odogip.Problem(form, p, coords, cells, coef)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+@pytest.mark.parametrize("d,p,form,N", CASES, ids=[f"{d}D-P{p}-{f}" for d, p, f, _ in CASES])
+def test_single_launch_reaches_tolerance(B, d, p, form, N, mode):
+    ctx, P = _problem(B, d, p, form, N)
+    b = ctx.load()
+    tol = 1e-10
+    l0 = ctx.launches()
+    x, info = ctx.solve(b, mode=mode, tol=tol, single_launch=True)
+    l1 = ctx.launches()
+    assert info["status"] == 0 and info["rel_residual"] <= tol
+    bb = b.cpu().numpy()
+    r = bb - P.apply(x.cpu().numpy())
+    assert np.linalg.norm(r) <= 1.01 * tol * np.linalg.norm(bb)
+    x2, info2 = ctx.solve(b, mode=mode, tol=tol, single_launch=False)
+    l2 = ctx.launches()
+    assert info2["status"] == 0
+    assert abs(info["iterations"] - info2["iterations"]) <= max(3, 0.1 * info2["iterations"])
+    # one kernel runs many iterations; the per-step PCG launches four per iteration
+    assert 2 * (l1 - l0) < l2 - l1
+    np.testing.assert_allclose(x.cpu().numpy(), x2.cpu().numpy(), rtol=0,
+                               atol=1e-5 * np.abs(x2.cpu().numpy()).max())
+    ctx.check()
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_single_launch_resumes_across_launches(B, mode):
+    """check_every = 1 caps a launch at 256 iterations, so this solve (several hundred
+    iterations) spans several launches, each resuming from the search direction the
+    previous one left; the result matches one long launch's to rounding."""
+    ctx, P = _problem(B, 2, 1, "elliptic", 96, seed=7)
+    b = ctx.load()
+    x1, i1 = ctx.solve(b, mode=mode, tol=1e-10, single_launch=True, check_every=1)
+    x2, i2 = ctx.solve(b, mode=mode, tol=1e-10, single_launch=True)
+    assert i1["status"] == 0 and i2["status"] == 0
+    assert i1["iterations"] > 256
+    assert abs(i1["iterations"] - i2["iterations"]) <= max(3, 0.05 * i2["iterations"])
+    bb = b.cpu().numpy()
+    r = bb - P.apply(x1.cpu().numpy())
+    assert np.linalg.norm(r) <= 1.01e-10 * np.linalg.norm(bb)
+
+
+def test_single_launch_iteration_limit(B):
+    """FP64 PCG stopped by maxiter inside a launch reports ENOTCONV with exactly
+    maxiter iterations and a finite iterate."""
+    ctx, _ = _problem(B, 2, 2, "elliptic", 16)
+    b = ctx.load()
+    x, info = ctx.solve(b, mode="fp64", tol=1e-12, maxiter=37, single_launch=True,
+                        allow_notconv=True)
+    assert info["status"] == B.ENOTCONV and info["iterations"] == 37
+    assert torch.isfinite(x).all()
+
+
+def test_single_launch_default_for_small_problems(B):
+    """With the default option the FP32 inner solves of a problem that fits in L2 run
+    the single launch (few kernel launches per solve); FP64 PCG keeps the per-step
+    kernels."""
+    ctx, _ = _problem(B, 2, 1, "elliptic", 32)
+    b = ctx.load()
+    l0 = ctx.launches()
+    _, info = ctx.solve(b, mode="mixed", tol=1e-8)
+    assert info["status"] == 0
+    l1 = ctx.launches()
+    assert l1 - l0 < info["iterations"]
+    _, info = ctx.solve(b, mode="fp64", tol=1e-8)
+    assert info["status"] == 0
+    assert ctx.launches() - l1 > 3 * info["iterations"]
+
+
+def test_single_launch_unsupported_falls_back(B):
+    """Where no single-launch instance exists (2D P3), single_launch=True keeps the
+    per-step PCG and still converges."""
+    ctx, P = _problem(B, 2, 3, "elliptic", 10)
+    b = ctx.load()
+    x, info = ctx.solve(b, mode="mixed", tol=1e-10, single_launch=True)
+    assert info["status"] == 0
+    bb = b.cpu().numpy()
+    assert np.linalg.norm(bb - P.apply(x.cpu().numpy())) <= 1.01e-10 * np.linalg.norm(bb)
