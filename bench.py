@@ -495,6 +495,27 @@ def main():
             if mode == "mixed":
                 t2t["mixed_outer"][f"P{p}"] = info["outer"]
             t2t.setdefault(f"{mode}_rel_residual", {})[f"P{p}"] = info["rel_residual"]
+    # the single-launch PCG (one cooperative kernel per solve; by default the FP32 inner
+    # solves of problems that fit in L2) against the per-step kernels, both precisions
+    sl = {}
+    for p in [q for q in P_LIST if q <= 2]:
+        c = ctxs[p]
+        row = {}
+        for mode in (["mixed"] + ([] if args.no_fp64 else ["fp64"])):
+            for single in (True, False):
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                ev0.record(stream)
+                _, info = c.solve(bs[p], us[p], mode=mode, tol=TOL, check_every=args.check_every,
+                                  allow_notconv=True, single_launch=single)
+                ev1.record(stream)
+                torch.cuda.synchronize()
+                key = f"{mode}_{'single_launch' if single else 'per_step'}"
+                row[f"{key}_ms"] = round(ev0.elapsed_time(ev1), 3)
+                row[f"{key}_iters"] = info["iterations"]
+        sl[f"P{p}"] = row
+    t2t["single_launch_vs_per_step"] = sl
 
     _section("apply")
     # apply throughput and roofline of the dominant kernel (FP32 apply)
