@@ -323,6 +323,57 @@ def csr_pcg(K, b, tol, maxiter=200000, check=50):
 # ------------------------------------------------------------- GPU arm
 
 
+def batch_workload(B, torch, stream):
+    """Config 5: 256 independent 2D elliptic problems, N ~ U{16..128}, p ~ U{1,2,3},
+    lognormal(0, 1) scalar coefficient, f = 1, mixed solves to 1e-8 in one
+    dogip_batch_solve call, in the default (concurrent) mode and in the lockstep
+    grouped mode."""
+    from paper_1710_09913_gb300 import inputs
+    specs = inputs.uneven_problems(256, seed=5)
+    bctx, bb, bu = [], [], []
+    for N, p, sd in specs:
+        bc, bcl = inputs.lattice_mesh(2, N)
+        m = inputs.coef_lognormal(len(bcl), 1.0, sd)
+        c = B.Context(bc, bcl, p, "elliptic", m)
+        c.autotune()  # cached per (p, size bucket) after the first of each kind
+        bctx.append(c)
+        bb.append(c.load())
+        bu.append(torch.zeros(c.n, dtype=torch.float64, device="cuda"))
+    dofs = sum(c.n for c in bctx)
+
+    def run_batch(bmode):
+        os.environ["DOGIP_BATCH_MODE"] = bmode
+        B.batch_solve(bctx, bb, bu, mode="mixed", tol=TOL)  # warm-up (graph capture)
+        l0 = sum(c.launches() for c in bctx)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        infos = B.batch_solve(bctx, bb, bu, mode="mixed", tol=TOL)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        work_b = sum(c.n * (i["iterations"] + i["outer"]) for c, i in zip(bctx, infos))
+        secs = np.array([i["seconds"] for i in infos]) * 1e3
+        return {"mode": bmode, "problems": len(bctx), "dofs": int(dofs), "ms": round(ms, 2),
+                "apply_gdofs": round(work_b / ms / 1e6, 3),
+                "solve_gdofs": round(dofs / ms / 1e6, 4),
+                "p50_ms": round(float(np.percentile(secs, 50)), 2),
+                "p99_ms": round(float(np.percentile(secs, 99)), 2),
+                "max_rel_residual": max(i["rel_residual"] for i in infos),
+                "all_converged": all(i["status"] == 0 for i in infos),
+                "gpu_launches": int(sum(c.launches() for c in bctx) - l0)}
+
+    # concurrent (the default): independent solves side by side; grouped: lockstep
+    # rounds with one launch per kernel for the whole batch
+    batch = run_batch("concurrent")
+    g = run_batch("grouped")
+    batch["grouped_lockstep"] = {k: g[k] for k in ("ms", "apply_gdofs", "p50_ms", "p99_ms",
+                                                    "gpu_launches", "all_converged")}
+    os.environ.pop("DOGIP_BATCH_MODE", None)
+    return batch
+
+
 def only_solve(args):
     """Profiling mode: build the workload at order P and run one mixed solve."""
     import torch
@@ -334,6 +385,16 @@ def only_solve(args):
     b = c.load()
     c.solve(b, mode="mixed", tol=TOL, check_every=args.check_every)
     torch.cuda.synchronize()
+    return 0
+
+
+def only_batch(args):
+    """Profiling mode: the batch of 256 uneven problems, both batch modes."""
+    import torch
+    from paper_1710_09913_gb300 import build
+    build.build()
+    from paper_1710_09913_gb300 import binding as B
+    print(json.dumps(batch_workload(B, torch, torch.cuda.current_stream())), flush=True)
     return 0
 
 
@@ -402,11 +463,16 @@ def main():
                     help="profiling mode: one mixed solve of order P (no JSON line)")
     ap.add_argument("--only-cube", action="store_true",
                     help="profiling mode: --reps 16-rhs applies of the 3D P2 workload (no JSON line)")
+    ap.add_argument("--only-batch", action="store_true",
+                    help="profiling mode: the batch of 256 uneven problems in both batch "
+                         "modes (prints their JSON summary, not the bench line)")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "tf32"])
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.only_batch:
+        return only_batch(args)
     if args.only_cube:
         return only_cube(args)
     if args.only_apply:
@@ -609,38 +675,7 @@ def main():
     # batched uneven problems (256 independent 2D problems, one graph launch per phase)
     batch = None
     if not args.no_batch:
-        from paper_1710_09913_gb300 import inputs
-        specs = inputs.uneven_problems(256, seed=5)
-        bctx, bb, bu = [], [], []
-        for N, p, sd in specs:
-            bc, bcl = inputs.lattice_mesh(2, N)
-            m = inputs.coef_lognormal(len(bcl), 1.0, sd)
-            c = B.Context(bc, bcl, p, "elliptic", m)
-            c.autotune()  # cached per (p, size bucket) after the first of each kind
-            bctx.append(c)
-            bb.append(c.load())
-            bu.append(torch.zeros(c.n, dtype=torch.float64, device="cuda"))
-        B.batch_solve(bctx, bb, bu, mode="mixed", tol=TOL)  # warm-up (graph capture)
-        l0 = sum(c.launches() for c in bctx)
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        infos = B.batch_solve(bctx, bb, bu, mode="mixed", tol=TOL)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        ms = ev0.elapsed_time(ev1)
-        dofs = sum(c.n for c in bctx)
-        work_b = sum(c.n * (i["iterations"] + i["outer"]) for c, i in zip(bctx, infos))
-        secs = np.array([i["seconds"] for i in infos]) * 1e3
-        batch = {"problems": len(bctx), "dofs": int(dofs), "ms": round(ms, 2),
-                 "apply_gdofs": round(work_b / ms / 1e6, 3),
-                 "solve_gdofs": round(dofs / ms / 1e6, 4),
-                 "p50_ms": round(float(np.percentile(secs, 50)), 2),
-                 "p99_ms": round(float(np.percentile(secs, 99)), 2),
-                 "max_rel_residual": max(i["rel_residual"] for i in infos),
-                 "all_converged": all(i["status"] == 0 for i in infos),
-                 "gpu_launches": int(sum(c.launches() for c in bctx) - l0)}
+        batch = batch_workload(B, torch, stream)
         del bctx, bb, bu
 
     _section("cube3d")

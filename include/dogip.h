@@ -355,8 +355,9 @@ typedef struct {
                          recurrence can run the iterations of a solve inside
                          one cooperative kernel (two grid-wide barriers an
                          iteration, up to min(4096, 256 check_every)
-                         iterations a launch; nrhs 1, atomic scatter, 2D and
-                         3D p <= 2, element-wise storage).  -1 (default): the
+                         iterations a launch, its grid sized to the problem;
+                         nrhs 1, atomic scatter, 2D p <= 3 and 3D p <= 2,
+                         element-wise storage).  -1 (default): the
                          FP32 inner solves whose operator and vectors fit in
                          L2 take it (FP64 PCG measured faster per step);
                          0 never (one kernel per step, graph-captured chunks
@@ -434,11 +435,20 @@ DOGIP_API int dogip_autotune(dogip_ctx* ctx, int force, dogip_tune_info* info,
 /*
  * Solve nprob independent problems K_i u_i = b_i together (one right-hand side
  * each; the contexts may differ in mesh, p and form, and must share a device and
- * be distinct).  Each phase of the solve -- FP64 residual, FP32 (or FP64) CG
- * iteration chunk, correction -- is one CUDA graph launch for the whole batch, with
- * one concurrent branch per problem; converged problems skip their work on the
- * device.  Modes DOGIP_SOLVE_FP64 and DOGIP_SOLVE_MIXED (in which every round of
- * inner iterations lasts until all inner solves are done); u_i start at 0.
+ * be distinct).  Modes DOGIP_SOLVE_FP64 and DOGIP_SOLVE_MIXED; u_i start at 0.
+ * The environment variable DOGIP_BATCH_MODE picks how:
+ *   concurrent (default): every problem is an ordinary dogip_solve on its own
+ *     context stream, run by a pool of host threads (16, or DOGIP_BATCH_THREADS),
+ *     the problems with the least estimated work first (DOGIP_BATCH_ORDER =
+ *     smallest, largest or given); problems refine independently and run side
+ *     by side on the GPU, with the per-step PCG kernels unless o->single_launch
+ *     is 1.  Call it from one host thread at a time per set of contexts.
+ *   grouped: lockstep rounds; each phase (FP64 residual, chunk of CG iterations,
+ *     correction) is one CUDA graph launch for the whole batch, the inner FP32
+ *     iterations one launch per kernel over (problem, block) work items; every
+ *     round of inner iterations lasts until all inner solves are done.
+ *   branches: as grouped, with one graph branch per problem in every phase.
+ * Converged problems skip their work on the device in the lockstep modes.
  *   ctxs : host array [nprob] of contexts;  b, u : host arrays [nprob] of DEVICE
  *   double [n_i] vectors;  infos : host [nprob] or NULL -- per problem status,
  *   iterations, refinement steps, final FP64 relative residual, and `seconds` =

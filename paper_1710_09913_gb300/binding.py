@@ -188,16 +188,16 @@ def residual_norms_noalloc(b, Ky, r=None, rel=None, stream=None):
 
 
 def batch_solve(ctxs, bs, us, *, mode="mixed", tol=1e-8, check_every=None, inner_tol=None,
-                max_outer=None, maxiter=None, stream=None):
+                max_outer=None, maxiter=None, stream=None, single_launch=None):
     """Solve independent problems together (dogip_batch_solve); returns per-problem
-    info dicts."""
+    info dicts.  single_launch applies to the concurrent batch mode's solves."""
     import torch
     n = len(ctxs)
     hs = (_vp * n)(*[c._h.value for c in ctxs])
     bp = (_vp * n)(*[_dptr(x, torch.float64).value for x in bs])
     up = (_vp * n)(*[_dptr(x, torch.float64).value for x in us])
     o = ctxs[0]._solve_opts(mode, tol, maxiter, inner_tol, None, max_outer, None, check_every,
-                            False, 0.0)
+                            False, 0.0, single_launch=single_launch)
     infos = (SolveInfo * n)()
     code = lib.dogip_batch_solve(hs, n, bp, up, C.byref(o), infos, _stream(stream))
     _check(code, allow=(ENOTCONV,))

@@ -395,6 +395,7 @@ SmallLaunch small_dispatch(int d, int p, int form, int prec) {
   case ((D * 10 + P) * 2 + F) * 2 + 0: return small_launch<D, P, F, float>();         \
   case ((D * 10 + P) * 2 + F) * 2 + 1: return small_launch<D, P, F, double>();
     DOGIP_SM(2, 1, 0) DOGIP_SM(2, 1, 1) DOGIP_SM(2, 2, 0) DOGIP_SM(2, 2, 1)
+    DOGIP_SM(2, 3, 0) DOGIP_SM(2, 3, 1)
     DOGIP_SM(3, 1, 0) DOGIP_SM(3, 1, 1) DOGIP_SM(3, 2, 0) DOGIP_SM(3, 2, 1)
 #undef DOGIP_SM
     default:
@@ -472,11 +473,16 @@ void pcg_small_run(Ctx& c, int prec, double* x64, int maxit) {
   cudaStream_t s = c.stream;
   const SmallLaunch L = small_dispatch(c.d, c.p, c.form, prec);
   if (!L.fn || L.grid <= 0) fail(DOGIP_EUNSUPPORTED, "no single-launch PCG for this problem");
-  maxit = std::max(0, std::min(maxit, (int)((1u << 31) / (unsigned)(2 * L.grid))));
+  // grid sized to the problem (two cells per thread at least), so that the solves of
+  // small problems can run side by side; every grid up to L.grid is co-resident
+  SmallLaunch Lp = L;
+  const int64_t want = (c.E + 2LL * L.threads - 1) / (2LL * L.threads);
+  Lp.grid = (int)std::max<int64_t>(1, std::min<int64_t>(L.grid, want));
+  maxit = std::max(0, std::min(maxit, (int)((1u << 31) / (unsigned)(2 * Lp.grid))));
   if (prec == DOGIP_FP64)
-    launch_small<double>(c, L, c.d_A64, x64, w.r64, w.p64, w.q64, c.d_dinv64, maxit, s);
+    launch_small<double>(c, Lp, c.d_A64, x64, w.r64, w.p64, w.q64, c.d_dinv64, maxit, s);
   else
-    launch_small<float>(c, L, c.d_A32, w.x32, w.r32, w.p32, w.q32, c.d_dinv32, maxit, s);
+    launch_small<float>(c, Lp, c.d_A32, w.x32, w.r32, w.p32, w.q32, c.d_dinv32, maxit, s);
   ++c.launches;
   cuda_check(cudaMemcpyAsync(w.h_flags, w.flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, s),
              "flags copy");
