@@ -358,8 +358,9 @@ typedef struct {
                          iterations a launch, its grid sized to the problem;
                          nrhs 1, atomic scatter, 2D p <= 3 and 3D p <= 2,
                          element-wise storage).  -1 (default): the
-                         FP32 inner solves whose operator and vectors fit in
-                         L2 take it (FP64 PCG measured faster per step);
+                         FP32 inner solves at p <= 2 whose operator and
+                         vectors fit in L2 take it (FP64 PCG and 2D P3
+                         measured faster per step);
                          0 never (one kernel per step, graph-captured chunks
                          of check_every iterations); 1 whenever supported,
                          FP64 included (else as 0)                          */

@@ -782,16 +782,18 @@ int solve(Ctx& c, const double* b, double* u, int R, const dogip_solve_opts* opt
   // The PCG iterations (FP64 mode, or the standard FP32 inner recurrence of MIXED) in
   // one cooperative launch when the problem stays in L2: its iteration cost is then
   // latency, which the kernel boundaries of the graph-captured chunks would dominate.
-  // By default only the FP32 inner solves take it: measured on GB300 (2D P1 and P2 on
-  // 512 x 512 squares) it is faster there, while FP64 PCG, whose one-thread-per-cell
-  // apply is bound by the FP64 rate, is faster with the per-step kernels.
+  // By default only the FP32 inner solves at p <= 2 take it: measured on GB300 (2D P1
+  // and P2 on 512 x 512 squares, 3D P1 and P2 on 32^3 cubes) it is faster there; at
+  // 2D P3 (128 x 128 squares) it was 4 % slower, and FP64 PCG, whose one-thread-per-
+  // cell apply is bound by the FP64 rate, is faster with the per-step kernels.
   const int cg_prec = o.mode == DOGIP_SOLVE_FP64 ? DOGIP_FP64 : DOGIP_FP32;
   bool single = false;
   if (o.single_launch != 0 && R == 1 && scatter == DOGIP_SCATTER_ATOMIC && rec == 0 &&
       o.mode != DOGIP_SOLVE_MIXED_RELIABLE && (o.mode == DOGIP_SOLVE_FP64 || ip == DOGIP_FP32) &&
       pcg_small_supported(c, cg_prec))
     single = o.single_launch == 1 ||
-             (cg_prec == DOGIP_FP32 && c.l2_bytes > 0 && pcg_small_bytes(c, cg_prec) <= c.l2_bytes);
+             (cg_prec == DOGIP_FP32 && c.p <= 2 && c.l2_bytes > 0 &&
+              pcg_small_bytes(c, cg_prec) <= c.l2_bytes);
   // iterations per single launch (host checks for timeouts between launches)
   const int step_iters = single ? std::min(4096, 256 * chunk) : chunk;
   cuda_check(cudaEventRecord(c.ev_in, user), "event record");
