@@ -672,11 +672,11 @@ def main():
             torch.cuda.empty_cache()
 
     _section("batch")
-    # batched uneven problems (256 independent 2D problems, one graph launch per phase)
+    # batched uneven problems (256 independent 2D problems; concurrent and grouped modes)
     batch = None
     if not args.no_batch:
         batch = batch_workload(B, torch, stream)
-        del bctx, bb, bu
+        torch.cuda.empty_cache()
 
     _section("cube3d")
     # 3D, 64^3 cube x 6 tetrahedra, P2, inclusions, 16 right-hand sides in one launch
