@@ -46,6 +46,8 @@
  *  - DOGIP_GRAPH_PDL: 1 (default) launches the kernels of a captured CG chunk as
  *    programmatic dependents of each other where they are written for it (the next
  *    kernel starts while the previous one drains); 0 keeps full serialisation.
+ *  - DOGIP_BATCH_MODE, DOGIP_BATCH_ORDER, DOGIP_BATCH_THREADS: how dogip_batch_solve
+ *    runs its problems (see there).
  *  - DOGIP_TEST_WAIT_CYCLES, DOGIP_TEST_SKIP_CHUNK: test hooks of the device-side
  *    failure path (a shorter bound on the kernels' waits; one chunk of the staged
  *    apply, or one tile of the tensor-core apply, whose copy is never issued, and

@@ -21,8 +21,6 @@
 // possibly stale L1 line.  Each barrier wait is bounded by a clock budget: on expiry
 // the block raises the kernel error flag and leaves; the others see the flag (or run
 // out of budget) at their next wait and leave too.
-#include <cstdlib>
-
 #include "kernels.cuh"
 
 namespace dogip {
@@ -363,29 +361,27 @@ struct SmallLaunch {
 
 template <int D, int P, int FORM, typename T>
 SmallLaunch small_launch() {
-  static SmallLaunch L = [] {
-    constexpr int NT = pcg_threads<D, P, T>();
-    SmallLaunch t;
-    t.fn = (const void*)k_pcg_small<D, P, FORM, T, NT>;
-    t.threads = NT;
-    int dev = 0, sms = 1, nb = 0;
-    cuda_check(cudaGetDevice(&dev), "device");
-    cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+  constexpr int NT = pcg_threads<D, P, T>();
+  // resident blocks per SM: a property of the kernel and the architecture (cached);
+  // the SM count is read for the current device at every call
+  static const int per_sm = [] {
+    int nb = 0;
     cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pcg_small<D, P, FORM, T, NT>,
                                                              NT, 0),
                "occupancy");
-    // every block must be resident at once (cooperative launch); the partial buffer
-    // holds 4 doubles per block.  DOGIP_SINGLE_LAUNCH_BPS caps the blocks per SM.
-    nb = std::max(nb, 0);
-    if (const char* v = std::getenv("DOGIP_SINGLE_LAUNCH_BPS")) {
-      const int cap = std::atoi(v);
-      if (cap > 0) nb = std::min(nb, cap);
-    }
-    t.per_sm = nb;
-    t.grid = std::min(nb * sms, kMaxRedBlocks);
-    return t;
+    return std::max(nb, 0);
   }();
-  return L;
+  SmallLaunch t;
+  t.fn = (const void*)k_pcg_small<D, P, FORM, T, NT>;
+  t.threads = NT;
+  int dev = 0, sms = 1;
+  cuda_check(cudaGetDevice(&dev), "device");
+  cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+  // every block must be resident at once (cooperative launch); the partial buffer
+  // holds 4 doubles per block
+  t.per_sm = per_sm;
+  t.grid = std::min(per_sm * sms, kMaxRedBlocks);
+  return t;
 }
 
 SmallLaunch small_dispatch(int d, int p, int form, int prec) {
