@@ -113,7 +113,10 @@ extern "C" {
 
 typedef struct dogip_ctx dogip_ctx;
 
-/* Simplex mesh, host memory, caller order.  The library copies it. */
+/* Simplex mesh, host memory, caller order.  The library copies it.  There is no
+ * per-vertex boundary flag: the boundary is derived from the cells (a facet that
+ * belongs to exactly one cell is on the boundary, and so are the dofs on it), which
+ * is the boundary of the meshed domain for any conforming simplex mesh. */
 typedef struct {
   int dim;                 /* 2 (triangles) or 3 (tetrahedra)                  */
   int64_t n_vertices;
