@@ -87,3 +87,48 @@ def test_setup_rejects_bad_input_on_host(lib):
     with pytest.raises(lib.DogipError) as e:
         lib.Context(nanc, cells, 1, "elliptic", coef)
     assert e.value.code == lib.EINVAL
+
+
+def _struct_fields(name):
+    """(type, field) pairs of a typedef struct in include/dogip.h, comments removed."""
+    src = open(os.path.join(ROOT, "include", "dogip.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    m = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r"\s*;", src)
+    assert m, name
+    out = []
+    for decl in m.group(1).split(";"):
+        decl = " ".join(decl.split())
+        if decl:
+            typ, names = re.match(r"(\w+)\s+(.*)", decl).groups()
+            out += [(typ, nm.strip()) for nm in names.split(",")]
+    return out
+
+
+def test_solve_opts_layout_and_defaults(lib):
+    """The binding's ctypes mirror of dogip_solve_opts has the header's fields in the
+    header's order and types (an ABI drift would scramble every solve option), and
+    dogip_solve_opts_default fills the documented defaults."""
+    ctype = {"int": C.c_int, "double": C.c_double}
+    hdr = _struct_fields("dogip_solve_opts")
+    py = lib.SolveOpts._fields_
+    assert [f for _, f in hdr] == [f for f, _ in py]
+    assert all(ctype[t] is pt for (t, _), (_, pt) in zip(hdr, py))
+    o = lib.SolveOpts()
+    assert lib.lib.dogip_solve_opts_default(C.byref(o)) == lib.OK
+    assert o.mode == lib.SOLVE_FP64 and o.tol == 1e-8 and o.check_every == 16
+    assert o.inner_tol == 1e-4 and o.reliable_delta == 0.1 and o.scatter == -1
+    assert o.inner_prec == lib.FP32 and o.inner_recurrence == 0 and o.single_launch == -1
+
+
+def test_solve_info_layout(lib):
+    hdr = _struct_fields("dogip_solve_info")
+    assert [f for _, f in hdr] == [f for f, _ in lib.SolveInfo._fields_]
+
+
+@pytest.mark.parametrize("cname,pyname", [("dogip_opts", "Opts"), ("dogip_info", "Info")])
+def test_setup_struct_layouts(lib, cname, pyname):
+    ctype = {"int": C.c_int, "double": C.c_double, "int64_t": C.c_int64}
+    hdr = _struct_fields(cname)
+    py = getattr(lib, pyname)._fields_
+    assert [f for _, f in hdr] == [f for f, _ in py]
+    assert all(ctype[t] is pt for (t, _), (_, pt) in zip(hdr, py))
